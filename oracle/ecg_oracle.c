@@ -1,0 +1,581 @@
+/*
+ * ecg_oracle.c -- plain, slow, double-precision CPU oracle for the enlarged
+ * Conjugate Gradient methods of S. Moufawad, "Flexibly Enlarged Conjugate
+ * Gradient methods" (arXiv 2305.19013).
+ *
+ * TEST INFRASTRUCTURE.  This file exists to check the CUDA solver.  Only the
+ * test suite, the smoke check and the CPU-baseline leg of the benchmark load
+ * it.  It shares no code, header, table or helper with the CUDA path; it is
+ * single-threaded, uses no BLAS, and runs every loop in its obvious order.
+ * It is compiled with -ffp-contract=off so that x86 and Arm builds round
+ * identically.
+ *
+ * Conventions.  A block of w vectors of length n is a row-major n x w array
+ * (entry (i, j) at [i*w + j]).  Small w x w matrices are row-major too.
+ *
+ * Readings of the paper taken here where it is silent or garbled (each is
+ * repeated at the function that uses it):
+ *   - CGS2 ("Algorithm 18" of the author's thesis, not reproduced in the
+ *     paper, Section 2.1 and Section 5): block classical Gram-Schmidt in the
+ *     A-inner product, two full passes, with C = (A Q)^T W read off the
+ *     stored A Q blocks.
+ *   - Pre-CholQR (Section 5; the paper cites it without its body): a
+ *     Householder QR of the block, signs fixed so that diag(R) > 0, followed
+ *     by A-CholQR of the orthonormal factor.  A-CholQR alone is the other
+ *     option Section 2.1 names and is kept as a mode.
+ *   - Breakdown (not discussed in the paper): a Cholesky pivot that is not
+ *     larger than 1e-14 times the diagonal entry it started from, or is not
+ *     finite, stops the solve with status BREAKDOWN and the current iterate.
+ *   - The switch test uses |rho_k - rho_{k-1}| / rho_0 (Section 4.2 and the
+ *     restart test of Section 3 write the absolute value; Algorithms 3 and 4
+ *     drop it, which would trigger the switch at the first decrease).
+ *   - Halving pairs 0-based subdomains {2j, 2j+1} into subdomain j
+ *     (Section 4, the merged sets delta~_i = delta_{2i-1} U delta_{2i}).
+ *   - The loop runs while rho_{k-1} > eps*rho_0 and k < k_max (Algorithm 1),
+ *     so at most k_max - 1 iterations; "iters" is the number of loop bodies.
+ *   - switch_it is the last iteration that used t vectors (k_F of
+ *     Section 4.1), so that mem = t*switch_it + (t/2)*(iters - switch_it)
+ *     as in Tables 6-9.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_OK 0
+#define OR_ENOCONV 1
+#define OR_EINVAL (-1)
+#define OR_ENOMEM (-2)
+#define OR_EBREAKDOWN (-4)
+#define OR_ENOTSPD (-5)
+
+#define OR_BREAKDOWN_RATIO 1e-14
+
+/* ---------------------------------------------------------------- products */
+
+/* y = A x for A in CSR (Algorithm 1 line 1: r0 = b - A x0). */
+void or_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+             const double* x, double* y) {
+  for (int64_t i = 0; i < n; i++) {
+    double s = 0.0;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * x[col[p]];
+    y[i] = s;
+  }
+}
+
+/* Y = A X for an n x w block X (the product A W_{k-1} of Algorithm 1 line 6
+ * and V_k = A P_k of Algorithm 2 line 9). */
+void or_spmm(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int w,
+             const double* X, double* Y) {
+  for (int64_t i = 0; i < n; i++) {
+    for (int c = 0; c < w; c++) {
+      double s = 0.0;
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * X[(int64_t)col[p] * w + c];
+      Y[i * w + c] = s;
+    }
+  }
+}
+
+/* W = [T^t(r)]: column j holds r restricted to subdomain delta_j, zero
+ * elsewhere (Section 1, eq. (Tt)). */
+void or_split(int64_t n, const int32_t* part, int t, const double* r, double* W) {
+  for (int64_t i = 0; i < n; i++) {
+    for (int j = 0; j < t; j++) W[i * t + j] = 0.0;
+    W[i * t + part[i]] = r[i];
+  }
+}
+
+/* W = [T^{t/2}(r)] over the merged subdomains {2j, 2j+1} (Section 4,
+ * eq. (Tt)); W is n x t/2. */
+void or_split_half(int64_t n, const int32_t* part, int t, const double* r, double* W) {
+  int h = t / 2;
+  for (int64_t i = 0; i < n; i++) {
+    for (int j = 0; j < h; j++) W[i * h + j] = 0.0;
+    W[i * h + part[i] / 2] = r[i];
+  }
+}
+
+/* C = X^T Y (wx x wy) for n x wx X and n x wy Y: the block inner products
+ * W^T r, P^T A P and (AQ)^T W of Sections 2-4. */
+void or_block_tdot(int64_t n, int wx, const double* X, int wy, const double* Y, double* C) {
+  for (int a = 0; a < wx; a++)
+    for (int b = 0; b < wy; b++) {
+      double s = 0.0;
+      for (int64_t i = 0; i < n; i++) s += X[i * wx + a] * Y[i * wy + b];
+      C[a * wy + b] = s;
+    }
+}
+
+/* W -= Q C for n x wq Q, wq x w C and n x w W (the CGS update). */
+void or_block_sub(int64_t n, int wq, const double* Q, int w, const double* C, double* W) {
+  for (int64_t i = 0; i < n; i++)
+    for (int b = 0; b < w; b++) {
+      double s = 0.0;
+      for (int a = 0; a < wq; a++) s += Q[i * wq + a] * C[a * w + b];
+      W[i * w + b] -= s;
+    }
+}
+
+/* X <- X R^{-1} for upper-triangular R, one row at a time. */
+void or_right_trsm(int64_t n, int w, const double* R, double* X) {
+  for (int64_t i = 0; i < n; i++) {
+    double* x = X + i * w;
+    for (int j = 0; j < w; j++) {
+      double s = x[j];
+      for (int a = 0; a < j; a++) s -= x[a] * R[a * w + j];
+      x[j] = s / R[j * w + j];
+    }
+  }
+}
+
+/* -------------------------------------------------------------- small dense */
+
+/* Cholesky G = R^T R, R upper triangular with positive diagonal; only the
+ * upper triangle of G is read.  Returns 0, or j+1 when pivot j fails the
+ * breakdown test (pivot <= 1e-14 * G_jj, or not finite). */
+int or_cholesky(int w, const double* G, double* R) {
+  for (int i = 0; i < w * w; i++) R[i] = 0.0;
+  for (int j = 0; j < w; j++) {
+    double d = G[j * w + j];
+    for (int k = 0; k < j; k++) d -= R[k * w + j] * R[k * w + j];
+    if (!(d > OR_BREAKDOWN_RATIO * G[j * w + j]) || !isfinite(d)) return j + 1;
+    double rjj = sqrt(d);
+    R[j * w + j] = rjj;
+    for (int i = j + 1; i < w; i++) {
+      double s = G[j * w + i];
+      for (int k = 0; k < j; k++) s -= R[k * w + j] * R[k * w + i];
+      R[j * w + i] = s / rjj;
+    }
+  }
+  return 0;
+}
+
+/* Thin Householder QR of the n x w block W (n >= w): W = Q R with Q n x w,
+ * Q^T Q = I, R upper triangular with nonnegative diagonal.  Returns 0, or
+ * j+1 when column j is numerically dependent on the columns before it
+ * (R_jj^2 <= 1e-14 ||w_j||^2), mirroring the Cholesky test. */
+int or_householder_qr(int64_t n, int w, const double* W, double* Q, double* R) {
+  double* Wc = (double*)malloc(sizeof(double) * (size_t)(n * w));
+  double* Vh = (double*)malloc(sizeof(double) * (size_t)(n * w)); /* Householder vectors */
+  double* beta = (double*)malloc(sizeof(double) * (size_t)w);
+  double* cn2 = (double*)malloc(sizeof(double) * (size_t)w);
+  if (!Wc || !Vh || !beta || !cn2) {
+    free(Wc); free(Vh); free(beta); free(cn2);
+    return -1;
+  }
+  memcpy(Wc, W, sizeof(double) * (size_t)(n * w));
+  for (int j = 0; j < w; j++) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += W[i * w + j] * W[i * w + j];
+    cn2[j] = s;
+  }
+  for (int j = 0; j < w; j++) {
+    /* Householder vector for Wc[j:, j]. */
+    double nx2 = 0.0;
+    for (int64_t i = j; i < n; i++) nx2 += Wc[i * w + j] * Wc[i * w + j];
+    double nx = sqrt(nx2);
+    double x0 = Wc[(int64_t)j * w + j];
+    double alpha = (x0 >= 0.0) ? -nx : nx;
+    for (int64_t i = 0; i < n; i++) Vh[i * w + j] = 0.0;
+    for (int64_t i = j; i < n; i++) Vh[i * w + j] = Wc[i * w + j];
+    Vh[(int64_t)j * w + j] -= alpha;
+    double vn2 = 0.0;
+    for (int64_t i = j; i < n; i++) vn2 += Vh[i * w + j] * Vh[i * w + j];
+    beta[j] = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
+    /* Apply H_j = I - beta v v^T to Wc[j:, j:]. */
+    for (int c = j; c < w; c++) {
+      double d = 0.0;
+      for (int64_t i = j; i < n; i++) d += Vh[i * w + j] * Wc[i * w + c];
+      d *= beta[j];
+      for (int64_t i = j; i < n; i++) Wc[i * w + c] -= d * Vh[i * w + j];
+    }
+  }
+  for (int a = 0; a < w; a++)
+    for (int b = 0; b < w; b++) R[a * w + b] = (b >= a) ? Wc[(int64_t)a * w + b] : 0.0;
+  /* Q = H_0 ... H_{w-1} [I; 0]. */
+  for (int64_t i = 0; i < n; i++)
+    for (int c = 0; c < w; c++) Q[i * w + c] = (i == c) ? 1.0 : 0.0;
+  for (int j = w - 1; j >= 0; j--) {
+    for (int c = 0; c < w; c++) {
+      double d = 0.0;
+      for (int64_t i = j; i < n; i++) d += Vh[i * w + j] * Q[i * w + c];
+      d *= beta[j];
+      for (int64_t i = j; i < n; i++) Q[i * w + c] -= d * Vh[i * w + j];
+    }
+  }
+  /* Make diag(R) nonnegative. */
+  for (int j = 0; j < w; j++) {
+    if (R[j * w + j] < 0.0) {
+      for (int b = 0; b < w; b++) R[j * w + b] = -R[j * w + b];
+      for (int64_t i = 0; i < n; i++) Q[i * w + j] = -Q[i * w + j];
+    }
+  }
+  int status = 0;
+  for (int j = 0; j < w; j++) {
+    double rjj = R[j * w + j];
+    if (!(rjj * rjj > OR_BREAKDOWN_RATIO * cn2[j]) || !isfinite(rjj)) {
+      status = j + 1;
+      break;
+    }
+  }
+  free(Wc); free(Vh); free(beta); free(cn2);
+  return status;
+}
+
+/* Dense SPD solve by Cholesky for the small agreement checks: A x = b with A
+ * an n x n row-major matrix.  Returns 0, or 1 if a pivot is not positive. */
+int or_dense_spd_solve(int n, const double* A, const double* b, double* x) {
+  double* L = (double*)calloc((size_t)n * n, sizeof(double));
+  double* y = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!L || !y) { free(L); free(y); return -1; }
+  for (int j = 0; j < n; j++) {
+    double d = A[j * n + j];
+    for (int k = 0; k < j; k++) d -= L[j * n + k] * L[j * n + k];
+    if (!(d > 0.0)) { free(L); free(y); return 1; }
+    L[j * n + j] = sqrt(d);
+    for (int i = j + 1; i < n; i++) {
+      double s = A[i * n + j];
+      for (int k = 0; k < j; k++) s -= L[i * n + k] * L[j * n + k];
+      L[i * n + j] = s / L[j * n + j];
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    double s = b[i];
+    for (int k = 0; k < i; k++) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    double s = y[i];
+    for (int k = i + 1; k < n; k++) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+  free(L); free(y);
+  return 0;
+}
+
+/* ------------------------------------------------------ A-orthonormalisation */
+
+/* A-orthonormalise the n x w block W in place ("A-orthonormalize W_k",
+ * Algorithm 1 lines 4 and 8).  On return W holds W_k with W_k^T A W_k = I and
+ * V holds A W_k.  mode 0: Pre-CholQR (Householder QR W = Q_e R_e, then
+ * A-CholQR of Q_e: Q_e^T A Q_e = S^T S, W_k = Q_e S^{-1}, A W_k =
+ * (A Q_e) S^{-1}).  mode 1: A-CholQR (W^T A W = R^T R, W_k = W R^{-1}).
+ * Returns 0 or OR_EBREAKDOWN. */
+int or_a_orthonormalize(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                        int w, int mode, double* W, double* V) {
+  double* G = (double*)malloc(sizeof(double) * (size_t)(w * w));
+  double* R = (double*)malloc(sizeof(double) * (size_t)(w * w));
+  double* Qe = NULL;
+  int status = OR_OK;
+  if (!G || !R) { free(G); free(R); return OR_ENOMEM; }
+  if (mode == 0) {
+    Qe = (double*)malloc(sizeof(double) * (size_t)(n * w));
+    if (!Qe) { free(G); free(R); return OR_ENOMEM; }
+    int qs = or_householder_qr(n, w, W, Qe, R);
+    if (qs < 0) { status = OR_ENOMEM; goto done; }
+    if (qs > 0) { status = OR_EBREAKDOWN; goto done; }
+    memcpy(W, Qe, sizeof(double) * (size_t)(n * w));
+  }
+  or_spmm(n, rowptr, col, val, w, W, V);
+  or_block_tdot(n, w, W, w, V, G);
+  if (or_cholesky(w, G, R) != 0) { status = OR_EBREAKDOWN; goto done; }
+  or_right_trsm(n, w, R, W);
+  or_right_trsm(n, w, R, V);
+done:
+  free(G); free(R); free(Qe);
+  return status;
+}
+
+/* Two passes of block classical Gram-Schmidt in the A-inner product of W
+ * (n x w) against the m stored blocks Q_j (n x wq[j]) with V_j = A Q_j
+ * ("A-orthonormalize W_k against Q", Algorithm 1 line 7; CGS2 per Sections
+ * 2.1 and 5).  Each pass computes every coefficient block C_j = V_j^T W from
+ * the same W, then subtracts sum_j Q_j C_j. */
+int or_cgs2(int64_t n, int m, const double* const* Q, const double* const* V, const int* wq, int w,
+            double* W) {
+  int tot = 0;
+  for (int j = 0; j < m; j++) tot += wq[j];
+  double* C = (double*)malloc(sizeof(double) * (size_t)((tot > 0 ? tot : 1) * w));
+  if (!C) return OR_ENOMEM;
+  for (int pass = 0; pass < 2; pass++) {
+    int off = 0;
+    for (int j = 0; j < m; j++) {
+      or_block_tdot(n, wq[j], V[j], w, W, C + (size_t)off * w);
+      off += wq[j];
+    }
+    off = 0;
+    for (int j = 0; j < m; j++) {
+      or_block_sub(n, wq[j], Q[j], w, C + (size_t)off * w, W);
+      off += wq[j];
+    }
+  }
+  free(C);
+  return OR_OK;
+}
+
+/* ----------------------------------------------------------------- solvers */
+
+typedef struct {
+  int iters;            /* loop bodies executed (k - 1 at exit) */
+  int switch_it;        /* k_F: last iteration with t vectors; 0 if no switch */
+  int status;           /* OR_OK, OR_ENOCONV, OR_EBREAKDOWN, OR_EINVAL, ... */
+  int64_t mem_vectors;  /* largest number of stored basis vectors */
+  double relres;        /* rho_k / rho_0 (recursively updated residual) */
+  double relres_true;   /* ||b - A x|| / ||b|| */
+} or_result;
+
+static double or_norm2(int64_t n, const double* v) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; i++) s += v[i] * v[i];
+  return sqrt(s);
+}
+
+/* Enlarged CG.  variant 0: SRE-CG2 (Algorithm 1; W_k = A W_{k-1}); 1: MSDO-CG
+ * (Algorithm 2; P_k = T(r_{k-1}) + P_{k-1} diag(beta_k), beta_k =
+ * -V_{k-1}^T r_{k-1}); 2: modified MSDO-CG (Section 2.2; W_k = T(r_{k-1})).
+ * trunc == 0 orthonormalises against every stored block; trunc >= 1 against
+ * the last trunc blocks only (Section 3; trunc = 2 on variant 0 is SRE-CG).
+ * switch_tol > 0 enables the flexible halving of Algorithms 3 and 4.
+ * ortho: 0 Pre-CholQR, 1 A-CholQR.  k_max follows Algorithm 1 (at most
+ * k_max - 1 iterations).  history (length k_max, may be NULL) receives rho_k
+ * for k = 0..iters.  xhist (n * (k_max - 1), may be NULL) receives x_k after
+ * iteration k at offset (k-1)*n.  basis (may be NULL) receives every W_k
+ * in order, block after block (n * sum of widths entries, capacity
+ * basis_cap doubles); widths (k_max entries, may be NULL) their widths. */
+int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                 const int32_t* part, int t, int variant, int trunc, double switch_tol, int ortho,
+                 const double* b, const double* x0, double eps, int kmax, double* x,
+                 double* history, double* xhist, double* basis, int64_t basis_cap, int* widths,
+                 or_result* res) {
+  memset(res, 0, sizeof(*res));
+  if (n <= 0 || t < 1 || variant < 0 || variant > 2 || trunc < 0 || ortho < 0 || ortho > 1 ||
+      !(eps >= 0.0) || (switch_tol > 0.0 && (t % 2 != 0))) {
+    res->status = OR_EINVAL;
+    return OR_EINVAL;
+  }
+  {
+    /* Every subdomain must be non-empty and every id in [0, t). */
+    int* cnt = (int*)calloc((size_t)t, sizeof(int));
+    if (!cnt) { res->status = OR_ENOMEM; return OR_ENOMEM; }
+    int bad = 0;
+    for (int64_t i = 0; i < n; i++) {
+      if (part[i] < 0 || part[i] >= t) { bad = 1; break; }
+      cnt[part[i]]++;
+    }
+    for (int j = 0; j < t && !bad; j++) if (cnt[j] == 0) bad = 1;
+    free(cnt);
+    if (bad) { res->status = OR_EINVAL; return OR_EINVAL; }
+  }
+  for (int64_t i = 0; i < n; i++) {
+    double d = 0.0;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) if (col[p] == i) d += val[p];
+    if (!(d > 0.0)) { res->status = OR_ENOTSPD; return OR_ENOTSPD; }
+  }
+
+  int cap = (trunc == 0) ? (kmax > 1 ? kmax : 1) : trunc; /* blocks kept in Q */
+  double** Qb = (double**)calloc((size_t)cap, sizeof(double*));
+  double** Vb = (double**)calloc((size_t)cap, sizeof(double*));
+  int* wq = (int*)calloc((size_t)cap, sizeof(int));
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+  double* W = (double*)malloc(sizeof(double) * (size_t)(n * t));
+  double* Vn = (double*)malloc(sizeof(double) * (size_t)(n * t));
+  double* Pprev = (double*)malloc(sizeof(double) * (size_t)(n * t)); /* P_{k-1} */
+  double* Vprev = (double*)malloc(sizeof(double) * (size_t)(n * t)); /* V_{k-1} = A P_{k-1} */
+  double* alpha = (double*)malloc(sizeof(double) * (size_t)t);
+  double* beta = (double*)malloc(sizeof(double) * (size_t)t);
+  const double** qs = (const double**)calloc((size_t)cap, sizeof(double*));
+  const double** vs = (const double**)calloc((size_t)cap, sizeof(double*));
+  int* ws = (int*)calloc((size_t)cap, sizeof(int));
+  double rho0 = 0.0;
+  int64_t mem = 0;
+  int status = OR_ENOCONV;
+  int k = 1;
+  if (!Qb || !Vb || !wq || !r || !tmp || !W || !Vn || !Pprev || !Vprev || !alpha || !beta || !qs ||
+      !vs || !ws) {
+    status = OR_ENOMEM;
+    goto out;
+  }
+
+  /* Algorithm 1 line 1: r0 = b - A x0, rho0 = ||r0||. */
+  if (x0) memcpy(x, x0, sizeof(double) * (size_t)n);
+  else memset(x, 0, sizeof(double) * (size_t)n);
+  or_spmv(n, rowptr, col, val, x, tmp);
+  for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
+  rho0 = or_norm2(n, r);
+  double rho_prev = rho0;
+  double tol1 = 1.0;
+  int counter = 0;
+  int width = t;      /* width of the block generated this iteration */
+  int wprev = t;      /* width of W_{k-1} / P_{k-1} */
+  int nq = 0;         /* blocks currently in Q */
+  int head = 0;       /* ring position of the oldest block */
+  int64_t basis_used = 0;
+  if (history) history[0] = rho0;
+
+  while (rho_prev > eps * rho0 && k < kmax) {
+    /* ---- generate the raw block (Algorithms 1-4, lines 3-11) ---- */
+    if (k == 1) {
+      width = t;
+      or_split(n, part, t, r, W); /* W_1 = [T^t(r_0)] */
+    } else if (switch_tol > 0.0 && tol1 < switch_tol && counter == 0) {
+      width = t / 2;
+      or_split_half(n, part, t, r, W); /* W_k = [T^{t/2}(r_{k-1})] */
+      counter = 1;
+      res->switch_it = k - 1;
+    } else {
+      width = wprev;
+      if (variant == 0) {
+        memcpy(W, Vprev, sizeof(double) * (size_t)(n * width)); /* W_k = A W_{k-1} */
+      } else {
+        if (width == t) or_split(n, part, t, r, W);
+        else or_split_half(n, part, t, r, W);
+        if (variant == 1) {
+          /* beta_k = -V_{k-1}^T r_{k-1}; P_k = T(r_{k-1}) + P_{k-1} diag(beta_k). */
+          or_block_tdot(n, width, Vprev, 1, r, beta);
+          for (int j = 0; j < width; j++) beta[j] = -beta[j];
+          for (int64_t i = 0; i < n; i++)
+            for (int j = 0; j < width; j++) W[i * width + j] += Pprev[i * width + j] * beta[j];
+        }
+      }
+    }
+
+    /* ---- A-orthonormalise against Q (CGS2), then itself ---- */
+    int64_t stored = width;
+    if (k > 1 && nq > 0) {
+      int m = nq;
+      for (int j = 0; j < m; j++) {
+        int slot = (head + j) % cap;
+        qs[j] = Qb[slot];
+        vs[j] = Vb[slot];
+        ws[j] = wq[slot];
+        stored += wq[slot];
+      }
+      int cs = or_cgs2(n, m, qs, vs, ws, width, W);
+      if (cs != OR_OK) { status = cs; goto out; }
+    }
+    if (stored > mem) mem = stored;
+    int st = or_a_orthonormalize(n, rowptr, col, val, width, ortho, W, Vn);
+    if (st != OR_OK) { status = st; goto out; }
+
+    /* ---- push (W_k, V_k) into Q, dropping the oldest beyond trunc ---- */
+    {
+      int slot;
+      if (nq < cap) {
+        slot = (head + nq) % cap;
+        nq++;
+      } else {
+        slot = head;
+        head = (head + 1) % cap;
+      }
+      if (!Qb[slot]) {
+        Qb[slot] = (double*)malloc(sizeof(double) * (size_t)(n * t));
+        Vb[slot] = (double*)malloc(sizeof(double) * (size_t)(n * t));
+        if (!Qb[slot] || !Vb[slot]) { status = OR_ENOMEM; goto out; }
+      }
+      memcpy(Qb[slot], W, sizeof(double) * (size_t)(n * width));
+      memcpy(Vb[slot], Vn, sizeof(double) * (size_t)(n * width));
+      wq[slot] = width;
+    }
+    if (basis && basis_used + n * width <= basis_cap) {
+      memcpy(basis + basis_used, W, sizeof(double) * (size_t)(n * width));
+      basis_used += n * width;
+    }
+    if (widths) widths[k - 1] = width;
+
+    /* ---- alpha_k = W_k^T r_{k-1}; x_k, r_k, rho_k (lines 12-15) ---- */
+    or_block_tdot(n, width, W, 1, r, alpha);
+    for (int64_t i = 0; i < n; i++) {
+      double sx = 0.0, sr = 0.0;
+      for (int j = 0; j < width; j++) {
+        sx += W[i * width + j] * alpha[j];
+        sr += Vn[i * width + j] * alpha[j];
+      }
+      x[i] += sx;
+      r[i] -= sr;
+    }
+    double rho = or_norm2(n, r);
+    tol1 = fabs(rho - rho_prev) / rho0;
+    rho_prev = rho;
+    if (history) history[k] = rho;
+    if (xhist) memcpy(xhist + (int64_t)(k - 1) * n, x, sizeof(double) * (size_t)n);
+    memcpy(Pprev, W, sizeof(double) * (size_t)(n * width));
+    memcpy(Vprev, Vn, sizeof(double) * (size_t)(n * width));
+    wprev = width;
+    k++;
+  }
+  if (status == OR_ENOCONV && rho_prev <= eps * rho0) status = OR_OK;
+
+out:
+  res->iters = k - 1;
+  res->status = status;
+  res->mem_vectors = mem;
+  if (r && tmp) {
+    double rr = or_norm2(n, r);
+    res->relres = (rho0 > 0.0) ? rr / rho0 : rr;
+    or_spmv(n, rowptr, col, val, x, tmp);
+    for (int64_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
+    double nb = or_norm2(n, b);
+    res->relres_true = (nb > 0.0) ? or_norm2(n, tmp) / nb : or_norm2(n, tmp);
+  }
+  if (Qb) for (int j = 0; j < cap; j++) free(Qb[j]);
+  if (Vb) for (int j = 0; j < cap; j++) free(Vb[j]);
+  free(Qb); free(Vb); free(wq); free(r); free(tmp); free(W); free(Vn); free(Pprev); free(Vprev);
+  free(alpha); free(beta); free(qs); free(vs); free(ws);
+  return status;
+}
+
+/* Classical CG (Hestenes-Stiefel), the method of Section 1 that the enlarged
+ * methods generalise.  Same loop convention as or_ecg_solve: at most
+ * k_max - 1 iterations, stop when ||r_k|| <= eps ||r_0||. */
+int or_cg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                const double* b, const double* x0, double eps, int kmax, double* x,
+                double* history, double* xhist, or_result* res) {
+  memset(res, 0, sizeof(*res));
+  double* r = (double*)malloc(sizeof(double) * (size_t)n);
+  double* p = (double*)malloc(sizeof(double) * (size_t)n);
+  double* q = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!r || !p || !q) { free(r); free(p); free(q); res->status = OR_ENOMEM; return OR_ENOMEM; }
+  if (x0) memcpy(x, x0, sizeof(double) * (size_t)n);
+  else memset(x, 0, sizeof(double) * (size_t)n);
+  or_spmv(n, rowptr, col, val, x, q);
+  for (int64_t i = 0; i < n; i++) { r[i] = b[i] - q[i]; p[i] = r[i]; }
+  double rr = 0.0;
+  for (int64_t i = 0; i < n; i++) rr += r[i] * r[i];
+  double rho0 = sqrt(rr), rho = rho0;
+  if (history) history[0] = rho0;
+  int k = 1;
+  while (rho > eps * rho0 && k < kmax) {
+    or_spmv(n, rowptr, col, val, p, q);
+    double pq = 0.0;
+    for (int64_t i = 0; i < n; i++) pq += p[i] * q[i];
+    double a = rr / pq;
+    for (int64_t i = 0; i < n; i++) { x[i] += a * p[i]; r[i] -= a * q[i]; }
+    double rr_new = 0.0;
+    for (int64_t i = 0; i < n; i++) rr_new += r[i] * r[i];
+    double bcoef = rr_new / rr;
+    for (int64_t i = 0; i < n; i++) p[i] = r[i] + bcoef * p[i];
+    rr = rr_new;
+    rho = sqrt(rr);
+    if (history) history[k] = rho;
+    if (xhist) memcpy(xhist + (int64_t)(k - 1) * n, x, sizeof(double) * (size_t)n);
+    k++;
+  }
+  res->iters = k - 1;
+  res->status = (rho <= eps * rho0) ? OR_OK : OR_ENOCONV;
+  res->relres = rho0 > 0.0 ? rho / rho0 : rho;
+  or_spmv(n, rowptr, col, val, x, q);
+  double nb = or_norm2(n, b);
+  for (int64_t i = 0; i < n; i++) q[i] = b[i] - q[i];
+  res->relres_true = nb > 0.0 ? or_norm2(n, q) / nb : or_norm2(n, q);
+  free(r); free(p); free(q);
+  return res->status;
+}
+
+/* The paper's memory count (Tables 6-9): number of stored basis vectors of a
+ * flexible run, t per iteration up to switch_it, t/2 afterwards; t * iters
+ * without a switch. */
+int64_t or_mem_flexible(int t, int iters, int switch_it) {
+  if (switch_it <= 0) return (int64_t)t * iters;
+  return (int64_t)t * switch_it + (int64_t)(t / 2) * (iters - switch_it);
+}

@@ -1,0 +1,482 @@
+"""Pins of the FP64 CPU oracle against things other than itself.
+
+Each test ties an oracle function to a library routine, a closed form, an
+invariant the paper states, brute force in extended precision, or a number
+printed in the paper.  All CPU-only.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle as O
+from paper_2305_19013_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ------------------------------------------------------------------ kernels
+
+
+def test_spmv_spmm_match_scipy():
+    p = W.random_spd_grid(12, 4, seed=1)
+    A = p.scipy()
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(p.n)
+    X = rng.standard_normal((p.n, 5))
+    assert rel(O.spmv(A, x), A @ x) < 1e-15
+    assert rel(O.spmm(A, X), A @ X) < 1e-15
+
+
+def test_split_reassembles_vector_and_halves_by_pairs():
+    """eq. (Tt): one nonzero per row, in the row's subdomain column, and
+    [T^t(v)] 1_t = v (the identity behind Theorem 2); [T^{t/2}(v)] merges the
+    column pairs {2j, 2j+1} (Section 4)."""
+    rng = np.random.default_rng(1)
+    t = 8
+    part = rng.integers(0, t, 50).astype(np.int32)
+    r = rng.standard_normal(50)
+    Wt = O.split(part, t, r)
+    assert np.array_equal(Wt.sum(axis=1), r)
+    assert np.all((Wt != 0).sum(axis=1) <= 1)
+    assert np.array_equal(Wt[np.arange(50), part], r)
+    Wh = O.split_half(part, t, r)
+    assert Wh.shape == (50, t // 2)
+    assert np.array_equal(Wh, Wt[:, 0::2] + Wt[:, 1::2])
+
+
+def test_block_products_match_numpy():
+    rng = np.random.default_rng(2)
+    X = rng.standard_normal((40, 3))
+    Y = rng.standard_normal((40, 4))
+    Cm = rng.standard_normal((3, 4))
+    assert rel(O.block_tdot(X, Y), X.T @ Y) < 1e-14
+    assert rel(O.block_sub(X, Cm, Y), Y - X @ Cm) < 1e-14
+    R = np.triu(rng.standard_normal((4, 4))) + 4 * np.eye(4)
+    assert rel(O.right_trsm(R, Y), Y @ np.linalg.inv(R)) < 1e-13
+
+
+def test_cholesky_matches_numpy_and_flags_breakdown():
+    rng = np.random.default_rng(3)
+    M = rng.standard_normal((6, 6))
+    G = M.T @ M + 0.1 * np.eye(6)
+    R, st = O.cholesky(G)
+    assert st == 0
+    assert rel(R, np.linalg.cholesky(G).T) < 1e-13
+    # a dependent column: column 3 = column 0 + column 1
+    M2 = M.copy()
+    M2[:, 3] = M2[:, 0] + M2[:, 1]
+    _, st = O.cholesky(M2.T @ M2)
+    assert st == 4
+    _, st = O.cholesky(-G)
+    assert st == 1
+
+
+def test_householder_qr_matches_numpy():
+    rng = np.random.default_rng(4)
+    Wm = rng.standard_normal((30, 5))
+    Q, R, st = O.householder_qr(Wm)
+    assert st == 0
+    assert np.all(np.diag(R) > 0)
+    assert np.abs(Q.T @ Q - np.eye(5)).max() < 1e-14
+    assert rel(Q @ R, Wm) < 1e-14
+    Qn, Rn = np.linalg.qr(Wm)
+    s = np.sign(np.diag(Rn))
+    assert rel(Q, Qn * s) < 1e-13
+    Wm[:, 2] = 2.0 * Wm[:, 0]
+    _, _, st = O.householder_qr(Wm)
+    assert st == 3
+
+
+def test_dense_spd_solve_matches_numpy():
+    p = W.random_spd_grid(6, 4, seed=5)
+    Ad = p.scipy().toarray()
+    x, st = O.dense_spd_solve(Ad, p.b)
+    assert st == 0
+    assert rel(x, np.linalg.solve(Ad, p.b)) < 1e-13
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_a_orthonormalize_gives_the_unique_factor(mode):
+    """W = W_k R with W_k^T A W_k = I and R upper triangular with positive
+    diagonal has one solution; compute it with scipy and compare."""
+    p = W.random_spd_grid(10, 4, seed=6)
+    A = p.scipy()
+    rng = np.random.default_rng(7)
+    Wm = rng.standard_normal((p.n, 4))
+    Wk, Vk, st = O.a_orthonormalize(A, Wm, mode)
+    assert st == 0
+    G = Wm.T @ (A @ Wm)
+    R = np.linalg.cholesky(G).T
+    ref = sla.solve_triangular(R, Wm.T, trans="T", lower=False).T
+    assert rel(Wk, ref) < 1e-12
+    assert rel(Vk, A @ ref) < 1e-12
+    assert np.abs(Wk.T @ (A @ Wk) - np.eye(4)).max() < 1e-13
+
+
+def test_a_orthonormalize_flags_dependent_block():
+    p = W.random_spd_grid(8, 4, seed=8)
+    rng = np.random.default_rng(9)
+    Wm = rng.standard_normal((p.n, 4))
+    Wm[:, 3] = Wm[:, 1]
+    for mode in (0, 1):
+        _, _, st = O.a_orthonormalize(p.scipy(), Wm, mode)
+        assert st == O.EBREAKDOWN
+
+
+def test_cgs2_is_the_a_orthogonal_projection():
+    """After CGS2 against an A-orthonormal set Q, W_out = (I - Q (AQ)^T) W,
+    the A-orthogonal projection onto the complement of span(Q)."""
+    p = W.random_spd_grid(10, 4, seed=10)
+    A = p.scipy()
+    rng = np.random.default_rng(11)
+    Qs, Vs = [], []
+    for w in (4, 4, 2):
+        Z = rng.standard_normal((p.n, w))
+        for q in Qs:  # dense A-orthogonalisation with numpy, twice
+            Z = Z - q @ (q.T @ (A @ Z))
+            Z = Z - q @ (q.T @ (A @ Z))
+        R = np.linalg.cholesky(Z.T @ (A @ Z)).T
+        Z = np.linalg.solve(R.T, Z.T).T
+        Qs.append(Z)
+        Vs.append(A @ Z)
+    Win = rng.standard_normal((p.n, 4))
+    Wout, st = O.cgs2(Qs, Vs, Win)
+    assert st == 0
+    Q = np.hstack(Qs)
+    ref = Win - Q @ ((A @ Q).T @ Win)
+    assert rel(Wout, ref) < 1e-12
+    assert np.abs((A @ Q).T @ Wout).max() < 1e-12 * np.abs(Win).max()
+
+
+# ------------------------------------------------------------------ solvers
+
+
+def test_t1_reduces_to_classical_cg_iterates():
+    """With t = 1, T^1(r) = r and SRE-CG2 builds the Krylov basis; its iterates
+    are those of CG.  Compare x_k with scipy's CG for the first 50 steps."""
+    p = W.poisson2d(32, 4, seed=12)
+    A = p.scipy()
+    part1 = np.zeros(p.n, dtype=np.int32)
+    r = O.ecg_solve(A, part1, 1, p.b, maxit=51, tol=0.0, keep_x=True)
+    xs = []
+    spla.cg(A, p.b, x0=np.zeros(p.n), rtol=1e-30, atol=0.0, maxiter=50, callback=lambda xk: xs.append(xk.copy()))
+    assert len(xs) == 50 and r.xhist.shape[0] == 50
+    for k in range(50):
+        assert rel(r.xhist[k], xs[k]) < 1e-10, k
+    cg = O.cg_solve(A, p.b, maxit=51, tol=0.0, keep_x=True)
+    for k in range(50):
+        assert rel(cg.xhist[k], xs[k]) < 1e-10, k
+
+
+def test_t1_iteration_count_equals_cg():
+    p = W.poisson2d(32, 4, seed=13)
+    A = p.scipy()
+    e = O.ecg_solve(A, np.zeros(p.n, dtype=np.int32), 1, p.b, maxit=2000)
+    c = O.cg_solve(A, p.b, maxit=2000)
+    assert e.status == 0 and c.status == 0
+    assert abs(e.iters - c.iters) <= 1
+
+
+mp = pytest.importorskip("mpmath")
+import brute as BF  # noqa: E402
+
+
+def _tiny(seed=14, side=8, t=4):
+    p = W.random_spd_grid(side, t, seed=seed)
+    mp.mp.dps = 40
+    Am = BF.to_mp_dense(p.scipy())
+    bm = BF.mp_vec(p.b)
+    return p, Am, bm
+
+
+@pytest.mark.parametrize("trunc", [0, 2])
+def test_sre_cg2_matches_brute_force_galerkin(trunc):
+    """x_k = x_0 + V (V^T A V)^{-1} V^T r_0 with V spanning the enlarged Krylov
+    space K_{k,t}(A, r_0) (Sections 1-2).  The truncated form with trunc = 2
+    (SRE-CG) must agree too: W_k = A W_{k-1} is A-orthogonal to W_i for
+    i <= k-3 in exact arithmetic (Section 2.1)."""
+    p, Am, bm = _tiny()
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=7, tol=0.0, trunc=trunc, keep_x=True)
+    assert r.iters == 6
+    x0 = mp.matrix(p.n, 1)
+    T0 = BF.split_cols(p.part, p.t, bm)
+    for k in range(1, 7):
+        xk = BF.to_np(BF.galerkin(Am, x0, bm, BF.krylov_block(Am, T0, k)))
+        assert rel(r.xhist[k - 1], xk) < 1e-10, k
+
+
+def test_flexible_matches_brute_force_recurrence():
+    """Flexibly SRE-CG2 (Algorithm 3) with the switch forced at the first
+    opportunity (a huge switchTol gives k_F = 1): compare every x_k with the
+    Galerkin iterate over the blocks Algorithm 3 generates, built in
+    extended precision.  After the switch W_k = A W_{k-1} multiplies the
+    A-orthonormalised block, so the space is the one this recurrence spans
+    (which differs from the formula of Section 4.1 by the projection terms)."""
+    p, Am, bm = _tiny(seed=15)
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=7, tol=0.0, switch_tol=1e30, keep_x=True)
+    assert r.switch_it == 1
+    xs = BF.flexible_sre_iterates(Am, bm, p.part, p.t, 1, 6)
+    for k in range(1, 7):
+        assert rel(r.xhist[k - 1], BF.to_np(xs[k - 1])) < 1e-10, k
+
+
+def test_flexible_late_switch_matches_brute_force():
+    """Switch after k_F = 3 (switchTol chosen between the residual drops)."""
+    p, Am, bm = _tiny(seed=16)
+    A = p.scipy()
+    base = O.ecg_solve(A, p.part, p.t, p.b, maxit=7, tol=0.0)
+    h = base.history
+    tol1 = np.abs(np.diff(h)) / h[0]  # tol1 after iterations 1..6
+    if not (tol1[2] < tol1[0] and tol1[2] < tol1[1]):
+        pytest.skip("residual drops not ordered for this seed")
+    st = 0.5 * (tol1[2] + min(tol1[0], tol1[1]))
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=7, tol=0.0, switch_tol=st, keep_x=True)
+    assert r.switch_it == 3
+    xs = BF.flexible_sre_iterates(Am, bm, p.part, p.t, 3, 6)
+    for k in range(1, 7):
+        assert rel(r.xhist[k - 1], BF.to_np(xs[k - 1])) < 1e-10, k
+
+
+def test_switch_block_lies_in_section41_space():
+    """At the switch iteration itself the space is exactly
+    K_{k_F,t}(A,r_0) + K_{1,t/2}(A,r_{k_F}) (Section 4.1)."""
+    p, Am, bm = _tiny(seed=15)
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=3, tol=0.0, switch_tol=1e30, keep_x=True)
+    x0 = mp.matrix(p.n, 1)
+    T0 = BF.split_cols(p.part, p.t, bm)
+    x1 = BF.galerkin(Am, x0, bm, T0)
+    T1 = BF.split_cols(p.part, p.t // 2, bm - Am * x1, half=True)
+    x2 = BF.galerkin(Am, x0, bm, T0 + T1)
+    assert rel(r.xhist[1], BF.to_np(x2)) < 1e-10
+
+
+@pytest.mark.parametrize("variant", ["modmsdo", "msdo"])
+def test_msdo_variants_match_brute_force_galerkin(variant):
+    """Modified MSDO-CG searches span{T^t(r_0), ..., T^t(r_{k-1})} (Section
+    2.2).  MSDO-CG's P_k = T^t(r_{k-1}) + P_{k-1} diag(beta_k) spans the same
+    space when every block is kept, so with full A-orthonormalisation both
+    give the same iterates in exact arithmetic."""
+    p, Am, bm = _tiny(seed=17)
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=6, tol=0.0, variant=variant, keep_x=True)
+    x0 = mp.matrix(p.n, 1)
+    cols = []
+    xk = x0
+    for k in range(1, 6):
+        cols = cols + BF.split_cols(p.part, p.t, bm - Am * xk)
+        xk = BF.galerkin(Am, x0, bm, cols)
+        assert rel(r.xhist[k - 1], BF.to_np(xk)) < 1e-10, k
+
+
+def test_finite_termination():
+    """n = 16, t = 4: K_{4,4} fills R^16, so full SRE-CG2 reaches the exact
+    solution in at most n/t = 4 iterations."""
+    p = W.random_spd_grid(4, 4, seed=18)
+    r = O.ecg_solve(p.scipy(), p.part, 4, p.b, maxit=10, tol=1e-13)
+    assert r.status == 0
+    assert r.iters <= 4
+    assert rel(r.x, p.x_star) < 1e-12
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [
+        dict(),
+        dict(trunc=2),
+        dict(switch_tol=1e-3),
+        dict(variant="msdo"),
+        dict(variant="modmsdo", trunc=3),
+        dict(ortho=1),
+    ],
+    ids=["full", "trunc2", "flex", "msdo", "modmsdo_t3", "acholqr"],
+)
+def test_converged_solution_matches_dense_solve(kw):
+    p = W.random_spd_grid(20, 8, seed=19)
+    A = p.scipy()
+    Ad = A.toarray()
+    x_ref, st = O.dense_spd_solve(Ad, p.b)
+    assert st == 0
+    assert rel(x_ref, np.linalg.solve(Ad, p.b)) < 1e-12
+    kappa = np.linalg.cond(Ad)
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=2000, **kw)
+    assert r.status == 0
+    assert r.relres <= 1e-8
+    assert r.relres_true <= 1e-7
+    assert rel(r.x, x_ref) <= kappa * 1e-8
+
+
+@pytest.mark.parametrize(
+    "kw",
+    [dict(), dict(trunc=2), dict(switch_tol=1e-4), dict(variant="msdo", trunc=2), dict(variant="modmsdo")],
+    ids=["full", "trunc2", "flex", "msdo_t2", "modmsdo"],
+)
+def test_a_norm_error_is_monotone(kw):
+    """Every step minimises phi over x_{k-1} + span(W_k) (Section 2.1), so the
+    A-norm of the error cannot grow, whatever the variant."""
+    p = W.random_spd_grid(16, 4, seed=20)
+    A = p.scipy()
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=60, keep_x=True, **kw)
+    errs = [np.sqrt((x - p.x_star) @ (A @ (x - p.x_star))) for x in r.xhist]
+    e0 = np.sqrt(p.x_star @ (A @ p.x_star))
+    prev = e0
+    for k, e in enumerate(errs):
+        assert e <= prev * (1 + 1e-10) + 1e-14 * e0, k
+        prev = e
+
+
+def test_basis_invariants_full_sre():
+    """Q_k^T A Q_k = I (Section 2.1) and r_k orthogonal to the enlarged
+    subspace (the orthogonality condition of Section 2)."""
+    p = W.random_spd_grid(16, 4, seed=21)
+    A = p.scipy()
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=31, tol=0.0, keep_x=True, keep_basis=True)
+    assert r.iters == 30
+    Q = np.hstack(r.basis)
+    G = Q.T @ (A @ Q)
+    assert np.abs(G - np.eye(Q.shape[1])).max() < 1e-10
+    for k in (5, 15, 30):
+        Qk = np.hstack(r.basis[:k])
+        rk = p.b - A @ r.xhist[k - 1]
+        assert np.linalg.norm(Qk.T @ rk) / (np.linalg.norm(rk) * np.linalg.norm(Qk)) < 1e-10
+
+
+def test_basis_invariants_truncated_window():
+    """Truncated runs keep A-orthonormality inside the window of trunc blocks."""
+    p = W.random_spd_grid(16, 4, seed=22)
+    A = p.scipy()
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=31, tol=0.0, trunc=3, keep_basis=True)
+    for k in range(len(r.basis)):
+        Wk = r.basis[k]
+        assert np.abs(Wk.T @ (A @ Wk) - np.eye(Wk.shape[1])).max() < 1e-10
+        for j in range(max(0, k - 3), k):
+            assert np.abs(Wk.T @ (A @ r.basis[j])).max() < 1e-10
+
+
+def test_recursive_residual_tracks_true_residual():
+    p = W.random_spd_grid(16, 4, seed=23)
+    A = p.scipy()
+    r = O.ecg_solve(A, p.part, p.t, p.b, maxit=40, tol=0.0, keep_x=True)
+    for k in range(1, r.iters + 1):
+        true = np.linalg.norm(p.b - A @ r.xhist[k - 1])
+        assert abs(r.history[k] - true) <= 1e-10 * r.history[0], k
+
+
+def test_krylov_space_inside_enlarged_space():
+    """Theorem 2: K_k(A, r_0) lies in K_{k,t}(A, r_0), the space SRE-CG2
+    builds."""
+    p = W.random_spd_grid(8, 4, seed=24)
+    A = p.scipy().toarray()
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=7, tol=0.0, keep_basis=True)
+    Qo, _ = np.linalg.qr(np.hstack(r.basis))
+    v = p.b.copy()
+    for j in range(6):
+        res = v - Qo @ (Qo.T @ v)
+        assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(v), j
+        v = A @ v
+
+
+def test_algorithm3_space_differs_from_section41_formula():
+    """Algorithm 3 takes W_k = A W_{k-1} with W_{k-1} already A-orthonormalised
+    against every earlier block.  Two iterations after the switch its iterate
+    is no longer the Galerkin iterate over K_{k_F,t}(A,r_0) +
+    K_{k-k_F,t/2}(A,r_{k_F}) (Section 4.1).  The Corollary's premise
+    r_{k_F} in K_{k_F+1}(A,r_0) holds for classical CG but not for the enlarged
+    residual (r_1 = r_0 - A W_1 alpha lies in the enlarged space), and A r_0
+    is already outside the space built at the switch.  The solver follows
+    Algorithm 3, the procedure behind the paper's Tables 6-9."""
+    p, Am, bm = _tiny(seed=15)
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=4, tol=0.0, switch_tol=1e30, keep_x=True, keep_basis=True)
+    x0 = mp.matrix(p.n, 1)
+    T0 = BF.split_cols(p.part, p.t, bm)
+    x1 = BF.galerkin(Am, x0, bm, T0)
+    T1 = BF.split_cols(p.part, p.t // 2, bm - Am * x1, half=True)
+    x3_sec41 = BF.to_np(BF.galerkin(Am, x0, bm, T0 + BF.krylov_block(Am, T1, 2)))
+    assert rel(r.xhist[2], x3_sec41) > 1e-6
+    A = p.scipy().toarray()
+    Qo, _ = np.linalg.qr(np.hstack(r.basis))
+    v = A @ p.b
+    Q2, _ = np.linalg.qr(np.hstack(r.basis[:2]))
+    assert np.linalg.norm(v - Q2 @ (Q2.T @ v)) > 1e-6 * np.linalg.norm(v)
+
+
+# ------------------------------------------------------------ bookkeeping
+
+
+def _mem_rows():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "paper_table6_table8_mem.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        m, t, tol, it, sit, mem = line.split()
+        rows.append((m, int(t), tol, int(it), int(sit), int(mem)))
+    return rows
+
+
+def test_mem_formula_reproduces_paper_tables():
+    rows = _mem_rows()
+    assert len(rows) == 96
+    for m, t, tol, it, sit, mem in rows:
+        assert O.mem_flexible(t, it, sit) == mem, (m, t, tol)
+
+
+@pytest.mark.parametrize("kw,t", [(dict(), 4), (dict(switch_tol=1e-3), 4), (dict(switch_tol=1e-5), 8)])
+def test_solver_mem_count_follows_paper_convention(kw, t):
+    p = W.random_spd_grid(16, t, seed=25)
+    r = O.ecg_solve(p.scipy(), p.part, t, p.b, maxit=500, **kw)
+    assert r.status == 0
+    assert r.mem_vectors == O.mem_flexible(t, r.iters, r.switch_it)
+
+
+def test_truncated_mem_is_trunc_plus_one_blocks():
+    p = W.random_spd_grid(16, 4, seed=26)
+    r = O.ecg_solve(p.scipy(), p.part, 4, p.b, maxit=500, trunc=2)
+    assert r.iters > 3
+    assert r.mem_vectors == 3 * 4
+
+
+# ---------------------------------------------------------- edge cases
+
+
+def test_status_codes():
+    p = W.random_spd_grid(8, 4, seed=27)
+    A = p.scipy()
+    bad = p.part.copy()
+    bad[0] = 4
+    assert O.ecg_solve(A, bad, 4, p.b).status == O.EINVAL
+    empty = np.zeros(p.n, dtype=np.int32)  # subdomains 1..3 empty
+    assert O.ecg_solve(A, empty, 4, p.b).status == O.EINVAL
+    odd = (p.part % 3).astype(np.int32)
+    assert O.ecg_solve(A, odd, 3, p.b, switch_tol=1e-3).status == O.EINVAL
+    neg = sp.csr_matrix(-A)
+    assert O.ecg_solve(neg, p.part, 4, p.b).status == O.ENOTSPD
+    r = O.ecg_solve(A, p.part, 4, p.b, maxit=3)
+    assert r.status == O.ENOCONV and r.iters == 2
+    r = O.ecg_solve(A, p.part, 4, p.b, maxit=1)
+    assert r.status == O.ENOCONV and r.iters == 0
+    r = O.ecg_solve(A, p.part, 4, np.zeros(p.n))
+    assert r.status == O.OK and r.iters == 0 and np.all(r.x == 0)
+
+
+def test_breakdown_on_empty_residual_subdomain():
+    """r_0 zero on a whole subdomain makes a zero column of T^t(r_0)."""
+    p = W.random_spd_grid(8, 4, seed=28)
+    b = p.b.copy()
+    b[p.part == 2] = 0.0
+    for ortho in (0, 1):
+        r = O.ecg_solve(p.scipy(), p.part, 4, b, ortho=ortho)
+        assert r.status == O.EBREAKDOWN and r.iters == 0
+
+
+def test_warm_start_is_honoured():
+    p = W.random_spd_grid(12, 4, seed=29)
+    A = p.scipy()
+    x0 = p.x_star + 1e-3 * np.random.default_rng(0).standard_normal(p.n)
+    r = O.ecg_solve(A, p.part, 4, p.b, x0=x0, maxit=500)
+    assert r.status == 0 and rel(r.x, p.x_star) < 1e-6
