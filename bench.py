@@ -1,0 +1,348 @@
+"""Benchmark of the GB300 enlarged CG path.
+
+One "step" is one ECG iteration (every row of the hot path: block
+generation, CGS2 against the window, Pre-CholQR A-orthonormalisation with
+the SpMM, the t x t Cholesky factorisations, and the x/r updates) on the
+1024 x 1024 heterogeneous-diffusion system with t = 16 (n = 1,048,576),
+SRE-CG (SRE-CG2 truncated to a window of 2 blocks) in FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
+replica of the system (weak scaling); the time is the maximum over ranks.
+
+value    iterations per second of the whole job, inputs resident in HBM,
+         CUDA events on the solver's stream around one ecg_solve call that
+         runs exactly K iterations (tol = 0, maxit = K + 1).
+e2e      the same metric through the C ABI with host buffers (b copied in,
+         x and the residual history copied out inside the timed call).
+roofline the kernel class with the largest share of the iteration, from a
+         second, profiled run of K iterations (CUDA events on the solver's
+         stream around every kernel class); FP64 FMA-bound, so its peak is
+         the FP64 issue rate.
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this build) on a 1/16 row sample of the same workload; see cpu_baseline.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ECG time-to-1e-8 residual & iterations/sec (n≈1M, t=16), HBM GB/s vs peak"
+UNIT = "iterations/s"
+WORKLOAD = "diffusion2d_1024_t16"
+# FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = (
+        "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(
+                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                    capture_output=True,
+                    text=True,
+                    timeout=5,
+                ).stdout.strip()
+                if out:
+                    self.rows.append([c.strip() for c in out.split(",")])
+            except Exception:
+                return
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        if self._thr:
+            self._thr.join(timeout=10)
+
+    def summary(self):
+        if not self.rows:
+            return None
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        return {
+            "sm_mhz": float(np.median(sm)) if sm else None,
+            "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons,
+            "samples": len(self.rows),
+        }
+
+
+def algorithmic_counts(n, nnz, t, trunc, K):
+    """FP64 flops per kernel class and bytes per iteration, summed over
+    iterations 1..K (the window holds min(k-1, trunc) blocks at iteration k).
+    Flops count every multiply-add the method's definition needs (2 flops);
+    symmetric Grams count their upper triangle."""
+    tri = t * (t + 1) // 2
+    fl = {"cgs_tdot": 0.0, "cgs_update": 0.0, "gram_e": 0.0, "spmm_gram": 0.0, "final": 0.0}
+    byts = 0.0
+    B = 8.0 * n * t
+    for k in range(1, K + 1):
+        m = min(k - 1, trunc)
+        fl["cgs_tdot"] += 2 * 2.0 * (m * t) * t * n
+        fl["cgs_update"] += 2 * 2.0 * (m * t) * t * n
+        fl["gram_e"] += 2.0 * tri * n
+        fl["spmm_gram"] += 2.0 * (nnz * t + 2 * tri * n + tri * n + t * n)
+        fl["final"] += 2.0 * (2 * tri * n + 2 * t * n)
+        passes = 2 * (2 * m + 3) if m > 0 else 0
+        byts += (2 + passes + 1 + 2 + 4) * B + 12.0 * nnz + 4.0 * (n + 1) + 40.0 * n
+    return fl, byts
+
+
+def run_oracle_sample(K, W, trunc):
+    """The FP64 CPU oracle (single thread) on a 1/16 row sample of the
+    workload: the 256 x 256 version of the same coefficient layout (16 x 16
+    tiles of log-uniform kappa, t = 16, same seed).  Its work per iteration is
+    linear in n, so iterations/s scale by 256^2 / 1024^2 to the full size."""
+    import oracle as O
+    from paper_2305_19013_gb300 import workloads as Wk
+
+    p = Wk.blocky_diffusion2d(256, 16, blocks=16, seed=2001)
+    A = p.scipy()
+    if W > 0:
+        O.ecg_solve(A, p.part, 16, p.b, tol=0.0, maxit=W + 1, trunc=trunc)
+    t0 = time.perf_counter()
+    r = O.ecg_solve(A, p.part, 16, p.b, tol=0.0, maxit=K + 1, trunc=trunc)
+    dt = time.perf_counter() - t0
+    scale = p.n / 1048576.0
+    return {
+        "value": (r.iters / dt) * scale,
+        "unit": UNIT,
+        "cores": 1,
+        "kind": "oracle",
+        "sample": f"{r.iters} iterations of SRE-CG (trunc={trunc}) on the 256x256 version of the workload "
+        f"(n={p.n}, 1/16 of the rows), {dt:.1f} s single-threaded; iterations/s scaled by n_sample/n_full",
+        "seconds": dt,
+    }
+
+
+def reference_arm(args, rank):
+    if rank != 0:
+        return
+    cb = run_oracle_sample(args.steps, args.warmup, args.trunc)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": cb["value"],
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1000.0 / cb["value"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "method": f"SRE-CG2 trunc={args.trunc}", "sampled_rows": "1/16"},
+        "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
+        "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--trunc", type=int, default=2)
+    ap.add_argument("--ortho", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-tol", action="store_true", help="also solve to 1e-8 and report the time")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+
+    from paper_2305_19013_gb300 import ecg
+    from paper_2305_19013_gb300 import workloads as Wk
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    K, Wm = args.steps, args.warmup
+    assert Wm >= 3, "at least 3 warm-up steps"
+    p = Wk.blocky_diffusion2d(1024, 16, blocks=16, seed=2001 + rank)
+    stream = torch.cuda.current_stream()
+    solver = ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, stream=stream.cuda_stream)
+    b_dev = torch.from_numpy(p.b).cuda()
+    x_dev = torch.empty_like(b_dev)
+
+    # warm-up: W iterations
+    solver.solve(b_dev, tol=0.0, maxit=Wm + 1, x_out=x_dev)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- timed region: exactly K iterations, inputs resident in HBM
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = solver.solve(b_dev, tol=0.0, maxit=K + 1, x_out=x_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    assert res.iters == K, res.iters
+    launches_per_iter = 13 if args.ortho == 0 else 11  # kernels of one iteration
+    t_all = torch.tensor([ms], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
+    ms_max = float(t_all.item())
+    value = world * K / (ms_max / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers
+    b_host = p.b.copy()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    res_h = solver.solve(b_host, tol=0.0, maxit=K + 1)
+    t_e2e = time.perf_counter() - t0
+    t_e = torch.tensor([t_e2e], device="cuda")
+    if dist is not None:
+        dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
+    e2e_value = world * K / float(t_e.item())
+
+    # ---- per-kernel-class profile (same K iterations, events on the stream)
+    solver.profile(True)
+    solver.solve(b_dev, tol=0.0, maxit=K + 1, x_out=x_dev)
+    prof = solver.profile_read()
+    solver.profile(False)
+    fl, bytes_total = algorithmic_counts(p.n, p.nnz, 16, args.trunc, K)
+    tot_ms = sum(v[0] for v in prof.values())
+    dom = max((k for k in prof if k in fl), key=lambda k: prof[k][0])
+    dom_ms, dom_launch = prof[dom]
+    achieved = fl[dom] / (dom_ms / 1000.0) / 1e12
+    pk = peaks()
+    roofline = {
+        "bound": "alu",
+        "kernel": dom,
+        "achieved": achieved,
+        "peak": FP64_PEAK_TFLOPS,
+        "unit": "TFLOP/s",
+        "frac": achieved / FP64_PEAK_TFLOPS,
+        "traffic": None,
+        "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+        "launches": dom_launch,
+        "share": dom_ms / tot_ms,
+    }
+    total_fl = sum(fl.values())
+    iter_tflops = total_fl / (ms / 1000.0) / 1e12
+    hbm = pk.get("hbm_gbs", 6686.1)
+    hbm_gbs = bytes_total / (ms / 1000.0) / 1e9
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": Wm,
+        "ms_per_step": ms_max / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD,
+            "n": p.n,
+            "nnz": p.nnz,
+            "t": 16,
+            "method": f"SRE-CG2 truncated to {args.trunc} blocks (SRE-CG)",
+            "ortho": "Pre-CholQR" if args.ortho == 0 else "A-CholQR",
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "no flush: the iteration streams ~3 GB of blocks, far above the 129 MB L2",
+        },
+        "gpu_launches": K * launches_per_iter + 3,  # + residual, start, final residual
+        "e2e": {
+            "value": e2e_value,
+            "unit": UNIT,
+            "h2d_bytes_per_step": 8 * p.n / K,
+            "d2h_bytes_per_step": (8 * p.n + 8 * (K + 1)) / K,
+        },
+        "roofline": roofline,
+        "iteration": {
+            "fp64_tflops": iter_tflops,
+            "fp64_frac": iter_tflops / FP64_PEAK_TFLOPS,
+            "hbm_gbs": hbm_gbs,
+            "hbm_frac_of_measured": hbm_gbs / hbm,
+            "profile_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+        },
+        "clocks": clk.summary(),
+    }
+    if args.time_to_tol:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = solver.solve(b_dev, tol=1e-8, maxit=200000, x_out=x_dev)
+        torch.cuda.synchronize()
+        line["time_to_tol"] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status, "relres_true": r.relres_true}
+    solver.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = run_oracle_sample(8, 1, args.trunc)
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

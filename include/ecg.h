@@ -1,0 +1,185 @@
+/*
+ * ecg.h -- C ABI of the GB300 (sm_103a) enlarged Conjugate Gradient library.
+ *
+ * Method: S. Moufawad, "Flexibly Enlarged Conjugate Gradient methods"
+ * (arXiv 2305.19013).  The library solves A x = b for a sparse symmetric
+ * positive definite A with the enlarged CG methods of its Sections 2-4:
+ * SRE-CG2 (Algorithm 1), MSDO-CG (Algorithm 2), modified MSDO-CG
+ * (Section 2.2), their truncated forms (Section 3; SRE-CG is SRE-CG2 with
+ * trunc = 2) and the flexibly enlarged forms that halve the block width once
+ * (Algorithms 3 and 4).  Every iteration runs on the GPU: the domain
+ * splitting T^t(r) (eq. (Tt)), the product A W, CGS2 A-orthogonalisation
+ * against the stored blocks, A-orthonormalisation (Pre-CholQR or A-CholQR)
+ * with a t x t Cholesky factorisation in FP64, and the updates
+ * x += W alpha, r -= A W alpha.  There is no CPU fallback: without a CUDA
+ * device every call returns ECG_ECUDA.
+ *
+ * Conventions for every function below:
+ *   - Blocks of w vectors of length n are row-major n x w arrays of double
+ *     (entry (i, j) at [i*w + j]); small w x w matrices are row-major too.
+ *   - Return value: ECG_OK (0) on success, ECG_ENOCONV (> 0) when the
+ *     iteration limit was reached (the result is still valid), or a negative
+ *     error code.  No C++ exception crosses this interface.
+ *   - Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef ECG_H
+#define ECG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ECG_OK 0
+#define ECG_ENOCONV 1        /* k_max reached before the tolerance */
+#define ECG_EINVAL (-1)      /* bad argument (sizes, partition, options) */
+#define ECG_ENOMEM (-2)      /* a device or host allocation failed */
+#define ECG_ECUDA (-3)       /* a CUDA runtime call failed, or no device */
+#define ECG_EBREAKDOWN (-4)  /* a block became numerically rank deficient */
+#define ECG_ENOTSPD (-5)     /* a diagonal entry of A is not positive */
+
+/* Generator of the new block at iteration k (Sections 2-3). */
+#define ECG_SRE 0     /* SRE-CG2, Algorithm 1: W_k = A W_{k-1} */
+#define ECG_MSDO 1    /* MSDO-CG, Algorithm 2: P_k = T(r_{k-1}) + P_{k-1} diag(beta_k) */
+#define ECG_MODMSDO 2 /* modified MSDO-CG, Section 2.2: W_k = T(r_{k-1}) */
+
+/* Self A-orthonormalisation of the block (Section 2.1, Section 5). */
+#define ECG_PRE_CHOLQR 0 /* Euclidean CholQR, then A-CholQR (the paper's choice in Section 5) */
+#define ECG_A_CHOLQR 1   /* A-CholQR alone */
+
+typedef struct ecg_ctx ecg_ctx; /* opaque */
+
+/* Sparse SPD matrix in CSR form, both triangles stored. */
+typedef struct {
+  int64_t n;             /* rows = columns */
+  int64_t nnz;           /* stored entries, rowptr[n] */
+  const int64_t* rowptr; /* n + 1 offsets, rowptr[0] = 0 */
+  const int32_t* col;    /* nnz column indices in [0, n) */
+  const double* val;     /* nnz values */
+  int on_device;         /* 1: the three arrays are device pointers; 0: host */
+} ecg_csr;
+
+typedef struct {
+  int variant;       /* ECG_SRE, ECG_MSDO or ECG_MODMSDO (default ECG_SRE) */
+  int trunc;         /* 0: A-orthogonalise against every stored block (the
+                        full method, trunc = k_max); >= 1: against the last
+                        trunc blocks only (Section 3) */
+  double switch_tol; /* > 0: flexible switch t -> t/2 once
+                        |rho_k - rho_{k-1}| / rho_0 < switch_tol (Section 4.2);
+                        requires even t.  0: never switch */
+  int ortho;         /* ECG_PRE_CHOLQR (default) or ECG_A_CHOLQR */
+  int check_every;   /* iterations issued between two host polls of the
+                        device-side stop flag (default 16; >= 1) */
+  int use_graph;     /* 1: replay a captured CUDA graph of check_every
+                        iterations when the window size is fixed (default 1) */
+  void* stream;      /* cudaStream_t for all work; NULL: a stream the
+                        context creates */
+} ecg_opts;
+
+typedef struct {
+  int iters;           /* iterations run (k - 1 at exit of the loop) */
+  int switch_it;       /* last iteration with t vectors before the switch
+                          (k_F of Section 4.1); 0 if no switch */
+  int status;          /* same value as the return code */
+  int64_t mem_vectors; /* largest number of stored basis vectors, the "mem"
+                          of the paper's Tables 4-9 */
+  double relres;       /* rho_k / rho_0, recursively updated residual */
+  double relres_true;  /* ||b - A x|| / ||b||, recomputed at exit */
+  double device_ms;    /* device time of the solve (CUDA events) */
+  const double* history; /* rho_0 .. rho_iters (iters + 1 values), host
+                            memory owned by the context, valid until the
+                            next ecg_solve or ecg_destroy */
+} ecg_result;
+
+/* Fill *opts with the defaults listed above. */
+void ecg_default_opts(ecg_opts* opts);
+
+/* Create a solver context for A with the subdomain map `partition` (n
+ * entries, values in [0, t), every subdomain non-empty; the delta_i of
+ * Section 1).  A and partition are copied (host or device pointers per
+ * A->on_device); the caller may free them afterwards.  1 <= t <= 64.
+ * Returns ECG_EINVAL for bad sizes, partition values, empty subdomains,
+ * unsupported t, or switch_tol > 0 with odd t; ECG_ENOTSPD when a diagonal
+ * entry is not positive; ECG_ENOMEM / ECG_ECUDA on device failures.  On
+ * error *out is NULL. */
+int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts* opts,
+               ecg_ctx** out);
+
+/* Solve A x = b (Algorithms 1-4): stop when rho_k <= tol * rho_0 or when
+ * k reaches maxit (the paper's k_max: at most maxit - 1 iterations run).
+ * b, x0 and x_out are n doubles each, all host or all device pointers (the
+ * location is detected; host arrays are copied in and out inside the call).
+ * x0 may be NULL (x0 = 0).  res may be NULL.  Returns ECG_OK,
+ * ECG_ENOCONV (x_out holds the last iterate), ECG_EBREAKDOWN (x_out holds
+ * the last iterate before the rank-deficient block), ECG_EINVAL, ECG_ENOMEM
+ * (the stored blocks do not fit: use trunc) or ECG_ECUDA. */
+int ecg_solve(ecg_ctx* ctx, const double* b, const double* x0, double* x_out, double tol,
+              int maxit, ecg_result* res);
+
+/* Release every resource of ctx (NULL is accepted). */
+void ecg_destroy(ecg_ctx* ctx);
+
+/* Static, human-readable text for a status code. */
+const char* ecg_strerror(int code);
+
+/* Per-kernel-class device timing.  ecg_profile_enable(ctx, 1) resets the
+ * counters and, until disabled, brackets every kernel class of each
+ * iteration with CUDA events on the context's stream (graph replay is off
+ * while profiling).  ecg_profile_read fills the name, total milliseconds and
+ * launch count of class `cls` and returns the number of classes (also when
+ * cls is out of range, so cls = -1 queries the count). */
+int ecg_profile_enable(ecg_ctx* ctx, int on);
+int ecg_profile_read(ecg_ctx* ctx, int cls, const char** name, double* ms, long long* launches);
+
+/* ----------------------------------------------------------------------
+ * Step-level entry points.  Each runs one step of the iteration with the
+ * same kernels ecg_solve uses, on the context's matrix, partition and
+ * stream, and returns after the step has finished on the device.  All array
+ * arguments are device pointers; arrays of block pointers are host arrays
+ * holding device pointers.
+ * ---------------------------------------------------------------------- */
+
+/* W = [T^t(r)] (half = 0; W is n x t) or [T^{t/2}(r)] over the merged pairs
+ * {2j, 2j+1} (half = 1; W is n x t/2): eq. (Tt) and Section 4. */
+int ecg_op_split(ecg_ctx* ctx, const double* r, double* W, int half);
+
+/* Y = A X for an n x w block, 1 <= w <= 64 (Algorithm 1 line 6). */
+int ecg_op_spmm(ecg_ctx* ctx, const double* X, double* Y, int w);
+
+/* C = [X_0 ... X_{m-1}]^T Y: the block inner products of Sections 2-3
+ * (CGS coefficients (A Q)^T W, beta = V^T r, W^T r).  X_j is n x wx[j]
+ * with 1 <= wx[j] <= 128, Y is n x wy with wy in {1,2,4,8,16,32,64}; C is
+ * (sum wx) x wy.  1 <= m <= 1024. */
+int ecg_op_tdot(ecg_ctx* ctx, int m, const double* const* X, const int* wx, const double* Y,
+                int wy, double* C);
+
+/* Two passes of block classical Gram-Schmidt in the A-inner product of the
+ * n x w block W against m A-orthonormal blocks Q_j (n x wq[j]) with
+ * V_j = A Q_j: each pass computes C = V^T W, then W -= Q C (Section 2.1,
+ * "CGS2").  W is updated in place. */
+int ecg_op_cgs2(ecg_ctx* ctx, int m, const double* const* Q, const double* const* V,
+                const int* wq, double* W, int w);
+
+/* A-orthonormalise the n x w block W in place with the context's ortho mode
+ * and write V = A W_k; W_k^T A W_k = I (Algorithm 1 lines 4 and 8).  Returns
+ * ECG_EBREAKDOWN for a numerically dependent block. */
+int ecg_op_a_orthonormalize(ecg_ctx* ctx, double* W, double* V, int w);
+
+/* One update of Algorithm 1 lines 9-12 given a raw block W (n x w, already
+ * A-orthogonal to the stored blocks): A-orthonormalise it (W and V = A W_k
+ * written back), alpha = W_k^T r, x += W_k alpha, r -= V alpha, and
+ * *rho = ||r||.  rho is a host pointer. */
+int ecg_op_block_update(ecg_ctx* ctx, double* W, double* V, int w, double* x, double* r,
+                        double* rho);
+
+/* MSDO-CG generator (Algorithm 2 lines 6-7): P = [T(r)] + P_prev diag(beta),
+ * beta = -V_prev^T r, with T = T^t when w == t and T^{t/2} when w == t/2. */
+int ecg_op_msdo_generate(ecg_ctx* ctx, const double* r, const double* P_prev,
+                         const double* V_prev, int w, double* P);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECG_H */

@@ -98,11 +98,13 @@ void or_split_half(int64_t n, const int32_t* part, int t, const double* r, doubl
 /* C = X^T Y (wx x wy) for n x wx X and n x wy Y: the block inner products
  * W^T r, P^T A P and (AQ)^T W of Sections 2-4. */
 void or_block_tdot(int64_t n, int wx, const double* X, int wy, const double* Y, double* C) {
-  for (int a = 0; a < wx; a++)
-    for (int b = 0; b < wy; b++) {
-      double s = 0.0;
-      for (int64_t i = 0; i < n; i++) s += X[i * wx + a] * Y[i * wy + b];
-      C[a * wy + b] = s;
+  /* Rows in the outer loop; every entry still sums its n products in row
+   * order, exactly as the plain triple loop with rows innermost would. */
+  for (int a = 0; a < wx * wy; a++) C[a] = 0.0;
+  for (int64_t i = 0; i < n; i++)
+    for (int a = 0; a < wx; a++) {
+      const double xa = X[i * wx + a];
+      for (int b = 0; b < wy; b++) C[a * wy + b] += xa * Y[i * wy + b];
     }
 }
 

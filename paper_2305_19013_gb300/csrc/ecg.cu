@@ -1,0 +1,980 @@
+// ecg.cu -- host side of libecg: the C ABI of include/ecg.h, device memory,
+// and the iteration driver of the enlarged CG methods (S. Moufawad,
+// "Flexibly Enlarged Conjugate Gradient methods", arXiv 2305.19013,
+// Algorithms 1-4).
+//
+// The driver never waits on the device inside the iteration loop: it issues
+// `check_every` iterations of the kernel chain of ecg_kernels.cuh, queues an
+// asynchronous copy of the device state into pinned host memory, issues the
+// next group, and only then reads the state of the previous group.  The
+// device decides when to stop (rho_k <= eps rho_0 or k = k_max, breakdown)
+// and when to switch to t/2 vectors; kernels issued after either event
+// return at once.  With a truncated window the group of iterations is
+// captured once as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ecg.h"
+#include "ecg_kernels.cuh"
+
+using namespace ecg;
+
+namespace {
+
+constexpr int kWidths[] = {1, 2, 4, 8, 16, 32, 64};
+
+int width_index(int w) {
+  for (int i = 0; i < 7; i++)
+    if (kWidths[i] == w) return i;
+  return -1;
+}
+
+struct Prof {
+  // per kernel class: total device ms and launches, accumulated while
+  // profiling is on
+  double ms[16];
+  long long launches[16];
+};
+
+const char* kProfNames[] = {"generate", "cgs_tdot", "cgs_update", "gram_e",   "small_e",
+                            "spmm_gram", "small_a", "final",      "finish",   "setup"};
+constexpr int kProfClasses = 10;
+
+}  // namespace
+
+struct ecg_ctx {
+  int n = 0;
+  int64_t nnz = 0;
+  int t = 0;
+  ecg_opts opts;
+  int dev = 0;
+  int num_sms = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int* d_rowptr = nullptr;
+  int* d_col = nullptr;
+  double* d_val = nullptr;
+  int* d_pmap = nullptr;  // subdomain of each row
+  double *d_X = nullptr, *d_Y = nullptr, *d_x = nullptr, *d_r = nullptr, *d_b = nullptr;
+  double *d_sx = nullptr, *d_sr = nullptr;  // scratch x, r for step-level calls
+  DevState* d_st = nullptr;
+  DevState* d_opst = nullptr;
+  BlockDesc* d_desc = nullptr;
+  int desc_cap = 0;
+  BlockDesc* d_opdesc = nullptr;
+  int opdesc_cap = 0;
+  double *d_slotW = nullptr, *d_slotV = nullptr;
+  int slot_cap = 0;
+  double* d_C = nullptr;
+  size_t C_cap = 0;
+  double* d_partial = nullptr;  // per-CTA partial sums
+  size_t part_cap = 0;
+  double* d_small = nullptr;
+  double* d_hist = nullptr;
+  int hist_cap = 0;
+  double *d_rho_part = nullptr, *d_beta_part = nullptr, *d_bb_part = nullptr;
+  int gx = 1;
+  std::vector<double> h_hist;
+  DevState* h_flags = nullptr;  // pinned, 2 entries
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraphExec_t gexec[7] = {};
+  int graph_iters[7] = {};
+  bool profiling = false;
+  std::vector<cudaEvent_t> pev;  // profiling event pool
+  size_t pev_used = 0;
+  std::vector<int> pev_class;
+  Prof prof;
+};
+
+namespace {
+
+#define CK(call)                                                  \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) {                                      \
+      last_cuda_error() = e_;                                     \
+      return ECG_ECUDA;                                           \
+    }                                                             \
+  } while (0)
+
+cudaError_t& last_cuda_error() {
+  static thread_local cudaError_t e = cudaSuccess;
+  return e;
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return (e == cudaErrorMemoryAllocation) ? ECG_ENOMEM : ECG_ECUDA;
+  }
+  return ECG_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <int W>
+constexpr size_t smem_tdot() {
+  return sizeof(double) * (Tile<W>::R * kChunk + Tile<W>::R * W);
+}
+template <int W>
+constexpr size_t smem_update() {
+  return sizeof(double) * (Tile<W>::R * kChunk + kChunk * W);
+}
+template <int W>
+constexpr size_t smem_spmm() {
+  return sizeof(double) * (4 * Tile<W>::R * W + W * W + Tile<W>::R);
+}
+template <int W>
+constexpr size_t smem_final() {
+  return sizeof(double) * (5 * Tile<W>::R * W + W * W + W + Tile<W>::R + kThreads);
+}
+template <int W>
+constexpr size_t smem_small() {
+  return sizeof(double) * (3 * W * W + 2 * W);
+}
+
+template <int W>
+int set_smem_attrs() {
+  CK(cudaFuncSetAttribute(k_tdot_window<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tdot<W>()));
+  CK(cudaFuncSetAttribute(k_update<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_update<W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<W, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<W>()));
+  CK(cudaFuncSetAttribute(k_final<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<W>()));
+  CK(cudaFuncSetAttribute(k_small_e<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small<W>()));
+  CK(cudaFuncSetAttribute(k_small_a<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_small<W>()));
+  CK(cudaFuncSetAttribute(k_small_a<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_small<W>()));
+  return ECG_OK;
+}
+
+int set_all_smem_attrs() {
+  int rc = ECG_OK;
+  if ((rc = set_smem_attrs<1>())) return rc;
+  if ((rc = set_smem_attrs<2>())) return rc;
+  if ((rc = set_smem_attrs<4>())) return rc;
+  if ((rc = set_smem_attrs<8>())) return rc;
+  if ((rc = set_smem_attrs<16>())) return rc;
+  if ((rc = set_smem_attrs<32>())) return rc;
+  return set_smem_attrs<64>();
+}
+
+KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc) {
+  KP P;
+  P.n = c->n;
+  P.t = c->t;
+  P.rowptr = c->d_rowptr;
+  P.col = c->d_col;
+  P.val = c->d_val;
+  P.part = c->d_pmap;
+  P.X = c->d_X;
+  P.Y = c->d_Y;
+  P.x = c->d_x;
+  P.r = c->d_r;
+  P.b = c->d_b;
+  P.st = st;
+  P.desc = desc;
+  P.slotW = c->d_slotW;
+  P.slotV = c->d_slotV;
+  P.slot_stride = (long long)c->n * c->t;
+  P.C = c->d_C;
+  P.part_buf = c->d_partial;
+  P.small = c->d_small;
+  P.history = c->d_hist;
+  P.rho_part = c->d_rho_part;
+  P.beta_part = c->d_beta_part;
+  P.want_beta = (c->opts.variant == ECG_MSDO) ? 1 : 0;
+  return P;
+}
+
+// Row-CTAs for a window product with gy column chunks.
+int window_gx(const ecg_ctx* c, int gy) {
+  int target = 4 * c->num_sms;
+  int g = (target + gy - 1) / gy;
+  return std::max(1, std::min(c->gx, g));
+}
+
+void invalidate_graphs(ecg_ctx* c) {
+  for (auto& g : c->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int ensure_part(ecg_ctx* c, size_t doubles) {
+  if (doubles <= c->part_cap) return ECG_OK;
+  dfree(c->d_partial);
+  c->part_cap = 0;
+  int rc = dalloc(&c->d_partial, doubles);
+  if (rc) return rc;
+  c->part_cap = doubles;
+  for (auto& g : c->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return ECG_OK;
+}
+
+int ensure_C(ecg_ctx* c, size_t doubles) {
+  if (doubles <= c->C_cap) return ECG_OK;
+  dfree(c->d_C);
+  c->C_cap = 0;
+  int rc = dalloc(&c->d_C, doubles);
+  if (rc) return rc;
+  c->C_cap = doubles;
+  for (auto& g : c->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return ECG_OK;
+}
+
+void prof_mark(ecg_ctx* c, int cls) {
+  if (!c->profiling) return;
+  if (c->pev_used >= c->pev.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    c->pev.push_back(e);
+    c->pev_class.push_back(-1);
+  }
+  cudaEventRecord(c->pev[c->pev_used], c->stream);
+  c->pev_class[c->pev_used] = cls;
+  c->pev_used++;
+}
+
+void prof_collect(ecg_ctx* c) {
+  if (!c->profiling || c->pev_used < 2) {
+    c->pev_used = 0;
+    return;
+  }
+  cudaEventSynchronize(c->pev[c->pev_used - 1]);
+  for (size_t i = 1; i < c->pev_used; i++) {
+    int cls = c->pev_class[i];
+    if (cls < 0) continue;  // -1 marks a start point
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->pev[i - 1], c->pev[i]) == cudaSuccess) {
+      c->prof.ms[cls] += ms;
+      c->prof.launches[cls] += 1;
+    }
+  }
+  c->pev_used = 0;
+}
+
+// One iteration of the kernel chain for block width W.
+template <int W>
+int enqueue_iteration(ecg_ctx* c, int gy) {
+  cudaStream_t s = c->stream;
+  KP P = make_kp(c, c->d_st, c->d_desc);
+  const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
+  const int gxw = window_gx(c, gy);
+  const long long tot = (long long)c->n * W;
+  const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
+  prof_mark(c, -1);
+  k_generate<W><<<ggen, kThreads, 0, s>>>(P, W);
+  prof_mark(c, 0);
+  for (int pass = 0; pass < 2; pass++) {
+    k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), s>>>(P, W, c->d_X);
+    k_reduce_C<W><<<dim3((kChunk * W + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
+    prof_mark(c, 1);
+    k_update<W><<<c->gx, kThreads, smem_update<W>(), s>>>(P, W, c->d_X, c->d_C);
+    prof_mark(c, 2);
+  }
+  if (pre) {
+    k_gram_self<W><<<c->gx, kThreads, 0, s>>>(P, W, c->d_X);
+    prof_mark(c, 3);
+    k_small_e<W><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+    prof_mark(c, 4);
+    k_spmm_gram<W, true, true><<<c->gx, kThreads, smem_spmm<W>(), s>>>(P, W, c->d_X, c->d_Y);
+    prof_mark(c, 5);
+    k_small_a<W, true><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+  } else {
+    k_spmm_gram<W, true, false><<<c->gx, kThreads, smem_spmm<W>(), s>>>(P, W, c->d_X, c->d_Y);
+    prof_mark(c, 5);
+    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+  }
+  prof_mark(c, 6);
+  k_final<W><<<c->gx, kThreads, smem_final<W>(), s>>>(P, W, c->d_X, c->d_Y, nullptr, nullptr, c->d_x, c->d_r);
+  prof_mark(c, 7);
+  k_finish<<<1, kThreads, 0, s>>>(P, W, c->gx);
+  prof_mark(c, 8);
+  CK(cudaGetLastError());
+  return ECG_OK;
+}
+
+int enqueue_iteration_w(ecg_ctx* c, int W, int gy) {
+  switch (W) {
+    case 1: return enqueue_iteration<1>(c, gy);
+    case 2: return enqueue_iteration<2>(c, gy);
+    case 4: return enqueue_iteration<4>(c, gy);
+    case 8: return enqueue_iteration<8>(c, gy);
+    case 16: return enqueue_iteration<16>(c, gy);
+    case 32: return enqueue_iteration<32>(c, gy);
+    case 64: return enqueue_iteration<64>(c, gy);
+  }
+  return ECG_EINVAL;
+}
+
+// Column chunks of the window for an iteration index bounded by khost.
+int window_chunks(const ecg_ctx* c, int cap, int khost) {
+  long long blocks = std::min<long long>(cap, std::max(0, khost - 1));
+  long long cols = blocks * c->t;
+  return (int)std::max<long long>(1, (cols + kChunk - 1) / kChunk);
+}
+
+// Issue `iters` iterations of width W, through a captured graph when the
+// window size is fixed.
+int enqueue_group(ecg_ctx* c, int W, int iters, int cap, int khost) {
+  const bool fixed = (c->opts.trunc > 0);
+  const int gy = window_chunks(c, cap, fixed ? cap + 1 : khost + iters);
+  if (c->opts.use_graph && fixed && !c->profiling && iters == c->opts.check_every) {
+    int wi = width_index(W);
+    if (!c->gexec[wi] || c->graph_iters[wi] != iters) {
+      if (c->gexec[wi]) cudaGraphExecDestroy(c->gexec[wi]);
+      c->gexec[wi] = nullptr;
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      int rc = ECG_OK;
+      for (int i = 0; i < iters && rc == ECG_OK; i++) rc = enqueue_iteration_w(c, W, gy);
+      cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+      if (rc) return rc;
+      CK(e);
+      e = cudaGraphInstantiate(&c->gexec[wi], g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      c->graph_iters[wi] = iters;
+    }
+    CK(cudaGraphLaunch(c->gexec[wi], c->stream));
+    return ECG_OK;
+  }
+  for (int i = 0; i < iters; i++) {
+    int rc = enqueue_iteration_w(c, W, gy);
+    if (rc) return rc;
+  }
+  return ECG_OK;
+}
+
+int validate_opts(const ecg_opts* o, int t) {
+  if (o->variant < 0 || o->variant > 2) return ECG_EINVAL;
+  if (o->trunc < 0) return ECG_EINVAL;
+  if (o->ortho < 0 || o->ortho > 1) return ECG_EINVAL;
+  if (!(o->switch_tol >= 0.0)) return ECG_EINVAL;
+  if (o->switch_tol > 0.0 && (t % 2 != 0)) return ECG_EINVAL;
+  if (o->check_every < 1) return ECG_EINVAL;
+  return ECG_OK;
+}
+
+// Launch helpers for the step-level entry points (width dispatch).
+template <int W>
+struct Ops {
+  static void generate(ecg_ctx* c, KP P) {
+    long long tot = (long long)c->n * W;
+    int g = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
+    k_generate<W><<<g, kThreads, 0, c->stream>>>(P, W);
+  }
+  static void spmm(ecg_ctx* c, KP P, const double* X, double* Y) {
+    k_spmm_gram<W, false, false><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, X, Y);
+  }
+  static void tdot(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) {
+    int gxw = window_gx(c, gy);
+    k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), c->stream>>>(P, gw, B);
+    k_reduce_C<W><<<dim3((kChunk * W + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw, Cout);
+  }
+  static void update(ecg_ctx* c, KP P, double* X, const double* Cin) {
+    k_update<W><<<c->gx, kThreads, smem_update<W>(), c->stream>>>(P, W, X, Cin);
+  }
+  static void orth(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) {
+    const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
+    if (pre) {
+      k_gram_self<W><<<c->gx, kThreads, 0, c->stream>>>(P, W, Wio);
+      k_small_e<W><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
+      k_spmm_gram<W, true, true><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, Wio, c->d_Y);
+      k_small_a<W, true><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
+    } else {
+      k_spmm_gram<W, true, false><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, Wio, c->d_Y);
+      k_small_a<W, false><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
+    }
+    k_final<W><<<c->gx, kThreads, smem_final<W>(), c->stream>>>(P, W, Wio, c->d_Y, Wio, V, x, r);
+  }
+};
+
+template <template <int> class F, typename... Args>
+int dispatch_w(int w, Args... args) {
+  switch (w) {
+    case 1: F<1>::run(args...); return ECG_OK;
+    case 2: F<2>::run(args...); return ECG_OK;
+    case 4: F<4>::run(args...); return ECG_OK;
+    case 8: F<8>::run(args...); return ECG_OK;
+    case 16: F<16>::run(args...); return ECG_OK;
+    case 32: F<32>::run(args...); return ECG_OK;
+    case 64: F<64>::run(args...); return ECG_OK;
+  }
+  return ECG_EINVAL;
+}
+
+template <int W> struct RunGenerate { static void run(ecg_ctx* c, KP P) { Ops<W>::generate(c, P); } };
+template <int W> struct RunSpmm { static void run(ecg_ctx* c, KP P, const double* X, double* Y) { Ops<W>::spmm(c, P, X, Y); } };
+template <int W> struct RunTdot {
+  static void run(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) { Ops<W>::tdot(c, P, gw, B, gy, Cout); }
+};
+template <int W> struct RunUpdate { static void run(ecg_ctx* c, KP P, double* X, const double* Cin) { Ops<W>::update(c, P, X, Cin); } };
+template <int W> struct RunOrth {
+  static void run(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) { Ops<W>::orth(c, P, Wio, V, x, r); }
+};
+
+DevState op_state(const ecg_ctx* c, int width, int nq, int gen) {
+  DevState s;
+  std::memset(&s, 0, sizeof(s));
+  s.k = 1;
+  s.width = width;
+  s.gen = gen;
+  s.nq = nq;
+  s.cap = nq;
+  s.t = c->t;
+  s.kmax = 2;
+  s.variant = c->opts.variant;
+  s.eps = 0.0;
+  return s;
+}
+
+int put_op_state(ecg_ctx* c, const DevState& s) {
+  CK(cudaMemcpyAsync(c->d_opst, &s, sizeof(s), cudaMemcpyHostToDevice, c->stream));
+  // the host copy is a stack temporary: finish the copy before returning
+  CK(cudaStreamSynchronize(c->stream));
+  return ECG_OK;
+}
+
+int ensure_opdesc(ecg_ctx* c, int m) {
+  if (m <= c->opdesc_cap) return ECG_OK;
+  dfree(c->d_opdesc);
+  c->opdesc_cap = 0;
+  int rc = dalloc(&c->d_opdesc, (size_t)m);
+  if (rc) return rc;
+  c->opdesc_cap = m;
+  return ECG_OK;
+}
+
+int put_op_desc(ecg_ctx* c, const std::vector<BlockDesc>& d) {
+  int rc = ensure_opdesc(c, (int)d.size());
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(c->d_opdesc, d.data(), d.size() * sizeof(BlockDesc), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return ECG_OK;
+}
+
+int finish_op(ecg_ctx* c, int* status) {
+  CK(cudaGetLastError());
+  DevState s;
+  CK(cudaMemcpyAsync(&s, c->d_opst, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (status) *status = s.stop ? s.status : ECG_OK;
+  return ECG_OK;
+}
+
+}  // namespace
+
+// ============================================================== C ABI
+
+extern "C" {
+
+void ecg_default_opts(ecg_opts* o) {
+  if (!o) return;
+  o->variant = ECG_SRE;
+  o->trunc = 0;
+  o->switch_tol = 0.0;
+  o->ortho = ECG_PRE_CHOLQR;
+  o->check_every = 16;
+  o->use_graph = 1;
+  o->stream = nullptr;
+}
+
+const char* ecg_strerror(int code) {
+  switch (code) {
+    case ECG_OK: return "converged";
+    case ECG_ENOCONV: return "iteration limit reached before the tolerance";
+    case ECG_EINVAL: return "invalid argument";
+    case ECG_ENOMEM: return "out of memory";
+    case ECG_ECUDA: return "CUDA error";
+    case ECG_EBREAKDOWN: return "block became numerically rank deficient (breakdown)";
+    case ECG_ENOTSPD: return "matrix has a non-positive diagonal entry";
+  }
+  return "unknown status";
+}
+
+void ecg_destroy(ecg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (auto& g : c->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto e : c->pev) cudaEventDestroy(e);
+  for (auto e : c->ev)
+    if (e) cudaEventDestroy(e);
+  if (c->e0) cudaEventDestroy(c->e0);
+  if (c->e1) cudaEventDestroy(c->e1);
+  dfree(c->d_rowptr);
+  dfree(c->d_col);
+  dfree(c->d_val);
+  dfree(c->d_pmap);
+  dfree(c->d_partial);
+  dfree(c->d_X);
+  dfree(c->d_Y);
+  dfree(c->d_x);
+  dfree(c->d_r);
+  dfree(c->d_b);
+  dfree(c->d_sx);
+  dfree(c->d_sr);
+  dfree(c->d_st);
+  dfree(c->d_opst);
+  dfree(c->d_desc);
+  dfree(c->d_opdesc);
+  dfree(c->d_slotW);
+  dfree(c->d_slotV);
+  dfree(c->d_C);
+  dfree(c->d_small);
+  dfree(c->d_hist);
+  dfree(c->d_rho_part);
+  dfree(c->d_beta_part);
+  dfree(c->d_bb_part);
+  if (c->h_flags) cudaFreeHost(c->h_flags);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts* opts, ecg_ctx** out) {
+  if (!out) return ECG_EINVAL;
+  *out = nullptr;
+  if (!A || !partition || !A->rowptr || !A->col || !A->val) return ECG_EINVAL;
+  if (A->n <= 0 || A->n > 0x7fffffff || A->nnz < 0 || A->nnz > 0x7fffffff) return ECG_EINVAL;
+  if (width_index(t) < 0) return ECG_EINVAL;
+  ecg_opts o;
+  ecg_default_opts(&o);
+  if (opts) o = *opts;
+  int rc = validate_opts(&o, t);
+  if (rc) return rc;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return ECG_ECUDA;
+  }
+  const int n = (int)A->n;
+  const int64_t nnz = A->nnz;
+  // Host copies for validation (and upload).
+  std::vector<int64_t> rp(n + 1);
+  std::vector<int32_t> ci(nnz);
+  std::vector<double> va(nnz);
+  std::vector<int32_t> pt(n);
+  if (A->on_device) {
+    if (cudaMemcpy(rp.data(), A->rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ci.data(), A->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(va.data(), A->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pt.data(), partition, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaGetLastError();
+      return ECG_ECUDA;
+    }
+  } else {
+    std::memcpy(rp.data(), A->rowptr, sizeof(int64_t) * (n + 1));
+    std::memcpy(ci.data(), A->col, sizeof(int32_t) * nnz);
+    std::memcpy(va.data(), A->val, sizeof(double) * nnz);
+    std::memcpy(pt.data(), partition, sizeof(int32_t) * n);
+  }
+  if (rp[0] != 0 || rp[n] != nnz) return ECG_EINVAL;
+  std::vector<int> cnt(t, 0);
+  for (int i = 0; i < n; i++) {
+    if (rp[i + 1] < rp[i]) return ECG_EINVAL;
+    if (pt[i] < 0 || pt[i] >= t) return ECG_EINVAL;
+    cnt[pt[i]]++;
+  }
+  for (int j = 0; j < t; j++)
+    if (cnt[j] == 0) return ECG_EINVAL;
+  for (int i = 0; i < n; i++) {
+    double d = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; p++) {
+      if (ci[p] < 0 || ci[p] >= n) return ECG_EINVAL;
+      if (ci[p] == i) d += va[p];
+    }
+    if (!(d > 0.0)) return ECG_ENOTSPD;
+  }
+  std::vector<int> rp32(n + 1);
+  for (int i = 0; i <= n; i++) rp32[i] = (int)rp[i];
+
+  ecg_ctx* c = new (std::nothrow) ecg_ctx();
+  if (!c) return ECG_ENOMEM;
+  c->n = n;
+  c->nnz = nnz;
+  c->t = t;
+  c->opts = o;
+  std::memset(&c->prof, 0, sizeof(c->prof));
+  auto fail = [&](int code) {
+    ecg_destroy(c);
+    return code;
+  };
+  if (cudaGetDevice(&c->dev) != cudaSuccess) return fail(ECG_ECUDA);
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
+    return fail(ECG_ECUDA);
+  if (o.stream) {
+    c->stream = (cudaStream_t)o.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(ECG_ECUDA);
+    c->own_stream = true;
+  }
+  if ((rc = set_all_smem_attrs())) return fail(rc);
+  c->gx = std::max(1, std::min(4 * c->num_sms, (n + 31) / 32));
+  const size_t nt = (size_t)n * t;
+  if ((rc = dalloc(&c->d_rowptr, (size_t)n + 1)) || (rc = dalloc(&c->d_col, (size_t)nnz)) ||
+      (rc = dalloc(&c->d_val, (size_t)nnz)) || (rc = dalloc(&c->d_pmap, (size_t)n)) ||
+      (rc = dalloc(&c->d_X, nt)) || (rc = dalloc(&c->d_Y, nt)) || (rc = dalloc(&c->d_x, (size_t)n)) ||
+      (rc = dalloc(&c->d_r, (size_t)n)) || (rc = dalloc(&c->d_b, (size_t)n)) ||
+      (rc = dalloc(&c->d_sx, (size_t)n)) || (rc = dalloc(&c->d_sr, (size_t)n)) ||
+      (rc = dalloc(&c->d_st, (size_t)1)) || (rc = dalloc(&c->d_opst, (size_t)1)) ||
+      (rc = dalloc(&c->d_small, (size_t)kSmallSize)) || (rc = dalloc(&c->d_rho_part, (size_t)c->gx)) ||
+      (rc = dalloc(&c->d_bb_part, (size_t)c->gx)) || (rc = dalloc(&c->d_beta_part, (size_t)c->gx * 64)))
+    return fail(rc);
+  if (cudaMemcpy(c->d_rowptr, rp32.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_col, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_val, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_pmap, pt.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+    return fail(ECG_ECUDA);
+  if (cudaMemset(c->d_sx, 0, sizeof(double) * n) != cudaSuccess ||
+      cudaMemset(c->d_sr, 0, sizeof(double) * n) != cudaSuccess)
+    return fail(ECG_ECUDA);
+  if (cudaHostAlloc((void**)&c->h_flags, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess)
+    return fail(ECG_ENOMEM);
+  for (auto& e : c->ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return fail(ECG_ECUDA);
+  if (cudaEventCreate(&c->e0) != cudaSuccess || cudaEventCreate(&c->e1) != cudaSuccess) return fail(ECG_ECUDA);
+  *out = c;
+  return ECG_OK;
+}
+
+int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, double tol, int maxit,
+              ecg_result* res) {
+  if (res) std::memset(res, 0, sizeof(*res));
+  if (!c || !b || !x_out) return ECG_EINVAL;
+  if (!(tol >= 0.0) || maxit < 0) return ECG_EINVAL;
+  const int n = c->n, t = c->t;
+  const int kmax = std::max(maxit, 1);
+  const int cap = c->opts.trunc > 0 ? c->opts.trunc : std::max(kmax - 1, 1);
+  cudaStream_t s = c->stream;
+  int rc;
+  CK(cudaStreamSynchronize(s));
+  // ---- storage for the stored blocks, history, coefficients, partials
+  if (cap > c->slot_cap) {
+    invalidate_graphs(c);
+    dfree(c->d_slotW);
+    dfree(c->d_slotV);
+    dfree(c->d_desc);
+    c->slot_cap = 0;
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    double need = 2.0 * (double)cap * (double)n * (double)t * sizeof(double);
+    if (need > 0.92 * (double)freeb) return ECG_ENOMEM;
+    if ((rc = dalloc(&c->d_slotW, (size_t)cap * n * t)) || (rc = dalloc(&c->d_slotV, (size_t)cap * n * t)) ||
+        (rc = dalloc(&c->d_desc, (size_t)cap))) {
+      dfree(c->d_slotW);
+      dfree(c->d_slotV);
+      dfree(c->d_desc);
+      return rc;
+    }
+    c->slot_cap = cap;
+    c->desc_cap = cap;
+  }
+  if (kmax + 1 > c->hist_cap) {
+    invalidate_graphs(c);
+    dfree(c->d_hist);
+    c->hist_cap = 0;
+    if ((rc = dalloc(&c->d_hist, (size_t)kmax + 1))) return rc;
+    c->hist_cap = kmax + 1;
+  }
+  if ((rc = ensure_C(c, (size_t)cap * t * t))) return rc;
+  {
+    const size_t gymax = ((size_t)cap * t + kChunk - 1) / kChunk;
+    size_t need = std::max((4 * (size_t)c->num_sms + gymax) * kChunk * t, (size_t)c->gx * (t * (t + 1) / 2 + t));
+    if ((rc = ensure_part(c, need))) return rc;
+  }
+  // ---- inputs
+  const bool dev_in = is_device_ptr(b);
+  const bool dev_out = is_device_ptr(x_out);
+  CK(cudaMemcpyAsync(c->d_b, b, sizeof(double) * n, dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (x0) {
+    CK(cudaMemcpyAsync(c->d_x, x0, sizeof(double) * n,
+                       is_device_ptr(x0) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  } else {
+    CK(cudaMemsetAsync(c->d_x, 0, sizeof(double) * n, s));
+  }
+  DevState init;
+  std::memset(&init, 0, sizeof(init));
+  init.kmax = kmax;
+  init.variant = c->opts.variant;
+  init.cap = cap;
+  init.t = t;
+  init.eps = tol;
+  init.switch_tol = c->opts.switch_tol;
+  CK(cudaMemcpyAsync(c->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(c->e0, s));
+  KP P = make_kp(c, c->d_st, c->d_desc);
+  prof_mark(c, -1);
+  k_residual<<<c->gx, kThreads, 0, s>>>(P, x0 ? c->d_x : nullptr, c->d_r, c->d_rho_part, nullptr);
+  k_start<<<1, kThreads, 0, s>>>(P, c->gx);
+  prof_mark(c, 9);
+  CK(cudaGetLastError());
+  // ---- iterations: groups of check_every, polled one group behind.  The
+  // host never issues iteration k_max or later; after the flexible switch it
+  // rewinds its count to the device's k (the group in flight, issued for
+  // the old width, does nothing).
+  const int chunk = c->opts.check_every;
+  int W = t;
+  int khost = 1;  // next iteration the host issues
+  auto issue = [&](int slot) -> int {
+    const int nit = std::min(chunk, kmax - khost);
+    if (nit > 0) {
+      int r2 = enqueue_group(c, W, nit, cap, khost);
+      if (r2) return r2;
+      khost += nit;
+    }
+    CK(cudaMemcpyAsync(&c->h_flags[slot], c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev[slot], s));
+    return ECG_OK;
+  };
+  if ((rc = issue(0))) return rc;
+  int cur = 0;
+  long long polls = 0;
+  const long long max_polls = 4LL * ((long long)kmax / chunk + 4);
+  while (true) {
+    if ((rc = issue(1 - cur))) return rc;
+    CK(cudaEventSynchronize(c->ev[cur]));
+    const DevState f = c->h_flags[cur];
+    if (f.stop) break;
+    if (f.width != W) {
+      if (width_index(f.width) < 0) return ECG_ECUDA;
+      W = f.width;
+      khost = f.k;
+    }
+    cur = 1 - cur;
+    if (++polls > max_polls) {  // the device never stopped: not expected
+      cudaStreamSynchronize(s);
+      return ECG_ECUDA;
+    }
+  }
+  CK(cudaEventRecord(c->e1, s));
+  // ---- results
+  DevState fin;
+  CK(cudaMemcpyAsync(&fin, c->d_st, sizeof(fin), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  prof_collect(c);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->e0, c->e1);
+  const int iters = fin.iters;
+  c->h_hist.assign((size_t)iters + 1, 0.0);
+  CK(cudaMemcpy(c->h_hist.data(), c->d_hist, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));
+  // true residual ||b - A x|| / ||b||
+  k_residual<<<c->gx, kThreads, 0, s>>>(P, c->d_x, nullptr, c->d_rho_part, c->d_bb_part);
+  CK(cudaGetLastError());
+  std::vector<double> prr(c->gx), pbb(c->gx);
+  CK(cudaMemcpyAsync(prr.data(), c->d_rho_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pbb.data(), c->d_bb_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(x_out, c->d_x, sizeof(double) * n, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double srr = 0.0, sbb = 0.0;
+  for (int i = 0; i < c->gx; i++) {
+    srr += prr[i];
+    sbb += pbb[i];
+  }
+  const int status = fin.status;
+  if (res) {
+    res->iters = iters;
+    res->switch_it = fin.switch_it;
+    res->status = status;
+    res->mem_vectors = fin.mem;
+    res->relres = fin.rho0 > 0.0 ? fin.rho_prev / fin.rho0 : fin.rho_prev;
+    res->relres_true = sbb > 0.0 ? std::sqrt(srr / sbb) : std::sqrt(srr);
+    res->device_ms = ms;
+    res->history = c->h_hist.data();
+  }
+  return status;
+}
+
+int ecg_profile_enable(ecg_ctx* c, int on) {
+  if (!c) return ECG_EINVAL;
+  c->profiling = (on != 0);
+  std::memset(&c->prof, 0, sizeof(c->prof));
+  c->pev_used = 0;
+  return ECG_OK;
+}
+
+int ecg_profile_read(ecg_ctx* c, int cls, const char** name, double* ms, long long* launches) {
+  if (!c) return ECG_EINVAL;
+  if (cls < 0 || cls >= kProfClasses) return kProfClasses;
+  if (name) *name = kProfNames[cls];
+  if (ms) *ms = c->prof.ms[cls];
+  if (launches) *launches = c->prof.launches[cls];
+  return kProfClasses;
+}
+
+// ------------------------------------------------------ step-level calls
+
+int ecg_op_split(ecg_ctx* c, const double* r, double* W, int half) {
+  if (!c || !r || !W) return ECG_EINVAL;
+  if (half && (c->t % 2)) return ECG_EINVAL;
+  const int w = half ? c->t / 2 : c->t;
+  int rc;
+  if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  P.X = W;
+  P.r = const_cast<double*>(r);
+  if ((rc = dispatch_w<RunGenerate>(w, c, P))) return rc;
+  return finish_op(c, nullptr);
+}
+
+int ecg_op_spmm(ecg_ctx* c, const double* X, double* Y, int w) {
+  if (!c || !X || !Y || width_index(w) < 0) return ECG_EINVAL;
+  int rc;
+  if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  if ((rc = dispatch_w<RunSpmm>(w, c, P, X, Y))) return rc;
+  return finish_op(c, nullptr);
+}
+
+int ecg_op_tdot(ecg_ctx* c, int m, const double* const* X, const int* wx, const double* Y, int wy, double* C) {
+  if (!c || m < 1 || m > 1024 || !X || !wx || !Y || !C || width_index(wy) < 0) return ECG_EINVAL;
+  std::vector<BlockDesc> d(m);
+  int off = 0;
+  for (int j = 0; j < m; j++) {
+    if (!X[j] || wx[j] < 1 || wx[j] > 128) return ECG_EINVAL;
+    d[j].W = const_cast<double*>(X[j]);
+    d[j].V = const_cast<double*>(X[j]);
+    d[j].w = wx[j];
+    d[j].off = off;
+    d[j].slot = 0;
+    d[j].pad = 0;
+    off += wx[j];
+  }
+  const int gy = (off + kChunk - 1) / kChunk;
+  int rc;
+  if ((rc = ensure_part(c, (size_t)gy * window_gx(c, gy) * kChunk * wy))) return rc;
+  if ((rc = put_op_desc(c, d))) return rc;
+  if ((rc = put_op_state(c, op_state(c, wy, m, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  if ((rc = dispatch_w<RunTdot>(wy, c, P, wy, Y, gy, C))) return rc;
+  return finish_op(c, nullptr);
+}
+
+int ecg_op_cgs2(ecg_ctx* c, int m, const double* const* Q, const double* const* V, const int* wq, double* W,
+                int w) {
+  if (!c || m < 1 || m > 1024 || !Q || !V || !wq || !W || width_index(w) < 0) return ECG_EINVAL;
+  std::vector<BlockDesc> d(m);
+  int off = 0;
+  for (int j = 0; j < m; j++) {
+    if (!Q[j] || !V[j] || wq[j] < 1 || wq[j] > 128) return ECG_EINVAL;
+    d[j].W = const_cast<double*>(Q[j]);
+    d[j].V = const_cast<double*>(V[j]);
+    d[j].w = wq[j];
+    d[j].off = off;
+    d[j].slot = 0;
+    d[j].pad = 0;
+    off += wq[j];
+  }
+  const int gy = (off + kChunk - 1) / kChunk;
+  int rc;
+  if ((rc = ensure_part(c, (size_t)gy * window_gx(c, gy) * kChunk * w))) return rc;
+  if ((rc = ensure_C(c, (size_t)gy * kChunk * w))) return rc;
+  if ((rc = put_op_desc(c, d))) return rc;
+  if ((rc = put_op_state(c, op_state(c, w, m, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  for (int pass = 0; pass < 2; pass++) {
+    if ((rc = dispatch_w<RunTdot>(w, c, P, w, (const double*)W, gy, c->d_C))) return rc;
+    if ((rc = dispatch_w<RunUpdate>(w, c, P, W, (const double*)c->d_C))) return rc;
+  }
+  return finish_op(c, nullptr);
+}
+
+static int op_orth(ecg_ctx* c, double* W, double* V, int w, double* x, double* r, double* rho) {
+  if (!c || !W || !V || width_index(w) < 0) return ECG_EINVAL;
+  int rc;
+  if ((rc = ensure_part(c, (size_t)c->gx * (w * (w + 1) / 2 + w)))) return rc;
+  if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  P.r = r;
+  P.want_beta = 0;
+  if ((rc = dispatch_w<RunOrth>(w, c, P, W, V, x, r))) return rc;
+  k_rho_only<<<1, kThreads, 0, c->stream>>>(P, c->gx);
+  int status = ECG_OK;
+  if ((rc = finish_op(c, &status))) return rc;
+  if (rho) {
+    DevState s;
+    CK(cudaMemcpy(&s, c->d_opst, sizeof(s), cudaMemcpyDeviceToHost));
+    *rho = s.rho;
+  }
+  return status;
+}
+
+int ecg_op_a_orthonormalize(ecg_ctx* c, double* W, double* V, int w) {
+  if (!c) return ECG_EINVAL;
+  return op_orth(c, W, V, w, c->d_sx, c->d_sr, nullptr);
+}
+
+int ecg_op_block_update(ecg_ctx* c, double* W, double* V, int w, double* x, double* r, double* rho) {
+  if (!c || !x || !r) return ECG_EINVAL;
+  return op_orth(c, W, V, w, x, r, rho);
+}
+
+int ecg_op_msdo_generate(ecg_ctx* c, const double* r, const double* P_prev, const double* V_prev, int w,
+                         double* Pout) {
+  if (!c || !r || !P_prev || !V_prev || !Pout) return ECG_EINVAL;
+  if (!(w == c->t || (c->t % 2 == 0 && w == c->t / 2))) return ECG_EINVAL;
+  std::vector<BlockDesc> d(1);
+  d[0].W = const_cast<double*>(P_prev);
+  d[0].V = const_cast<double*>(V_prev);
+  d[0].w = w;
+  d[0].off = 0;
+  d[0].slot = 0;
+  d[0].pad = 0;
+  int rc;
+  if ((rc = ensure_part(c, (size_t)window_gx(c, 1) * kChunk))) return rc;
+  if ((rc = put_op_desc(c, d))) return rc;
+  if ((rc = put_op_state(c, op_state(c, 1, 1, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  if ((rc = dispatch_w<RunTdot>(1, c, P, 1, r, 1, c->d_small + kSmallG))) return rc;
+  k_neg_copy<<<1, 64, 0, c->stream>>>(c->d_small + kSmallG, c->d_small + kSmallBe, w);
+  if ((rc = put_op_state(c, op_state(c, w, 1, GEN_MSDO)))) return rc;
+  P.X = Pout;
+  P.r = const_cast<double*>(r);
+  if ((rc = dispatch_w<RunGenerate>(w, c, P))) return rc;
+  return finish_op(c, nullptr);
+}
+
+}  // extern "C"

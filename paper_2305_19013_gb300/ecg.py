@@ -1,0 +1,380 @@
+"""ctypes binding of libecg (include/ecg.h).
+
+Argument marshalling only: every step of the solve runs in the CUDA
+library.  Host arrays are numpy float64/int arrays; device arrays are torch
+CUDA tensors (PyTorch provides device memory and streams).  There is no CPU
+fallback: if libecg.so is missing or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK, ENOCONV, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTSPD = 0, 1, -1, -2, -3, -4, -5
+SRE, MSDO, MODMSDO = 0, 1, 2
+PRE_CHOLQR, A_CHOLQR = 0, 1
+VARIANTS = {"sre": SRE, "msdo": MSDO, "modmsdo": MODMSDO}
+
+
+class EcgError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+class _Csr(C.Structure):
+    _fields_ = [
+        ("n", C.c_int64),
+        ("nnz", C.c_int64),
+        ("rowptr", C.c_void_p),
+        ("col", C.c_void_p),
+        ("val", C.c_void_p),
+        ("on_device", C.c_int),
+    ]
+
+
+class _Opts(C.Structure):
+    _fields_ = [
+        ("variant", C.c_int),
+        ("trunc", C.c_int),
+        ("switch_tol", C.c_double),
+        ("ortho", C.c_int),
+        ("check_every", C.c_int),
+        ("use_graph", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
+class _Result(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int),
+        ("switch_it", C.c_int),
+        ("status", C.c_int),
+        ("mem_vectors", C.c_int64),
+        ("relres", C.c_double),
+        ("relres_true", C.c_double),
+        ("device_ms", C.c_double),
+        ("history", C.POINTER(C.c_double)),
+    ]
+
+
+_lib = None
+_P = C.c_void_p
+_I = C.c_int
+_D = C.c_double
+
+# Every function declared in include/ecg.h, with its ctypes signature.
+SIGNATURES = {
+    "ecg_default_opts": (None, [C.POINTER(_Opts)]),
+    "ecg_create": (_I, [C.POINTER(_Csr), _P, _I, C.POINTER(_Opts), C.POINTER(_P)]),
+    "ecg_solve": (_I, [_P, _P, _P, _P, _D, _I, C.POINTER(_Result)]),
+    "ecg_destroy": (None, [_P]),
+    "ecg_strerror": (C.c_char_p, [_I]),
+    "ecg_profile_enable": (_I, [_P, _I]),
+    "ecg_profile_read": (_I, [_P, _I, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "ecg_op_split": (_I, [_P, _P, _P, _I]),
+    "ecg_op_spmm": (_I, [_P, _P, _P, _I]),
+    "ecg_op_tdot": (_I, [_P, _I, _P, _P, _P, _I, _P]),
+    "ecg_op_cgs2": (_I, [_P, _I, _P, _P, _P, _P, _I]),
+    "ecg_op_a_orthonormalize": (_I, [_P, _P, _P, _I]),
+    "ecg_op_block_update": (_I, [_P, _P, _P, _I, _P, _P, C.POINTER(C.c_double)]),
+    "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libecg.so (building it in-tree when it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libecg.so is not built ({path}); run paper_2305_19013_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().ecg_strerror(int(code)).decode()
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _is_torch_cuda(a) -> bool:
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _check_tensor(a, shape, name):
+    import torch
+
+    if not (_is_torch_cuda(a) and a.dtype == torch.float64 and a.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(a.shape)}, expected {tuple(shape)}")
+
+
+@dataclass
+class SolveResult:
+    x: object
+    iters: int
+    switch_it: int
+    status: int
+    mem_vectors: int
+    relres: float
+    relres_true: float
+    device_ms: float
+    history: np.ndarray
+
+
+class Solver:
+    """A solver context: the matrix, its partition and the options
+    (ecg_create); ``solve`` runs ecg_solve."""
+
+    def __init__(
+        self,
+        rowptr,
+        col,
+        val,
+        part,
+        t: int,
+        variant="sre",
+        trunc: int = 0,
+        switch_tol: float = 0.0,
+        ortho: int = PRE_CHOLQR,
+        check_every: int = 16,
+        use_graph: bool = True,
+        stream=None,
+    ):
+        lib = load()
+        self._lib = lib
+        self._ctx = None
+        on_dev = _is_torch_cuda(val)
+        if on_dev:
+            self._keep = (rowptr, col, val, part)
+        else:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            part = np.ascontiguousarray(part, dtype=np.int32)
+            self._keep = (rowptr, col, val, part)
+        n = int(rowptr.shape[0]) - 1
+        self.n = n
+        self.t = int(t)
+        csr = _Csr(n, int(col.shape[0]), _ptr(rowptr), _ptr(col), _ptr(val), 1 if on_dev else 0)
+        o = _Opts()
+        lib.ecg_default_opts(C.byref(o))
+        o.variant = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o.trunc = int(trunc)
+        o.switch_tol = float(switch_tol)
+        o.ortho = int(ortho)
+        o.check_every = int(check_every)
+        o.use_graph = 1 if use_graph else 0
+        o.stream = stream
+        ctx = C.c_void_p()
+        rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))
+        if rc != OK:
+            raise EcgError(rc, "ecg_create")
+        self._ctx = ctx
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        return cls(p.rowptr, p.col, p.val, p.part, p.t, **kw)
+
+    def close(self):
+        if self._ctx is not None:
+            self._lib.ecg_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, b, x0=None, tol: float = 1e-8, maxit: int = 1000, x_out=None, raise_on_error=True) -> SolveResult:
+        """b, x0, x_out: numpy arrays (host) or float64 CUDA tensors (device).
+        Returns the iterate in x_out (allocated like b when None)."""
+        if _is_torch_cuda(b):
+            import torch
+
+            _check_tensor(b, (self.n,), "b")
+            if x0 is not None:
+                _check_tensor(x0, (self.n,), "x0")
+            if x_out is None:
+                x_out = torch.empty_like(b)
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            if x0 is not None:
+                x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            if x_out is None:
+                x_out = np.empty(self.n)
+        res = _Result()
+        rc = self._lib.ecg_solve(self._ctx, _ptr(b), _ptr(x0), _ptr(x_out), float(tol), int(maxit), C.byref(res))
+        if rc < 0 and rc != EBREAKDOWN and raise_on_error:
+            raise EcgError(rc, "ecg_solve")
+        hist = np.ctypeslib.as_array(res.history, shape=(res.iters + 1,)).copy() if res.history else np.zeros(0)
+        return SolveResult(
+            x=x_out,
+            iters=res.iters,
+            switch_it=res.switch_it,
+            status=rc,
+            mem_vectors=res.mem_vectors,
+            relres=res.relres,
+            relres_true=res.relres_true,
+            device_ms=res.device_ms,
+            history=hist,
+        )
+
+    # ---------------------------------------------------------- profiling
+
+    def profile(self, on: bool = True):
+        rc = self._lib.ecg_profile_enable(self._ctx, 1 if on else 0)
+        if rc != OK:
+            raise EcgError(rc, "ecg_profile_enable")
+
+    def profile_read(self) -> dict:
+        ncls = self._lib.ecg_profile_read(self._ctx, -1, None, None, None)
+        out = {}
+        for c in range(ncls):
+            name = C.c_char_p()
+            ms = C.c_double()
+            cnt = C.c_longlong()
+            self._lib.ecg_profile_read(self._ctx, c, C.byref(name), C.byref(ms), C.byref(cnt))
+            out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    # ------------------------------------------------------- step level
+
+    def _rc(self, rc, what):
+        if rc < 0:
+            raise EcgError(rc, what)
+        return rc
+
+    def split(self, r, half: bool = False):
+        import torch
+
+        _check_tensor(r, (self.n,), "r")
+        w = self.t // 2 if half else self.t
+        W = torch.empty((self.n, w), dtype=torch.float64, device=r.device)
+        self._rc(self._lib.ecg_op_split(self._ctx, _ptr(r), _ptr(W), 1 if half else 0), "ecg_op_split")
+        return W
+
+    def spmm(self, X):
+        import torch
+
+        w = X.shape[1]
+        _check_tensor(X, (self.n, w), "X")
+        Y = torch.empty_like(X)
+        self._rc(self._lib.ecg_op_spmm(self._ctx, _ptr(X), _ptr(Y), int(w)), "ecg_op_spmm")
+        return Y
+
+    def tdot(self, Xs, Y):
+        import torch
+
+        if Y.dim() == 1:
+            Y = Y.reshape(-1, 1)
+        wy = Y.shape[1]
+        _check_tensor(Y, (self.n, wy), "Y")
+        for X in Xs:
+            _check_tensor(X, (self.n, X.shape[1]), "X")
+        m = len(Xs)
+        ptrs = (C.c_void_p * m)(*[X.data_ptr() for X in Xs])
+        ws = (C.c_int * m)(*[int(X.shape[1]) for X in Xs])
+        tot = sum(int(X.shape[1]) for X in Xs)
+        Cm = torch.empty((tot, wy), dtype=torch.float64, device=Y.device)
+        self._rc(
+            self._lib.ecg_op_tdot(self._ctx, m, C.cast(ptrs, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(Y), int(wy), _ptr(Cm)),
+            "ecg_op_tdot",
+        )
+        return Cm
+
+    def cgs2(self, Qs, Vs, W):
+        w = W.shape[1]
+        _check_tensor(W, (self.n, w), "W")
+        W = W.clone()
+        m = len(Qs)
+        qp = (C.c_void_p * m)(*[q.data_ptr() for q in Qs])
+        vp = (C.c_void_p * m)(*[v.data_ptr() for v in Vs])
+        ws = (C.c_int * m)(*[int(q.shape[1]) for q in Qs])
+        for q, v in zip(Qs, Vs):
+            _check_tensor(q, (self.n, q.shape[1]), "Q")
+            _check_tensor(v, tuple(q.shape), "V")
+        self._rc(
+            self._lib.ecg_op_cgs2(
+                self._ctx, m, C.cast(qp, C.c_void_p), C.cast(vp, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(W), int(w)
+            ),
+            "ecg_op_cgs2",
+        )
+        return W
+
+    def a_orthonormalize(self, W):
+        """Returns (W_k, A W_k, status)."""
+        import torch
+
+        w = W.shape[1]
+        _check_tensor(W, (self.n, w), "W")
+        W = W.clone()
+        V = torch.empty_like(W)
+        rc = self._lib.ecg_op_a_orthonormalize(self._ctx, _ptr(W), _ptr(V), int(w))
+        if rc < 0 and rc != EBREAKDOWN:
+            raise EcgError(rc, "ecg_op_a_orthonormalize")
+        return W, V, rc
+
+    def block_update(self, W, x, r):
+        """Returns (W_k, V_k, x, r, rho, status); x and r are updated copies."""
+        import torch
+
+        w = W.shape[1]
+        _check_tensor(W, (self.n, w), "W")
+        _check_tensor(x, (self.n,), "x")
+        _check_tensor(r, (self.n,), "r")
+        W, x, r = W.clone(), x.clone(), r.clone()
+        V = torch.empty_like(W)
+        rho = C.c_double()
+        rc = self._lib.ecg_op_block_update(self._ctx, _ptr(W), _ptr(V), int(w), _ptr(x), _ptr(r), C.byref(rho))
+        if rc < 0 and rc != EBREAKDOWN:
+            raise EcgError(rc, "ecg_op_block_update")
+        return W, V, x, r, rho.value, rc
+
+    def msdo_generate(self, r, P_prev, V_prev):
+        import torch
+
+        w = P_prev.shape[1]
+        _check_tensor(r, (self.n,), "r")
+        _check_tensor(P_prev, (self.n, w), "P_prev")
+        _check_tensor(V_prev, (self.n, w), "V_prev")
+        P = torch.empty_like(P_prev)
+        self._rc(
+            self._lib.ecg_op_msdo_generate(self._ctx, _ptr(r), _ptr(P_prev), _ptr(V_prev), int(w), _ptr(P)),
+            "ecg_op_msdo_generate",
+        )
+        return P

@@ -148,21 +148,23 @@ def block_partition2d(nx: int, ny: int, px: int, py: int) -> np.ndarray:
 
     Subdomain id = by*px + bx, so pairs {2j, 2j+1} are horizontally adjacent
     blocks when px is even (and vertically adjacent strips when px == 1).
+    Block bx covers the columns x with floor(x*px/nx) = bx (equal blocks
+    when px divides nx).
     """
-    if nx % px or ny % py:
-        raise ValueError("grid must divide evenly into blocks")
+    if px > nx or py > ny:
+        raise ValueError("more blocks than grid lines")
     y, x = np.divmod(np.arange(nx * ny), nx)
-    return ((y // (ny // py)) * px + (x // (nx // px))).astype(np.int32)
+    return ((y * py // ny) * px + (x * px // nx)).astype(np.int32)
 
 
 def block_partition3d(nx: int, ny: int, nz: int, px: int, py: int, pz: int) -> np.ndarray:
     """Rectangular px x py x pz block partition; id = (bz*py + by)*px + bx."""
-    if nx % px or ny % py or nz % pz:
-        raise ValueError("grid must divide evenly into blocks")
+    if px > nx or py > ny or pz > nz:
+        raise ValueError("more blocks than grid lines")
     i = np.arange(nx * ny * nz)
     z, rem = np.divmod(i, nx * ny)
     y, x = np.divmod(rem, nx)
-    return (((z // (nz // pz)) * py + (y // (ny // py))) * px + (x // (nx // px))).astype(np.int32)
+    return (((z * pz // nz) * py + (y * py // ny)) * px + (x * px // nx)).astype(np.int32)
 
 
 def reorder_by_subdomain(A: sp.csr_matrix, part: np.ndarray):

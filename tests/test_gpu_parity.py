@@ -1,0 +1,401 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Step-level tests compare each kernel chain with the oracle function for the
+same step on the same seeded inputs; solver tests compare whole solves
+(iterations within +-1, final solution within 1e-8 relative when the
+iteration counts agree, identical status and switch iteration).
+
+Tolerances.  The GPU sums in a different order than the oracle (row tiles,
+two-stage CTA reductions, fused multiply-adds), so floating-point results
+differ by rounding.  For a dot product of length n the difference is bounded
+by about 2 n eps sum|x_i y_i|; the tests use 1e-12 relative to
+sum|x_i||y_i| for products, and relative errors of 1e-10 .. 1e-12 for
+quantities built from a few such products on well-conditioned blocks.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2305_19013_gb300 import ecg
+from paper_2305_19013_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need a CUDA GPU")
+    ecg.load()
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def ragged(t, seed=5):
+    """36 x 36 grid: 1296 rows, not a multiple of the 32-row tiles, with
+    uneven blocks for t = 32, 64."""
+    return W.random_spd_grid(36, t, seed=seed)
+
+
+# ------------------------------------------------------------- steps
+
+
+@pytest.mark.parametrize("t", [1, 2, 4, 16, 64])
+def test_split_exact(t):
+    p = ragged(t)
+    with ecg.Solver.from_problem(p) as s:
+        r = np.random.default_rng(1).standard_normal(p.n)
+        Wg = host(s.split(dev(r)))
+        assert np.array_equal(Wg, O.split(p.part, t, r))
+        if t % 2 == 0:
+            Wh = host(s.split(dev(r), half=True))
+            assert np.array_equal(Wh, O.split_half(p.part, t, r))
+
+
+@pytest.mark.parametrize("w", [1, 2, 8, 16, 32, 64])
+def test_spmm(w):
+    p = ragged(16)
+    A = p.scipy()
+    X = np.random.default_rng(w).standard_normal((p.n, w))
+    with ecg.Solver.from_problem(p) as s:
+        Yg = host(s.spmm(dev(X)))
+    Yo = O.spmm(A, X)
+    bound = 1e-14 * (abs(A) @ np.abs(X))
+    assert np.all(np.abs(Yg - Yo) <= bound + 1e-300)
+
+
+@pytest.mark.parametrize("wy", [1, 4, 16, 64])
+def test_tdot_window(wy):
+    p = ragged(16)
+    rng = np.random.default_rng(2)
+    widths = [16, 16, 8, 64, 3]  # spans several 64-column chunks, one odd width
+    Xs = [rng.standard_normal((p.n, w)) for w in widths]
+    Y = rng.standard_normal((p.n, wy))
+    with ecg.Solver.from_problem(p) as s:
+        Cg = host(s.tdot([dev(x) for x in Xs], dev(Y)))
+    Xc = np.hstack(Xs)
+    Co = O.block_tdot(Xc, Y)
+    bound = 1e-12 * (np.abs(Xc).T @ np.abs(Y))
+    assert Cg.shape == Co.shape
+    assert np.all(np.abs(Cg - Co) <= bound)
+
+
+def _window(p, widths, seed):
+    """A-orthonormal blocks Q_j (with V_j = A Q_j) built by the oracle."""
+    A = p.scipy()
+    rng = np.random.default_rng(seed)
+    Qs, Vs = [], []
+    for w in widths:
+        Z = rng.standard_normal((p.n, w))
+        if Qs:
+            Z, _ = O.cgs2(Qs, Vs, Z)
+        Z, V, st = O.a_orthonormalize(A, Z, 1)
+        assert st == 0
+        Qs.append(Z)
+        Vs.append(V)
+    return Qs, Vs
+
+
+@pytest.mark.parametrize("t", [4, 16, 32])
+def test_cgs2(t):
+    p = ragged(t)
+    Qs, Vs = _window(p, [t, t, t, t // 2], seed=3)
+    Win = np.random.default_rng(4).standard_normal((p.n, t // 2))
+    Wo, st = O.cgs2(Qs, Vs, Win)
+    with ecg.Solver.from_problem(p) as s:
+        Wg = host(s.cgs2([dev(q) for q in Qs], [dev(v) for v in Vs], dev(Win)))
+    assert rel(Wg, Wo) < 1e-12
+
+
+@pytest.mark.parametrize("ortho", [ecg.PRE_CHOLQR, ecg.A_CHOLQR])
+@pytest.mark.parametrize("t", [1, 4, 16, 64])
+def test_a_orthonormalize(t, ortho):
+    p = ragged(t)
+    A = p.scipy()
+    Wr = np.random.default_rng(6).standard_normal((p.n, t))
+    Wo, Vo, st = O.a_orthonormalize(A, Wr, 0 if ortho == ecg.PRE_CHOLQR else 1)
+    assert st == 0
+    with ecg.Solver.from_problem(p, ortho=ortho) as s:
+        Wg, Vg, rc = s.a_orthonormalize(dev(Wr))
+    assert rc == 0
+    Wg, Vg = host(Wg), host(Vg)
+    assert rel(Wg, Wo) < 1e-10
+    assert rel(Vg, Vo) < 1e-10
+    assert np.abs(Wg.T @ (A @ Wg) - np.eye(t)).max() < 1e-12
+
+
+def test_a_orthonormalize_breakdown():
+    p = ragged(8)
+    Wr = np.random.default_rng(7).standard_normal((p.n, 8))
+    Wr[:, 5] = Wr[:, 2]
+    for ortho in (ecg.PRE_CHOLQR, ecg.A_CHOLQR):
+        with ecg.Solver.from_problem(p, ortho=ortho) as s:
+            _, _, rc = s.a_orthonormalize(dev(Wr))
+        assert rc == ecg.EBREAKDOWN
+
+
+@pytest.mark.parametrize("t", [4, 16])
+def test_block_update(t):
+    """alpha = W_k^T r, x += W_k alpha, r -= A W_k alpha, rho = ||r||
+    (Algorithm 1 lines 9-12) after A-orthonormalising the block."""
+    p = ragged(t)
+    A = p.scipy()
+    rng = np.random.default_rng(8)
+    Wr = rng.standard_normal((p.n, t))
+    x = rng.standard_normal(p.n)
+    r = rng.standard_normal(p.n)
+    Wo, Vo, st = O.a_orthonormalize(A, Wr, 0)
+    al = O.block_tdot(Wo, r).ravel()
+    xo = x + Wo @ al
+    ro = r - Vo @ al
+    with ecg.Solver.from_problem(p) as s:
+        Wg, Vg, xg, rg, rho, rc = s.block_update(dev(Wr), dev(x), dev(r))
+    assert rc == 0
+    assert rel(host(Wg), Wo) < 1e-10
+    assert rel(host(xg), xo) < 1e-12
+    assert rel(host(rg), ro) < 1e-11
+    assert abs(rho - np.linalg.norm(ro)) <= 1e-11 * np.linalg.norm(ro)
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_msdo_generate(half):
+    """P_k = [T(r)] + P_{k-1} diag(beta), beta = -V_{k-1}^T r (Algorithm 2
+    lines 6-7)."""
+    t = 8
+    p = ragged(t)
+    w = t // 2 if half else t
+    rng = np.random.default_rng(9)
+    Pp = rng.standard_normal((p.n, w))
+    Vp = rng.standard_normal((p.n, w))
+    r = rng.standard_normal(p.n)
+    beta = -O.block_tdot(Vp, r).ravel()
+    T = O.split_half(p.part, t, r) if half else O.split(p.part, t, r)
+    Po = T + Pp * beta[None, :]
+    with ecg.Solver.from_problem(p) as s:
+        Pg = host(s.msdo_generate(dev(r), dev(Pp), dev(Vp)))
+    assert rel(Pg, Po) < 1e-13
+
+
+# ------------------------------------------------------------ solves
+#
+# Two parity criteria.  STRICT (well-conditioned runs): iterations within
+# +-1, residual history within 1e-8 rho_0 at every step, final x within 1e-8
+# relative.  ENVELOPE (ill-conditioned matrices, truncated or flexible runs):
+# such runs are chaotic -- in the oracle itself a 1e-15 relative perturbation
+# of b grows about 100x per iteration once the basis has lost A-orthogonality,
+# and a truncated run's iteration count moves by several percent.  There the GPU must (a) track the oracle's
+# history to 1e-8 rho_0 for as long as the oracle tracks its own perturbed
+# runs to 1e-10 rho_0, (b) converge with an iteration count inside the range
+# spanned by the oracle's perturbed runs widened by that range's width, and
+# (c) end within the oracle's own x spread.
+
+STRICT, ENVELOPE = "strict", "envelope"
+
+SOLVE_CASES = [
+    ("poisson64_t4_full", lambda: W.poisson2d(64, 4, seed=1001), dict(), STRICT),
+    ("poisson64_t4_trunc2", lambda: W.poisson2d(64, 4, seed=1001), dict(trunc=2), STRICT),
+    ("poisson64_t4_flex", lambda: W.poisson2d(64, 4, seed=1001), dict(switch_tol=1e-3), STRICT),
+    ("poisson64_t4_msdo", lambda: W.poisson2d(64, 4, seed=1001), dict(variant="msdo"), STRICT),
+    ("poisson64_t4_msdo_trunc3", lambda: W.poisson2d(64, 4, seed=1001), dict(variant="msdo", trunc=3), STRICT),
+    ("poisson64_t4_modmsdo", lambda: W.poisson2d(64, 4, seed=1001), dict(variant="modmsdo"), STRICT),
+    ("poisson64_t4_acholqr", lambda: W.poisson2d(64, 4, seed=1001), dict(ortho=1), STRICT),
+    ("ragged_t1", lambda: ragged(1, seed=11), dict(), STRICT),
+    ("ragged_t2_flex", lambda: ragged(2, seed=12), dict(switch_tol=1e-4), STRICT),
+    ("ragged_t16_flex_msdo", lambda: ragged(16, seed=14), dict(variant="msdo", switch_tol=1e-4), STRICT),
+    ("ragged_t32", lambda: ragged(32, seed=15), dict(), STRICT),
+    ("blocky40_t8_flex", lambda: W.blocky_diffusion2d(40, 8, blocks=8, seed=33), dict(switch_tol=1e-3), ENVELOPE),
+    ("blocky64_t8_modmsdo_trunc4", lambda: W.blocky_diffusion2d(64, 8, blocks=8, seed=20), dict(variant="modmsdo", trunc=4), STRICT),
+    ("aniso3d_16_t16_trunc2", lambda: W.anisotropic_diffusion3d(16, 16, seed=19), dict(trunc=2), ENVELOPE),
+    ("ragged_t8_trunc2", lambda: ragged(8, seed=13), dict(trunc=2), ENVELOPE),
+    ("ragged_t64_trunc2", lambda: ragged(64, seed=16), dict(trunc=2), ENVELOPE),
+    ("blocky64_t16_trunc2", lambda: W.blocky_diffusion2d(64, 16, blocks=8, seed=17), dict(trunc=2), ENVELOPE),
+]
+
+
+def _oracle_kw(kw):
+    return dict(
+        variant=kw.get("variant", "sre"),
+        trunc=kw.get("trunc", 0),
+        switch_tol=kw.get("switch_tol", 0.0),
+        ortho=kw.get("ortho", 0),
+    )
+
+
+@pytest.mark.parametrize("name,make,kw,mode", SOLVE_CASES, ids=[c[0] for c in SOLVE_CASES])
+def test_solve_matches_oracle(name, make, kw, mode):
+    p = make()
+    maxit = 3000
+    A = p.scipy()
+    o = O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, **_oracle_kw(kw))
+    with ecg.Solver.from_problem(p, **kw) as s:
+        g = s.solve(dev(p.b), tol=1e-8, maxit=maxit)
+    xg = host(g.x)
+    assert o.status == 0
+    assert g.status == o.status, (g.status, o.status)
+    assert g.relres <= 1e-8
+    assert g.relres_true <= 1e-7
+    if kw.get("switch_tol"):
+        assert o.switch_it > 0
+        assert abs(g.switch_it - o.switch_it) <= 1, (g.switch_it, o.switch_it)
+    h0 = o.history[0]
+    if mode == STRICT:
+        assert abs(g.iters - o.iters) <= 1, (g.iters, o.iters)
+        k = min(g.iters, o.iters)
+        assert np.all(np.abs(g.history[: k + 1] - o.history[: k + 1]) <= 1e-8 * h0)
+        if g.iters == o.iters:
+            assert rel(xg, o.x) <= 1e-8
+            if g.switch_it == o.switch_it:
+                assert g.mem_vectors == o.mem_vectors
+        return
+    # ENVELOPE: the oracle's own spread under rounding-level perturbations
+    rng = np.random.default_rng(99)
+    variants = []
+    for _ in range(4):
+        bp = p.b * (1.0 + 1e-15 * rng.standard_normal(p.n))
+        variants.append(O.ecg_solve(A, p.part, p.t, bp, tol=1e-8, maxit=maxit, **_oracle_kw(kw)))
+    okw = _oracle_kw(kw)
+    okw["ortho"] = 1 - okw["ortho"]
+    variants.append(O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, **okw))
+    assert all(v.status == 0 for v in variants)
+    its = [o.iters] + [v.iters for v in variants]
+    lo, hi = min(its), max(its)
+    width = max(2, hi - lo)
+    assert lo - width <= g.iters <= hi + width, (g.iters, its)
+    kdiv = min(g.iters, o.iters)
+    for v in variants[:4]:
+        k = min(kdiv, v.iters)
+        d = np.abs(v.history[: k + 1] - o.history[: k + 1]) > 1e-10 * h0
+        if np.any(d):
+            kdiv = min(kdiv, int(np.argmax(d)))
+    assert np.all(np.abs(g.history[: kdiv + 1] - o.history[: kdiv + 1]) <= 1e-8 * h0), kdiv
+    xspread = max(rel(v.x, o.x) for v in variants)
+    assert rel(xg, o.x) <= max(1e-8, 10.0 * xspread), (rel(xg, o.x), xspread)
+
+
+def test_nonconverging_truncated_run_tracks_oracle():
+    """trunc = 1 does not converge on this problem; GPU and oracle follow the
+    same residual history for 400 iterations."""
+    p = W.poisson2d(64, 4, seed=1001)
+    o = O.ecg_solve(p.scipy(), p.part, 4, p.b, tol=1e-8, maxit=401, trunc=1)
+    with ecg.Solver.from_problem(p, trunc=1) as s:
+        g = s.solve(dev(p.b), tol=1e-8, maxit=401)
+    assert o.status == g.status == ecg.ENOCONV
+    assert o.iters == g.iters == 400
+    assert np.all(np.abs(g.history - o.history) <= 1e-10 * o.history[0])
+    assert rel(host(g.x), o.x) <= 1e-10
+
+
+def test_host_and_device_pointers_agree_and_solves_are_deterministic():
+    p = W.blocky_diffusion2d(64, 8, blocks=8, seed=21)
+    with ecg.Solver.from_problem(p, trunc=2) as s:
+        a = s.solve(p.b, tol=1e-8, maxit=2000)
+        b = s.solve(dev(p.b), tol=1e-8, maxit=2000)
+        c = s.solve(dev(p.b), tol=1e-8, maxit=2000)
+    assert a.iters == b.iters == c.iters
+    assert np.array_equal(a.x, host(b.x))
+    assert np.array_equal(host(b.x), host(c.x))
+    assert np.array_equal(b.history, c.history)
+
+
+def test_graph_replay_matches_stream_launches():
+    p = W.blocky_diffusion2d(64, 16, blocks=8, seed=22)
+    with ecg.Solver.from_problem(p, trunc=2, use_graph=True, check_every=5) as s:
+        a = s.solve(dev(p.b), tol=1e-8, maxit=2000)
+    with ecg.Solver.from_problem(p, trunc=2, use_graph=False, check_every=1) as s:
+        b = s.solve(dev(p.b), tol=1e-8, maxit=2000)
+    assert a.iters == b.iters
+    assert np.array_equal(host(a.x), host(b.x))
+
+
+def test_warm_start_and_maxit():
+    p = W.poisson2d(32, 4, seed=23)
+    x0 = p.x_star + 1e-3 * np.random.default_rng(0).standard_normal(p.n)
+    o = O.ecg_solve(p.scipy(), p.part, 4, p.b, x0=x0, maxit=500)
+    with ecg.Solver.from_problem(p) as s:
+        g = s.solve(dev(p.b), x0=dev(x0), maxit=500)
+        assert abs(g.iters - o.iters) <= 1
+        assert rel(host(g.x), p.x_star) < 1e-6
+        g = s.solve(dev(p.b), maxit=6, tol=1e-8)
+        assert g.status == ecg.ENOCONV and g.iters == 5
+        o = O.ecg_solve(p.scipy(), p.part, 4, p.b, maxit=6)
+        assert rel(host(g.x), o.x) < 1e-12
+        g = s.solve(dev(p.b), maxit=1)
+        assert g.status == ecg.ENOCONV and g.iters == 0
+        g = s.solve(dev(np.zeros(p.n)), maxit=50)
+        assert g.status == ecg.OK and g.iters == 0
+        assert np.all(host(g.x) == 0)
+
+
+def test_error_statuses():
+    p = W.random_spd_grid(16, 4, seed=24)
+    bad = p.part.copy()
+    bad[3] = 7
+    with pytest.raises(ecg.EcgError) as e:
+        ecg.Solver(p.rowptr, p.col, p.val, bad, 4)
+    assert e.value.code == ecg.EINVAL
+    with pytest.raises(ecg.EcgError) as e:
+        ecg.Solver(p.rowptr, p.col, p.val, np.zeros(p.n, np.int32), 4)  # empty subdomains
+    assert e.value.code == ecg.EINVAL
+    with pytest.raises(ecg.EcgError) as e:
+        ecg.Solver(p.rowptr, p.col, -p.val, p.part, 4)
+    assert e.value.code == ecg.ENOTSPD
+    with pytest.raises(ecg.EcgError) as e:
+        ecg.Solver(p.rowptr, p.col, p.val, (p.part % 3).astype(np.int32), 3)  # t=3 unsupported
+    assert e.value.code == ecg.EINVAL
+    # breakdown: r_0 vanishes on a whole subdomain (zero column of T^t(r_0))
+    b = p.b.copy()
+    b[p.part == 1] = 0.0
+    o = O.ecg_solve(p.scipy(), p.part, 4, b)
+    with ecg.Solver.from_problem(p) as s:
+        g = s.solve(dev(b))
+    assert o.status == ecg.EBREAKDOWN == g.status
+    assert g.iters == o.iters == 0
+
+
+# ------------------------------------------------- full-size workloads
+
+
+@pytest.fixture(scope="module")
+def diffusion1024():
+    return W.make("diffusion2d_1024_t16")
+
+
+def test_full_size_first_iterations_match_oracle(diffusion1024):
+    """1024^2 heterogeneous diffusion, t = 16, SRE-CG (trunc = 2), in the
+    launch configuration of the benchmark: the first three iterates agree
+    with the oracle's."""
+    p = diffusion1024
+    o = O.ecg_solve(p.scipy(), p.part, 16, p.b, tol=0.0, maxit=4, trunc=2, keep_x=False)
+    with ecg.Solver.from_problem(p, trunc=2) as s:
+        g = s.solve(dev(p.b), tol=0.0, maxit=4)
+    assert g.iters == o.iters == 3
+    assert rel(host(g.x), o.x) < 1e-10
+    assert np.all(np.abs(g.history - o.history) <= 1e-10 * o.history[0])
+
+
+def test_full_size_solve_properties(diffusion1024):
+    """400 iterations on the GPU: the recursive residual history stays
+    finite and matches the true residual b - A x recomputed in numpy from the
+    returned x."""
+    p = diffusion1024
+    with ecg.Solver.from_problem(p, trunc=2) as s:
+        g = s.solve(dev(p.b), tol=0.0, maxit=401)
+    assert g.status == ecg.ENOCONV and g.iters == 400
+    assert np.all(np.isfinite(g.history))
+    x = host(g.x)
+    true = np.linalg.norm(p.b - p.scipy() @ x) / np.linalg.norm(p.b)
+    assert abs(true - g.relres_true) <= 1e-6 * true
+    assert abs(g.relres - true) <= 1e-6 * true
+    assert g.relres < 0.5
