@@ -275,6 +275,22 @@ def test_msdo_variants_match_brute_force_galerkin(variant):
         assert rel(r.xhist[k - 1], BF.to_np(xk)) < 1e-10, k
 
 
+def test_truncated_msdo_equals_truncated_modified_msdo():
+    """With the previous block P_{k-1} inside the window (any trunc >= 1),
+    the term P_{k-1} diag(beta_k) of eq. (pk) is removed exactly by the
+    A-orthogonalisation against the window, so truncated MSDO-CG and
+    truncated modified MSDO-CG build the same iterates in exact arithmetic.
+    (This pins the generator's structure; the value of beta_k itself cannot
+    change the exact iterates and is pinned only by its formula.)"""
+    p = W.random_spd_grid(16, 4, seed=30)
+    A = p.scipy()
+    for trunc in (1, 3):
+        a = O.ecg_solve(A, p.part, 4, p.b, maxit=21, tol=0.0, variant="msdo", trunc=trunc, keep_x=True)
+        b = O.ecg_solve(A, p.part, 4, p.b, maxit=21, tol=0.0, variant="modmsdo", trunc=trunc, keep_x=True)
+        for k in range(20):
+            assert rel(a.xhist[k], b.xhist[k]) < 1e-9, (trunc, k)
+
+
 def test_finite_termination():
     """n = 16, t = 4: K_{4,4} fills R^16, so full SRE-CG2 reaches the exact
     solution in at most n/t = 4 iterations."""
