@@ -178,6 +178,31 @@ int ecg_op_block_update(ecg_ctx* ctx, double* W, double* V, int w, double* x, do
 int ecg_op_msdo_generate(ecg_ctx* ctx, const double* r, const double* P_prev,
                          const double* V_prev, int w, double* P);
 
+/* C = [X_0 ... X_{m-1}]^T Y like ecg_op_tdot, without a context and without
+ * allocating any memory.  The paper has no counterpart to this call; it is
+ * for callers that cannot allocate device memory when they need the
+ * product: services that reserve the whole GPU for their own pool
+ * allocator up front (so a library cudaMalloc would fail or fragment that
+ * pool), and code on a latency-critical path that must not hit
+ * cudaMalloc/cudaFree, which can block or synchronise the device.
+ *
+ * n rows (1 <= n < 2^31); 1 <= m <= 64 blocks X_j of n x wx[j] doubles,
+ * 1 <= wx[j] <= 128 and sum wx <= 256; Y is n x wy with wy in
+ * {1,2,4,8,16,32,64}; C is (sum wx) x wy.  X (a host array of device
+ * pointers), Y and C: X_j, Y, C are device pointers.  stream is a
+ * cudaStream_t (NULL: the default stream).  The call returns after C is
+ * written.  Sizes beyond these limits return ECG_EINVAL.
+ *
+ * Memory: the partial sums (4 MiB), the launch state and the block list
+ * live in static device arrays that every GPU loading this library holds
+ * until the process exits.  The first call on each device looks up their
+ * device addresses; make that first call before any stream capture.  All
+ * calls on a device share the arrays, so calls that overlap on the GPU
+ * (from two host threads or two streams at once) race and corrupt each
+ * other's results: issue them one after another. */
+int ecg_tdot_noalloc(int64_t n, int m, const double* const* X, const int* wx, const double* Y, int wy,
+                     double* C, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

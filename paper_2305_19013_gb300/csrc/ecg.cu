@@ -18,6 +18,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -978,3 +979,118 @@ int ecg_op_msdo_generate(ecg_ctx* c, const double* r, const double* P_prev, cons
 }
 
 }  // extern "C"
+
+// ===================================================== allocation-free call
+//
+// ecg_tdot_noalloc runs the same two kernels as ecg_op_tdot, but its
+// partial sums, launch state and block descriptors live in the file-scope
+// device arrays below instead of memory a context allocates.  Every GPU that
+// loads this library holds these arrays (about 4.2 MB) until the process
+// exits.  Host code must not pass the array names to a kernel: on the host
+// they are stand-ins, not device addresses.  The device addresses come from
+// cudaGetSymbolAddress, once per device, in noalloc_setup().
+
+namespace {
+constexpr int kNoAllocMaxBlocks = 64;     // blocks X_j per call
+constexpr int kNoAllocMaxCols = 256;      // sum of their widths
+constexpr size_t kNoAllocScratch = 1u << 19;  // doubles of partial sums (4 MiB)
+}  // namespace
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+static __device__ __align__(256) DevState g_noalloc_state;
+static __device__ __align__(256) BlockDesc g_noalloc_desc[kNoAllocMaxBlocks];
+
+namespace {
+
+struct NoAllocDevice {
+  double* scratch = nullptr;
+  DevState* st = nullptr;
+  BlockDesc* desc = nullptr;
+  int sms = 0;
+  bool ready = false;
+};
+
+constexpr int kNoAllocMaxDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// Device addresses of the arrays above for the current device, looked up on
+// the first call made on that device.
+int noalloc_setup(NoAllocDevice** out) {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return ECG_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    CK(cudaGetSymbolAddress((void**)&d.scratch, g_noalloc_scratch));
+    CK(cudaGetSymbolAddress((void**)&d.st, g_noalloc_state));
+    CK(cudaGetSymbolAddress((void**)&d.desc, g_noalloc_desc));
+    CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    d.ready = true;
+  }
+  *out = &d;
+  return ECG_OK;
+}
+
+template <int WB>
+void noalloc_launch(KP P, const double* Y, int gxw, int gy, double* C, cudaStream_t s) {
+  k_tdot_window<WB><<<dim3(gxw, gy), kThreads, smem_tdot<WB>(), s>>>(P, WB, Y);
+  k_reduce_C<WB><<<dim3((kChunk * WB + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, WB, gxw, C);
+}
+
+}  // namespace
+
+extern "C" int ecg_tdot_noalloc(int64_t n, int m, const double* const* X, const int* wx, const double* Y, int wy,
+                                double* C, void* stream) {
+  if (n < 1 || n > 0x7fffffff || m < 1 || m > kNoAllocMaxBlocks || !X || !wx || !Y || !C || width_index(wy) < 0)
+    return ECG_EINVAL;
+  BlockDesc hd[kNoAllocMaxBlocks];
+  int off = 0;
+  for (int j = 0; j < m; j++) {
+    if (!X[j] || wx[j] < 1 || wx[j] > 128) return ECG_EINVAL;
+    hd[j].W = const_cast<double*>(X[j]);
+    hd[j].V = const_cast<double*>(X[j]);
+    hd[j].w = wx[j];
+    hd[j].off = off;
+    hd[j].slot = 0;
+    hd[j].pad = 0;
+    off += wx[j];
+  }
+  if (off > kNoAllocMaxCols) return ECG_EINVAL;
+  NoAllocDevice* d = nullptr;
+  int rc = noalloc_setup(&d);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int gy = (off + kChunk - 1) / kChunk;
+  const size_t per_cta = (size_t)kChunk * wy;
+  int gxw = (4 * d->sms + gy - 1) / gy;
+  gxw = std::min<long long>(gxw, (long long)(kNoAllocScratch / (per_cta * gy)));
+  gxw = (int)std::max<long long>(1, std::min<long long>(gxw, (n + 31) / 32));
+  DevState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  hs.width = wy;
+  hs.nq = m;
+  hs.cap = m;
+  hs.k = 1;
+  CK(cudaMemcpyAsync(d->desc, hd, sizeof(BlockDesc) * m, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d->st, &hs, sizeof(hs), cudaMemcpyHostToDevice, s));
+  KP P;
+  std::memset(&P, 0, sizeof(P));
+  P.n = (int)n;
+  P.st = d->st;
+  P.desc = d->desc;
+  P.part_buf = d->scratch;
+  switch (wy) {
+    case 1: noalloc_launch<1>(P, Y, gxw, gy, C, s); break;
+    case 2: noalloc_launch<2>(P, Y, gxw, gy, C, s); break;
+    case 4: noalloc_launch<4>(P, Y, gxw, gy, C, s); break;
+    case 8: noalloc_launch<8>(P, Y, gxw, gy, C, s); break;
+    case 16: noalloc_launch<16>(P, Y, gxw, gy, C, s); break;
+    case 32: noalloc_launch<32>(P, Y, gxw, gy, C, s); break;
+    case 64: noalloc_launch<64>(P, Y, gxw, gy, C, s); break;
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(s));
+  return ECG_OK;
+}

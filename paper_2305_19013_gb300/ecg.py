@@ -84,6 +84,7 @@ SIGNATURES = {
     "ecg_op_a_orthonormalize": (_I, [_P, _P, _P, _I]),
     "ecg_op_block_update": (_I, [_P, _P, _P, _I, _P, _P, C.POINTER(C.c_double)]),
     "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
+    "ecg_tdot_noalloc": (_I, [C.c_int64, _I, _P, _P, _P, _I, _P, _P]),
 }
 
 
@@ -378,3 +379,30 @@ class Solver:
             "ecg_op_msdo_generate",
         )
         return P
+
+
+
+def tdot_noalloc(Xs, Y, out=None, stream=None):
+    """[X_0 .. X_{m-1}]^T Y through ecg_tdot_noalloc, which allocates no
+    device memory of its own (its scratch is a static array inside the
+    library).  Xs: float64 CUDA tensors n x w_j; Y: n x wy (or n); out:
+    a preallocated (sum w_j) x wy tensor, or None to let torch allocate the
+    result here in Python.  stream: a cudaStream_t handle or None.
+    Returns (status, out)."""
+    import torch
+
+    lib = load()
+    if Y.dim() == 1:
+        Y = Y.reshape(-1, 1)
+    n, wy = int(Y.shape[0]), int(Y.shape[1])
+    _check_tensor(Y, (n, wy), "Y")
+    for X in Xs:
+        _check_tensor(X, (n, X.shape[1]), "X")
+    m = len(Xs)
+    ptrs = (C.c_void_p * max(m, 1))(*[X.data_ptr() for X in Xs])
+    ws = (C.c_int * max(m, 1))(*[int(X.shape[1]) for X in Xs])
+    tot = sum(int(X.shape[1]) for X in Xs)
+    if out is None:
+        out = torch.empty((max(tot, 1), wy), dtype=torch.float64, device=Y.device)
+    rc = lib.ecg_tdot_noalloc(n, m, C.cast(ptrs, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(Y), wy, _ptr(out), stream)
+    return rc, out
