@@ -44,6 +44,11 @@ UNIT = "iterations/s"
 WORKLOAD = "diffusion2d_1024_t16"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one launch, from an ncu capture of the kernel
+# as it stands (profiles/k_tdot_window_16_diffusion2d_1024_t16.md): the
+# full-window launch (2 blocks) at n = 1,048,576, t = 16.  Reported only for
+# that kernel and shape; any other shape reports null.
+MEASURED_TRAFFIC = {("cgs_tdot", 16, 2): 402.8e6 + 3.9e6}
 
 
 def peaks():
@@ -278,7 +283,9 @@ def main():
         "peak": FP64_PEAK_TFLOPS,
         "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
-        "traffic": None,
+        "traffic": MEASURED_TRAFFIC.get((dom, 16, args.trunc)),
+        "traffic_note": "DRAM bytes per full-window launch of k_tdot_window<16> from one ncu capture; "
+        "algorithmic bytes per launch 3 x 8 x n x 16 = 402.7 MB read + 2.5 MB of partial sums",
         "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
         "launches": dom_launch,
         "share": dom_ms / tot_ms,

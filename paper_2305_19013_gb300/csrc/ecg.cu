@@ -310,7 +310,7 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
   prof_mark(c, 0);
   for (int pass = 0; pass < 2; pass++) {
     k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), s>>>(P, W, c->d_X);
-    k_reduce_C<W><<<dim3((kChunk * W + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
+    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
     prof_mark(c, 1);
     k_update<W><<<c->gx, kThreads, smem_update<W>(), s>>>(P, W, c->d_X, c->d_C);
     prof_mark(c, 2);
@@ -413,7 +413,7 @@ struct Ops {
   static void tdot(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) {
     int gxw = window_gx(c, gy);
     k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), c->stream>>>(P, gw, B);
-    k_reduce_C<W><<<dim3((kChunk * W + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw, Cout);
+    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw, Cout);
   }
   static void update(ecg_ctx* c, KP P, double* X, const double* Cin) {
     k_update<W><<<c->gx, kThreads, smem_update<W>(), c->stream>>>(P, W, X, Cin);
@@ -1036,7 +1036,7 @@ int noalloc_setup(NoAllocDevice** out) {
 template <int WB>
 void noalloc_launch(KP P, const double* Y, int gxw, int gy, double* C, cudaStream_t s) {
   k_tdot_window<WB><<<dim3(gxw, gy), kThreads, smem_tdot<WB>(), s>>>(P, WB, Y);
-  k_reduce_C<WB><<<dim3((kChunk * WB + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, WB, gxw, C);
+  k_reduce_C<WB><<<dim3((kChunk * WB * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, WB, gxw, C);
 }
 
 }  // namespace

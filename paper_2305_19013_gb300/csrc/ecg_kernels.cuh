@@ -180,6 +180,23 @@ __device__ __forceinline__ void tri_pair2(const double* x, const double* z, cons
   z2 = sz2;
 }
 
+// Sum of in[c * stride + e] over c < count for every e < nent, written to
+// out[e] via `store(e, sum)`: one warp per entry, lanes over c (lane l takes
+// c = l, l+32, ...), then a fixed shuffle tree, so the result does not
+// depend on timing.  All threads of the CTA must call it.
+template <typename Store>
+__device__ __forceinline__ void cta_reduce_partials(const double* in, long long stride, int count, int nent,
+                                                    Store store) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = warp; e < nent; e += nw) {
+    double s = 0.0;
+    for (int c = lane; c < count; c += 32) s += in[(long long)c * stride + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) store(e, s);
+  }
+}
+
 // ----------------------------------------------------------------- setup
 
 // r = b - A x (or r = b when x is null); per-CTA partial ||r||^2 and ||b||^2.
@@ -355,12 +372,16 @@ __global__ void __launch_bounds__(kThreads) k_reduce_C(KP P, int gw, int gxw, do
   const int c0 = blockIdx.y * kChunk;
   if (c0 >= wtot) return;
   const int ncol = min(kChunk, wtot - c0);
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per entry, lanes over the row-CTAs, fixed shuffle tree
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= ncol * WB) return;
   const double* in = P.part_buf + (long long)blockIdx.y * gxw * (kChunk * WB) + e;
   double s = 0.0;
-  for (int c = 0; c < gxw; c++) s += in[(long long)c * (kChunk * WB)];
-  Cout[(long long)c0 * WB + e] = s;
+  for (int c = lane; c < gxw; c += 32) s += in[(long long)c * (kChunk * WB)];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) Cout[(long long)c0 * WB + e] = s;
 }
 
 // X -= [Q_0 .. Q_{nq-1}] C over the whole window (CGS update).
@@ -539,14 +560,12 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
   double* sRi = sR + W * W;
   double* sD = sRi + W * W;
   __shared__ int sflag;
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < gx; c++) s += P.part_buf[(long long)c * E + e];
+  cta_reduce_partials(P.part_buf, E, gx, E, [&](int e, double s) {
     int a, b;
     upper_ab(e, W, a, b);
     sG[a * W + b] = s;
     sG[b * W + a] = s;
-  }
+  });
   __syncthreads();
   if (!cta_cholesky<W>(sG, sR, sD, &sflag)) {
     if (threadIdx.x == 0) {
@@ -680,9 +699,7 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   double* sD = sSi + W * W;
   double* sg = sD + W;
   __shared__ int sflag;
-  for (int e = threadIdx.x; e < E + W; e += blockDim.x) {
-    double s = 0.0;
-    for (int c = 0; c < gx; c++) s += P.part_buf[(long long)c * (E + W) + e];
+  cta_reduce_partials(P.part_buf, E + W, gx, E + W, [&](int e, double s) {
     if (e < E) {
       int a, b;
       upper_ab(e, W, a, b);
@@ -691,7 +708,7 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
     } else {
       sg[e - E] = s;
     }
-  }
+  });
   __syncthreads();
   if (!cta_cholesky<W>(sG, sR, sD, &sflag)) {
     if (threadIdx.x == 0) {
