@@ -197,6 +197,7 @@ def main():
     ap.add_argument("--ortho", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-tol", action="store_true", help="also solve to 1e-8 and report the time")
+    ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -335,13 +336,20 @@ def main():
         },
         "clocks": clk.summary(),
     }
-    if args.time_to_tol:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r = solver.solve(b_dev, tol=1e-8, maxit=200000, x_out=x_dev)
-        torch.cuda.synchronize()
-        line["time_to_tol"] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status, "relres_true": r.relres_true}
     solver.close()
+    if args.time_to_tol:
+        # time to the paper's tolerance, FP64 and FP32 inner solves with FP64 refinement
+        ttt = {}
+        for name, prec in (("fp64", ecg.FP64), ("mixed", ecg.MIXED)):
+            with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
+                                         stream=stream.cuda_stream) as sv:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = sv.solve(b_dev, tol=1e-8, maxit=args.time_to_tol_maxit, x_out=x_dev)
+                torch.cuda.synchronize()
+                ttt[name] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status,
+                             "relres_true": r.relres_true}
+        line["time_to_tol"] = ttt
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_oracle_sample(8, 1, args.trunc)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

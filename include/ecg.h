@@ -44,6 +44,12 @@ extern "C" {
 #define ECG_MSDO 1    /* MSDO-CG, Algorithm 2: P_k = T(r_{k-1}) + P_{k-1} diag(beta_k) */
 #define ECG_MODMSDO 2 /* modified MSDO-CG, Section 2.2: W_k = T(r_{k-1}) */
 
+/* Arithmetic of the iteration. */
+#define ECG_FP64 0  /* every step in FP64: the method as the paper states it */
+#define ECG_MIXED 1 /* FP32 blocks, vectors and matrix values inside an FP64
+                       iterative-refinement loop; t x t factorisations, alpha,
+                       beta and the true residual stay FP64 (not in the paper) */
+
 /* Self A-orthonormalisation of the block (Section 2.1, Section 5). */
 #define ECG_PRE_CHOLQR 0 /* Euclidean CholQR, then A-CholQR (the paper's choice in Section 5) */
 #define ECG_A_CHOLQR 1   /* A-CholQR alone */
@@ -73,6 +79,22 @@ typedef struct {
                         device-side stop flag (default 16; >= 1) */
   int use_graph;     /* 1: replay a captured CUDA graph of check_every
                         iterations when the window size is fixed (default 1) */
+  int precision;     /* ECG_FP64 (default) or ECG_MIXED */
+  double inner_tol;  /* ECG_MIXED: relative residual reduction each FP32
+                        inner solve aims for (default 1e-5; 0 = default) */
+  int restart_every; /* Section 3, restarted methods: j >= 2 restarts at the
+                        iterations k with k mod j == 1 (0: off) */
+  double restart_tol;   /* > 0: restart when |rho_{k-1} - rho_{k-2}| / rho_c
+                           < restart_tol, rho_c the residual norm at the
+                           start of the current cycle (Section 3); 0: off */
+  int restart_max;      /* restarts allowed by restart_tol (0: unlimited;
+                           1: the "restarted once" runs of Tables 8, 9) */
+  int restart_at_switch; /* 1: the flexible switch also restarts (the
+                            restarted flexibly method, Tables 8, 9); needs
+                            switch_tol > 0 */
+  /* A restart discards the stored blocks and takes the next block from
+     [T(r_{k-1})] with the width in force; x_{k-1} is kept and the stopping
+     test keeps comparing with rho_0. */
   void* stream;      /* cudaStream_t for all work; NULL: a stream the
                         context creates */
 } ecg_opts;
@@ -81,6 +103,7 @@ typedef struct {
   int iters;           /* iterations run (k - 1 at exit of the loop) */
   int switch_it;       /* last iteration with t vectors before the switch
                           (k_F of Section 4.1); 0 if no switch */
+  int restarts;        /* restarts performed (#r of Tables 4, 5) */
   int status;          /* same value as the return code */
   int64_t mem_vectors; /* largest number of stored basis vectors, the "mem"
                           of the paper's Tables 4-9 */
@@ -108,6 +131,10 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
 
 /* Solve A x = b (Algorithms 1-4): stop when rho_k <= tol * rho_0 or when
  * k reaches maxit (the paper's k_max: at most maxit - 1 iterations run).
+ * With ECG_MIXED, rho_k is the FP64 true residual b - A x_j after each
+ * refinement step j, maxit bounds the inner iterations of all steps
+ * together, and history holds the inner residual estimates scaled to the
+ * outer residual, with the true residual at every refinement point.
  * b, x0 and x_out are n doubles each, all host or all device pointers (the
  * location is detected; host arrays are copied in and out inside the call).
  * x0 may be NULL (x0 = 0).  res may be NULL.  Returns ECG_OK,

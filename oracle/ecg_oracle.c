@@ -324,7 +324,28 @@ typedef struct {
   int64_t mem_vectors;  /* largest number of stored basis vectors */
   double relres;        /* rho_k / rho_0 (recursively updated residual) */
   double relres_true;   /* ||b - A x|| / ||b|| */
+  int restarts;         /* restarts performed (Section 3) */
 } or_result;
+
+/* Restart controls of Section 3 (all zero: no restart).  every = j >= 2
+ * restarts at the iterations k with k mod j == 1; tol > 0 restarts when
+ * |rho_{k-1} - rho_{k-2}| / rho_c < tol, rho_c the residual norm at the
+ * start of the current cycle (rho_0 for the first cycle; at most max_count
+ * times when max_count > 0); at_switch = 1 restarts at the flexible switch
+ * (the "restarted flexibly" variant of Tables 8 and 9).  Reading: Section 3
+ * writes ||r_0|| in the restart test; taken literally it holds at every
+ * iteration once rho_k < tol * rho_0, which contradicts the 1 to 59
+ * restarts of Tables 4 and 5, so ||r_0|| is read as the initial residual of
+ * the restarted cycle.  A restart discards the
+ * stored blocks and takes the new block from [T(r_{k-1})], as at k = 1, with
+ * the width in force (t, or t/2 after the switch); the stopping test keeps
+ * comparing with rho_0. */
+typedef struct {
+  int every;
+  double tol;
+  int max_count;
+  int at_switch;
+} or_restart;
 
 static double or_norm2(int64_t n, const double* v) {
   double s = 0.0;
@@ -348,10 +369,14 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
                  const int32_t* part, int t, int variant, int trunc, double switch_tol, int ortho,
                  const double* b, const double* x0, double eps, int kmax, double* x,
                  double* history, double* xhist, double* basis, int64_t basis_cap, int* widths,
-                 or_result* res) {
+                 const or_restart* rs, or_result* res) {
   memset(res, 0, sizeof(*res));
+  or_restart rsz;
+  memset(&rsz, 0, sizeof(rsz));
+  if (!rs) rs = &rsz;
   if (n <= 0 || t < 1 || variant < 0 || variant > 2 || trunc < 0 || ortho < 0 || ortho > 1 ||
-      !(eps >= 0.0) || (switch_tol > 0.0 && (t % 2 != 0))) {
+      !(eps >= 0.0) || (switch_tol > 0.0 && (t % 2 != 0)) || rs->every == 1 || rs->every < 0 ||
+      !(rs->tol >= 0.0) || rs->max_count < 0 || (rs->at_switch && !(switch_tol > 0.0))) {
     res->status = OR_EINVAL;
     return OR_EINVAL;
   }
@@ -407,6 +432,8 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
   rho0 = or_norm2(n, r);
   double rho_prev = rho0;
   double tol1 = 1.0;
+  double rtol1 = 1.0;        /* |rho_{k-1} - rho_{k-2}| / rho_c */
+  double rho_cycle = rho0;   /* residual norm at the start of the cycle */
   int counter = 0;
   int width = t;      /* width of the block generated this iteration */
   int wprev = t;      /* width of W_{k-1} / P_{k-1} */
@@ -417,14 +444,32 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
 
   while (rho_prev > eps * rho0 && k < kmax) {
     /* ---- generate the raw block (Algorithms 1-4, lines 3-11) ---- */
+    int do_switch = (k > 1 && switch_tol > 0.0 && tol1 < switch_tol && counter == 0);
+    int do_restart = 0;
+    if (k > 1) {
+      if (rs->every >= 2 && k % rs->every == 1) do_restart = 1;
+      if (rs->tol > 0.0 && rtol1 < rs->tol && (rs->max_count == 0 || res->restarts < rs->max_count))
+        do_restart = 1;
+      if (do_switch && rs->at_switch) do_restart = 1;
+    }
+    if (do_restart) { /* Section 3: discard Q, start again from x_{k-1} */
+      nq = 0;
+      head = 0;
+      res->restarts++;
+      rho_cycle = rho_prev;
+    }
     if (k == 1) {
       width = t;
       or_split(n, part, t, r, W); /* W_1 = [T^t(r_0)] */
-    } else if (switch_tol > 0.0 && tol1 < switch_tol && counter == 0) {
+    } else if (do_switch) {
       width = t / 2;
       or_split_half(n, part, t, r, W); /* W_k = [T^{t/2}(r_{k-1})] */
       counter = 1;
       res->switch_it = k - 1;
+    } else if (do_restart) {
+      width = wprev; /* [T(r_{k-1})] with the width in force */
+      if (width == t) or_split(n, part, t, r, W);
+      else or_split_half(n, part, t, r, W);
     } else {
       width = wprev;
       if (variant == 0) {
@@ -498,6 +543,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
     }
     double rho = or_norm2(n, r);
     tol1 = fabs(rho - rho_prev) / rho0;
+    rtol1 = fabs(rho - rho_prev) / rho_cycle;
     rho_prev = rho;
     if (history) history[k] = rho;
     if (xhist) memcpy(xhist + (int64_t)(k - 1) * n, x, sizeof(double) * (size_t)n);

@@ -59,7 +59,12 @@ class _Res(C.Structure):
         ("mem_vectors", C.c_int64),
         ("relres", C.c_double),
         ("relres_true", C.c_double),
+        ("restarts", C.c_int),
     ]
+
+
+class _Restart(C.Structure):
+    _fields_ = [("every", C.c_int), ("tol", C.c_double), ("max_count", C.c_int), ("at_switch", C.c_int)]
 
 
 _P = C.c_void_p
@@ -88,7 +93,7 @@ def _load():
         "or_cgs2": (_INT, [_I64, _INT, _P, _P, _P, _INT, _P]),
         "or_ecg_solve": (
             _INT,
-            [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _D, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _I64, _P, _P],
+            [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _D, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _I64, _P, _P, _P],
         ),
         "or_cg_solve": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P, _P]),
         "or_mem_flexible": (_I64, [_INT, _INT, _INT]),
@@ -236,6 +241,7 @@ class OracleResult:
     history: np.ndarray
     xhist: np.ndarray | None = None
     basis: list | None = None
+    restarts: int = 0
 
 
 VARIANTS = {"sre": 0, "msdo": 1, "modmsdo": 2}
@@ -255,9 +261,14 @@ def ecg_solve(
     ortho=0,
     keep_x=False,
     keep_basis=False,
+    restart_every=0,
+    restart_tol=0.0,
+    restart_max=0,
+    restart_at_switch=False,
 ):
-    """Enlarged CG (Algorithms 1-4 and their truncated forms).  ``maxit`` is
-    the paper's k_max: at most maxit - 1 iterations run."""
+    """Enlarged CG (Algorithms 1-4, their truncated and restarted forms of
+    Section 3).  ``maxit`` is the paper's k_max: at most maxit - 1
+    iterations run."""
     rp, ci, va, n = _csr(A)
     part = np.ascontiguousarray(part, dtype=np.int32)
     b = _f64(b)
@@ -269,10 +280,11 @@ def ecg_solve(
     basis = np.zeros(cap) if keep_basis else None
     widths = np.zeros(max(maxit, 1), dtype=np.int32)
     res = _Res()
+    rs = _Restart(int(restart_every), float(restart_tol), int(restart_max), 1 if restart_at_switch else 0)
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     _load().or_ecg_solve(
         n, _p(rp), _p(ci), _p(va), _p(part), t, v, trunc, switch_tol, ortho, _p(b), _p(x0a), tol, maxit,
-        _p(x), _p(hist), _p(xh), _p(basis), cap, _p(widths), C.byref(res),
+        _p(x), _p(hist), _p(xh), _p(basis), cap, _p(widths), C.byref(rs), C.byref(res),
     )
     blocks = None
     if keep_basis:
@@ -292,6 +304,7 @@ def ecg_solve(
         history=hist[: res.iters + 1].copy(),
         xhist=None if xh is None else xh[: res.iters].copy(),
         basis=blocks,
+        restarts=res.restarts,
     )
 
 

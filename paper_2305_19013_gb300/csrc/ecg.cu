@@ -11,6 +11,16 @@
 // and when to switch to t/2 vectors; kernels issued after either event
 // return at once.  With a truncated window the group of iterations is
 // captured once as a CUDA graph and replayed.
+//
+// Mixed precision (ECG_MIXED): an FP64 iterative-refinement loop around FP32
+// inner solves.  Each outer step computes the true residual r = b - A x in
+// FP64, runs the same enlarged CG iteration in FP32 on A d = r / ||r|| (the
+// t x t factorisations, alpha and beta stay FP64), and updates
+// x += ||r|| d in FP64.  It stops on the FP64 true residual.  (Keeping the
+// window and only replacing the FP32 residual by the FP64 one was tried and
+// converges far worse: SRE-CG builds new directions from A W, so error
+// components of the replaced residual along directions that left the window
+// are never revisited; a restart rebuilds directions from T^t(r).)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +40,9 @@ using namespace ecg;
 namespace {
 
 constexpr int kWidths[] = {1, 2, 4, 8, 16, 32, 64};
+constexpr double kBreakdownFP64 = 1e-14;  // Cholesky pivot test, FP64 data
+constexpr double kBreakdownFP32 = 1e-8;   // FP32 blocks: Grams carry ~1e-7 rounding
+constexpr int kMaxOuter = 64;             // refinement steps of the mixed method
 
 int width_index(int w) {
   for (int i = 0; i < 7; i++)
@@ -62,8 +75,11 @@ struct ecg_ctx {
   int* d_rowptr = nullptr;
   int* d_col = nullptr;
   double* d_val = nullptr;
-  int* d_pmap = nullptr;  // subdomain of each row
-  double *d_X = nullptr, *d_Y = nullptr, *d_x = nullptr, *d_r = nullptr, *d_b = nullptr;
+  float* d_valf = nullptr;  // mixed precision only
+  int* d_pmap = nullptr;    // subdomain of each row
+  double *d_X = nullptr, *d_Y = nullptr;  // work blocks, n x t doubles (also hold FP32 blocks)
+  double *d_x = nullptr, *d_r = nullptr, *d_b = nullptr;
+  float *d_xf = nullptr, *d_rf = nullptr, *d_bf = nullptr;  // FP32 inner solve vectors
   double *d_sx = nullptr, *d_sr = nullptr;  // scratch x, r for step-level calls
   DevState* d_st = nullptr;
   DevState* d_opst = nullptr;
@@ -71,7 +87,7 @@ struct ecg_ctx {
   int desc_cap = 0;
   BlockDesc* d_opdesc = nullptr;
   int opdesc_cap = 0;
-  double *d_slotW = nullptr, *d_slotV = nullptr;
+  void *d_slotW = nullptr, *d_slotV = nullptr;  // window storage
   int slot_cap = 0;
   double* d_C = nullptr;
   size_t C_cap = 0;
@@ -86,8 +102,8 @@ struct ecg_ctx {
   DevState* h_flags = nullptr;  // pinned, 2 entries
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaGraphExec_t gexec[7] = {};
-  int graph_iters[7] = {};
+  cudaGraphExec_t gexec[14] = {};  // [FP32 ? 7 : 0] + width index
+  int graph_iters[14] = {};
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // profiling event pool
   size_t pev_used = 0;
@@ -97,13 +113,13 @@ struct ecg_ctx {
 
 namespace {
 
-#define CK(call)                                                  \
-  do {                                                            \
-    cudaError_t e_ = (call);                                      \
-    if (e_ != cudaSuccess) {                                      \
-      last_cuda_error() = e_;                                     \
-      return ECG_ECUDA;                                           \
-    }                                                             \
+#define CK(call)                     \
+  do {                               \
+    cudaError_t e_ = (call);         \
+    if (e_ != cudaSuccess) {         \
+      last_cuda_error() = e_;        \
+      return ECG_ECUDA;              \
+    }                                \
   } while (0)
 
 cudaError_t& last_cuda_error() {
@@ -116,6 +132,18 @@ int dalloc(T** p, size_t count) {
   *p = nullptr;
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return (e == cudaErrorMemoryAllocation) ? ECG_ENOMEM : ECG_ECUDA;
+  }
+  return ECG_OK;
+}
+
+int dalloc_bytes(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 1;
+  cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -141,38 +169,47 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <int W>
+template <typename T, int W>
 constexpr size_t smem_tdot() {
-  return sizeof(double) * (Tile<W>::R * kChunk + Tile<W>::R * W);
+  return sizeof(T) * (Tile<W>::R * kChunk + Tile<W>::R * W);
 }
-template <int W>
+template <typename T, int W>
 constexpr size_t smem_update() {
-  return sizeof(double) * (Tile<W>::R * kChunk + kChunk * W);
+  return sizeof(T) * (Tile<W>::R * kChunk + kChunk * W);
 }
-template <int W>
+template <typename T, int W>
 constexpr size_t smem_spmm() {
-  return sizeof(double) * (4 * Tile<W>::R * W + W * W + Tile<W>::R);
+  return sizeof(T) * (4 * Tile<W>::R * W + W * W + Tile<W>::R);
 }
-template <int W>
+template <typename T, int W>
 constexpr size_t smem_final() {
-  return sizeof(double) * (5 * Tile<W>::R * W + W * W + W + Tile<W>::R + kThreads);
+  return sizeof(double) * kThreads + sizeof(T) * (5 * Tile<W>::R * W + W * W + W + Tile<W>::R);
 }
 template <int W>
 constexpr size_t smem_small() {
   return sizeof(double) * (3 * W * W + 2 * W);
 }
 
+template <typename T, int W>
+int set_smem_attrs_t() {
+  CK(cudaFuncSetAttribute(k_tdot_window<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_tdot<T, W>()));
+  CK(cudaFuncSetAttribute(k_update<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_update<T, W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<T, W, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<T, W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<T, W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<T, W>()));
+  CK(cudaFuncSetAttribute(k_spmm_gram<T, W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_spmm<T, W>()));
+  CK(cudaFuncSetAttribute(k_final<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<T, W>()));
+  return ECG_OK;
+}
+
 template <int W>
 int set_smem_attrs() {
-  CK(cudaFuncSetAttribute(k_tdot_window<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_tdot<W>()));
-  CK(cudaFuncSetAttribute(k_update<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_update<W>()));
-  CK(cudaFuncSetAttribute(k_spmm_gram<W, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_spmm<W>()));
-  CK(cudaFuncSetAttribute(k_spmm_gram<W, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_spmm<W>()));
-  CK(cudaFuncSetAttribute(k_spmm_gram<W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)smem_spmm<W>()));
-  CK(cudaFuncSetAttribute(k_final<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<W>()));
+  int rc;
+  if ((rc = set_smem_attrs_t<double, W>())) return rc;
+  if ((rc = set_smem_attrs_t<float, W>())) return rc;
   CK(cudaFuncSetAttribute(k_small_e<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small<W>()));
   CK(cudaFuncSetAttribute(k_small_a<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem_small<W>()));
@@ -192,19 +229,20 @@ int set_all_smem_attrs() {
   return set_smem_attrs<64>();
 }
 
-KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc) {
+KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   KP P;
   P.n = c->n;
   P.t = c->t;
   P.rowptr = c->d_rowptr;
   P.col = c->d_col;
   P.val = c->d_val;
+  P.valf = c->d_valf;
   P.part = c->d_pmap;
   P.X = c->d_X;
   P.Y = c->d_Y;
-  P.x = c->d_x;
-  P.r = c->d_r;
-  P.b = c->d_b;
+  P.x = fp32 ? (void*)c->d_xf : (void*)c->d_x;
+  P.r = fp32 ? (void*)c->d_rf : (void*)c->d_r;
+  P.b = fp32 ? (const void*)c->d_bf : (const void*)c->d_b;
   P.st = st;
   P.desc = desc;
   P.slotW = c->d_slotW;
@@ -237,31 +275,23 @@ void invalidate_graphs(ecg_ctx* c) {
 
 int ensure_part(ecg_ctx* c, size_t doubles) {
   if (doubles <= c->part_cap) return ECG_OK;
+  invalidate_graphs(c);
   dfree(c->d_partial);
   c->part_cap = 0;
   int rc = dalloc(&c->d_partial, doubles);
   if (rc) return rc;
   c->part_cap = doubles;
-  for (auto& g : c->gexec)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
   return ECG_OK;
 }
 
 int ensure_C(ecg_ctx* c, size_t doubles) {
   if (doubles <= c->C_cap) return ECG_OK;
+  invalidate_graphs(c);
   dfree(c->d_C);
   c->C_cap = 0;
   int rc = dalloc(&c->d_C, doubles);
   if (rc) return rc;
   c->C_cap = doubles;
-  for (auto& g : c->gexec)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
   return ECG_OK;
 }
 
@@ -296,56 +326,72 @@ void prof_collect(ecg_ctx* c) {
   c->pev_used = 0;
 }
 
-// One iteration of the kernel chain for block width W.
-template <int W>
+// Reduce the gx per-CTA partials of nent small-matrix entries into
+// P.small[kSmallG ..] (one warp per entry).
+void reduce_small(ecg_ctx* c, const KP& P, int gw, int nent) {
+  const int blocks = (nent * 32 + kThreads - 1) / kThreads;
+  k_reduce_partials<<<blocks, kThreads, 0, c->stream>>>(P.st, gw, P.part_buf, c->gx, nent, P.small + kSmallG);
+}
+
+// One iteration of the kernel chain for scalar type T and block width W.
+template <typename T, int W>
 int enqueue_iteration(ecg_ctx* c, int gy) {
   cudaStream_t s = c->stream;
-  KP P = make_kp(c, c->d_st, c->d_desc);
+  const bool fp32 = sizeof(T) == 4;
+  KP P = make_kp(c, c->d_st, c->d_desc, fp32);
+  T* X = (T*)c->d_X;
+  T* Y = (T*)c->d_Y;
+  T* x = (T*)P.x;
+  T* r = (T*)P.r;
   const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
   const int gxw = window_gx(c, gy);
   const long long tot = (long long)c->n * W;
   const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
   prof_mark(c, -1);
-  k_generate<W><<<ggen, kThreads, 0, s>>>(P, W);
+  k_generate<T, W><<<ggen, kThreads, 0, s>>>(P, W);
   prof_mark(c, 0);
   for (int pass = 0; pass < 2; pass++) {
-    k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), s>>>(P, W, c->d_X);
+    k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(), s>>>(P, W, X);
     k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
     prof_mark(c, 1);
-    k_update<W><<<c->gx, kThreads, smem_update<W>(), s>>>(P, W, c->d_X, c->d_C);
+    k_update<T, W><<<c->gx, kThreads, smem_update<T, W>(), s>>>(P, W, X, c->d_C);
     prof_mark(c, 2);
   }
   if (pre) {
-    k_gram_self<W><<<c->gx, kThreads, 0, s>>>(P, W, c->d_X);
+    k_gram_self<T, W><<<c->gx, kThreads, 0, s>>>(P, W, X);
     prof_mark(c, 3);
+    reduce_small(c, P, W, W * (W + 1) / 2);
     k_small_e<W><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
     prof_mark(c, 4);
-    k_spmm_gram<W, true, true><<<c->gx, kThreads, smem_spmm<W>(), s>>>(P, W, c->d_X, c->d_Y);
+    k_spmm_gram<T, W, true, true><<<c->gx, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
     prof_mark(c, 5);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W);
     k_small_a<W, true><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
   } else {
-    k_spmm_gram<W, true, false><<<c->gx, kThreads, smem_spmm<W>(), s>>>(P, W, c->d_X, c->d_Y);
+    k_spmm_gram<T, W, true, false><<<c->gx, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
     prof_mark(c, 5);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W);
     k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
   }
   prof_mark(c, 6);
-  k_final<W><<<c->gx, kThreads, smem_final<W>(), s>>>(P, W, c->d_X, c->d_Y, nullptr, nullptr, c->d_x, c->d_r);
+  k_final<T, W><<<c->gx, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
   prof_mark(c, 7);
-  k_finish<<<1, kThreads, 0, s>>>(P, W, c->gx);
+  k_finish<<<1, kThreads, 0, s>>>(P, W, c->gx, (int)sizeof(T));
   prof_mark(c, 8);
   CK(cudaGetLastError());
   return ECG_OK;
 }
 
+template <typename T>
 int enqueue_iteration_w(ecg_ctx* c, int W, int gy) {
   switch (W) {
-    case 1: return enqueue_iteration<1>(c, gy);
-    case 2: return enqueue_iteration<2>(c, gy);
-    case 4: return enqueue_iteration<4>(c, gy);
-    case 8: return enqueue_iteration<8>(c, gy);
-    case 16: return enqueue_iteration<16>(c, gy);
-    case 32: return enqueue_iteration<32>(c, gy);
-    case 64: return enqueue_iteration<64>(c, gy);
+    case 1: return enqueue_iteration<T, 1>(c, gy);
+    case 2: return enqueue_iteration<T, 2>(c, gy);
+    case 4: return enqueue_iteration<T, 4>(c, gy);
+    case 8: return enqueue_iteration<T, 8>(c, gy);
+    case 16: return enqueue_iteration<T, 16>(c, gy);
+    case 32: return enqueue_iteration<T, 32>(c, gy);
+    case 64: return enqueue_iteration<T, 64>(c, gy);
   }
   return ECG_EINVAL;
 }
@@ -358,19 +404,20 @@ int window_chunks(const ecg_ctx* c, int cap, int khost) {
 }
 
 // Issue `iters` iterations of width W, through a captured graph when the
-// window size is fixed.
-int enqueue_group(ecg_ctx* c, int W, int iters, int cap, int khost) {
+// window size is fixed and the group is a full one.
+int enqueue_group(ecg_ctx* c, bool fp32, int W, int iters, int cap, int khost) {
   const bool fixed = (c->opts.trunc > 0);
   const int gy = window_chunks(c, cap, fixed ? cap + 1 : khost + iters);
+  auto one = [&]() { return fp32 ? enqueue_iteration_w<float>(c, W, gy) : enqueue_iteration_w<double>(c, W, gy); };
   if (c->opts.use_graph && fixed && !c->profiling && iters == c->opts.check_every) {
-    int wi = width_index(W);
+    const int wi = width_index(W) + (fp32 ? 7 : 0);
     if (!c->gexec[wi] || c->graph_iters[wi] != iters) {
       if (c->gexec[wi]) cudaGraphExecDestroy(c->gexec[wi]);
       c->gexec[wi] = nullptr;
       cudaGraph_t g;
       CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
       int rc = ECG_OK;
-      for (int i = 0; i < iters && rc == ECG_OK; i++) rc = enqueue_iteration_w(c, W, gy);
+      for (int i = 0; i < iters && rc == ECG_OK; i++) rc = one();
       cudaError_t e = cudaStreamEndCapture(c->stream, &g);
       if (rc) return rc;
       CK(e);
@@ -383,9 +430,108 @@ int enqueue_group(ecg_ctx* c, int W, int iters, int cap, int khost) {
     return ECG_OK;
   }
   for (int i = 0; i < iters; i++) {
-    int rc = enqueue_iteration_w(c, W, gy);
+    int rc = one();
     if (rc) return rc;
   }
+  return ECG_OK;
+}
+
+// One enlarged CG solve on the device (Algorithms 1-4): the right-hand side
+// is in b (FP64 d_b or FP32 d_bf) and the initial iterate in x; have_x0 =
+// false means x = 0 (already cleared).  Writes rho_k to history[hist_off+k]
+// and the final state to *fin.
+int run_solve(ecg_ctx* c, bool fp32, int kmax, int cap, double eps, int hist_off, bool have_x0, DevState* fin) {
+  cudaStream_t s = c->stream;
+  const int t = c->t;
+  DevState init;
+  std::memset(&init, 0, sizeof(init));
+  init.kmax = kmax;
+  init.variant = c->opts.variant;
+  init.cap = cap;
+  init.t = t;
+  init.eps = eps;
+  init.switch_tol = c->opts.switch_tol;
+  init.breakdown_ratio = fp32 ? kBreakdownFP32 : kBreakdownFP64;
+  init.hist_off = hist_off;
+  init.restart_every = c->opts.restart_every;
+  init.restart_tol = c->opts.restart_tol;
+  init.restart_max = c->opts.restart_max;
+  init.restart_at_switch = c->opts.restart_at_switch;
+  CK(cudaMemcpyAsync(c->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
+  KP P = make_kp(c, c->d_st, c->d_desc, fp32);
+  prof_mark(c, -1);
+  if (fp32) {
+    k_residual<float><<<c->gx, kThreads, 0, s>>>(P, have_x0 ? c->d_xf : nullptr, c->d_rf, c->d_bf, c->d_rho_part,
+                                                 nullptr);
+  } else {
+    k_residual<double><<<c->gx, kThreads, 0, s>>>(P, have_x0 ? c->d_x : nullptr, c->d_r, c->d_b, c->d_rho_part,
+                                                  nullptr);
+  }
+  k_start<<<1, kThreads, 0, s>>>(P, c->gx);
+  prof_mark(c, 9);
+  CK(cudaGetLastError());
+  // Groups of check_every iterations, polled one group behind.  The host
+  // never issues iteration k_max or later; after the flexible switch it
+  // rewinds its count to the device's k (the group in flight, issued for
+  // the old width, does nothing).
+  const int chunk = c->opts.check_every;
+  int W = t;
+  int khost = 1;  // next iteration the host issues
+  int rc;
+  auto issue = [&](int slot) -> int {
+    const int nit = std::min(chunk, kmax - khost);
+    if (nit > 0) {
+      int r2 = enqueue_group(c, fp32, W, nit, cap, khost);
+      if (r2) return r2;
+      khost += nit;
+    }
+    CK(cudaMemcpyAsync(&c->h_flags[slot], c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev[slot], s));
+    return ECG_OK;
+  };
+  if ((rc = issue(0))) return rc;
+  int cur = 0;
+  long long polls = 0;
+  const long long max_polls = 4LL * ((long long)kmax / chunk + 4);
+  while (true) {
+    if ((rc = issue(1 - cur))) return rc;
+    CK(cudaEventSynchronize(c->ev[cur]));
+    const DevState f = c->h_flags[cur];
+    if (f.stop) break;
+    if (f.width != W) {
+      if (width_index(f.width) < 0) return ECG_ECUDA;
+      W = f.width;
+      khost = f.k;
+    }
+    cur = 1 - cur;
+    if (++polls > max_polls) {  // the device never stopped: not expected
+      cudaStreamSynchronize(s);
+      return ECG_ECUDA;
+    }
+  }
+  CK(cudaMemcpyAsync(fin, c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return ECG_OK;
+}
+
+// ||b - A x||^2 and ||b||^2 in FP64 (r = b - A x kept in d_r).
+int true_residual(ecg_ctx* c, bool keep_r, double* rr, double* bb) {
+  cudaStream_t s = c->stream;
+  KP P = make_kp(c, c->d_st, c->d_desc, false);
+  k_residual<double><<<c->gx, kThreads, 0, s>>>(P, c->d_x, keep_r ? c->d_r : nullptr, c->d_b, c->d_rho_part,
+                                                c->d_bb_part);
+  CK(cudaGetLastError());
+  std::vector<double> prr(c->gx), pbb(c->gx);
+  CK(cudaMemcpyAsync(prr.data(), c->d_rho_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(pbb.data(), c->d_bb_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double a = 0.0, bsum = 0.0;
+  for (int i = 0; i < c->gx; i++) {
+    a += prr[i];
+    bsum += pbb[i];
+  }
+  *rr = a;
+  *bb = bsum;
   return ECG_OK;
 }
 
@@ -396,40 +542,50 @@ int validate_opts(const ecg_opts* o, int t) {
   if (!(o->switch_tol >= 0.0)) return ECG_EINVAL;
   if (o->switch_tol > 0.0 && (t % 2 != 0)) return ECG_EINVAL;
   if (o->check_every < 1) return ECG_EINVAL;
+  if (o->precision < 0 || o->precision > 1) return ECG_EINVAL;
+  if (!(o->inner_tol >= 0.0 && o->inner_tol < 1.0)) return ECG_EINVAL;
+  if (o->restart_every == 1 || o->restart_every < 0) return ECG_EINVAL;
+  if (!(o->restart_tol >= 0.0) || o->restart_max < 0) return ECG_EINVAL;
+  if (o->restart_at_switch && !(o->switch_tol > 0.0)) return ECG_EINVAL;
   return ECG_OK;
 }
 
-// Launch helpers for the step-level entry points (width dispatch).
+// Launch helpers for the step-level entry points (FP64, width dispatch).
 template <int W>
 struct Ops {
   static void generate(ecg_ctx* c, KP P) {
     long long tot = (long long)c->n * W;
     int g = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
-    k_generate<W><<<g, kThreads, 0, c->stream>>>(P, W);
+    k_generate<double, W><<<g, kThreads, 0, c->stream>>>(P, W);
   }
   static void spmm(ecg_ctx* c, KP P, const double* X, double* Y) {
-    k_spmm_gram<W, false, false><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, X, Y);
+    k_spmm_gram<double, W, false, false><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, X, Y);
   }
   static void tdot(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) {
     int gxw = window_gx(c, gy);
-    k_tdot_window<W><<<dim3(gxw, gy), kThreads, smem_tdot<W>(), c->stream>>>(P, gw, B);
-    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw, Cout);
+    k_tdot_window<double, W><<<dim3(gxw, gy), kThreads, smem_tdot<double, W>(), c->stream>>>(P, gw, B);
+    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw,
+                                                                                                   Cout);
   }
   static void update(ecg_ctx* c, KP P, double* X, const double* Cin) {
-    k_update<W><<<c->gx, kThreads, smem_update<W>(), c->stream>>>(P, W, X, Cin);
+    k_update<double, W><<<c->gx, kThreads, smem_update<double, W>(), c->stream>>>(P, W, X, Cin);
   }
   static void orth(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) {
     const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
+    double* Y = c->d_Y;
     if (pre) {
-      k_gram_self<W><<<c->gx, kThreads, 0, c->stream>>>(P, W, Wio);
+      k_gram_self<double, W><<<c->gx, kThreads, 0, c->stream>>>(P, W, Wio);
+      reduce_small(c, P, W, W * (W + 1) / 2);
       k_small_e<W><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
-      k_spmm_gram<W, true, true><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, Wio, c->d_Y);
+      k_spmm_gram<double, W, true, true><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
+      reduce_small(c, P, W, W * (W + 1) / 2 + W);
       k_small_a<W, true><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
     } else {
-      k_spmm_gram<W, true, false><<<c->gx, kThreads, smem_spmm<W>(), c->stream>>>(P, W, Wio, c->d_Y);
+      k_spmm_gram<double, W, true, false><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
+      reduce_small(c, P, W, W * (W + 1) / 2 + W);
       k_small_a<W, false><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
     }
-    k_final<W><<<c->gx, kThreads, smem_final<W>(), c->stream>>>(P, W, Wio, c->d_Y, Wio, V, x, r);
+    k_final<double, W><<<c->gx, kThreads, smem_final<double, W>(), c->stream>>>(P, W, Wio, Y, Wio, V, x, r);
   }
 };
 
@@ -469,6 +625,7 @@ DevState op_state(const ecg_ctx* c, int width, int nq, int gen) {
   s.kmax = 2;
   s.variant = c->opts.variant;
   s.eps = 0.0;
+  s.breakdown_ratio = kBreakdownFP64;
   return s;
 }
 
@@ -520,6 +677,12 @@ void ecg_default_opts(ecg_opts* o) {
   o->ortho = ECG_PRE_CHOLQR;
   o->check_every = 16;
   o->use_graph = 1;
+  o->precision = ECG_FP64;
+  o->inner_tol = 1e-5;
+  o->restart_every = 0;
+  o->restart_tol = 0.0;
+  o->restart_max = 0;
+  o->restart_at_switch = 0;
   o->stream = nullptr;
 }
 
@@ -550,6 +713,7 @@ void ecg_destroy(ecg_ctx* c) {
   dfree(c->d_rowptr);
   dfree(c->d_col);
   dfree(c->d_val);
+  dfree(c->d_valf);
   dfree(c->d_pmap);
   dfree(c->d_partial);
   dfree(c->d_X);
@@ -557,6 +721,9 @@ void ecg_destroy(ecg_ctx* c) {
   dfree(c->d_x);
   dfree(c->d_r);
   dfree(c->d_b);
+  dfree(c->d_xf);
+  dfree(c->d_rf);
+  dfree(c->d_bf);
   dfree(c->d_sx);
   dfree(c->d_sr);
   dfree(c->d_st);
@@ -585,6 +752,7 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
   ecg_opts o;
   ecg_default_opts(&o);
   if (opts) o = *opts;
+  if (o.inner_tol == 0.0) o.inner_tol = 1e-5;
   int rc = validate_opts(&o, t);
   if (rc) return rc;
   int ndev = 0;
@@ -656,6 +824,7 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
   if ((rc = set_all_smem_attrs())) return fail(rc);
   c->gx = std::max(1, std::min(4 * c->num_sms, (n + 31) / 32));
   const size_t nt = (size_t)n * t;
+  const bool mixed = (o.precision == ECG_MIXED);
   if ((rc = dalloc(&c->d_rowptr, (size_t)n + 1)) || (rc = dalloc(&c->d_col, (size_t)nnz)) ||
       (rc = dalloc(&c->d_val, (size_t)nnz)) || (rc = dalloc(&c->d_pmap, (size_t)n)) ||
       (rc = dalloc(&c->d_X, nt)) || (rc = dalloc(&c->d_Y, nt)) || (rc = dalloc(&c->d_x, (size_t)n)) ||
@@ -665,11 +834,19 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
       (rc = dalloc(&c->d_small, (size_t)kSmallSize)) || (rc = dalloc(&c->d_rho_part, (size_t)c->gx)) ||
       (rc = dalloc(&c->d_bb_part, (size_t)c->gx)) || (rc = dalloc(&c->d_beta_part, (size_t)c->gx * 64)))
     return fail(rc);
+  if (mixed && ((rc = dalloc(&c->d_valf, (size_t)nnz)) || (rc = dalloc(&c->d_xf, (size_t)n)) ||
+                (rc = dalloc(&c->d_rf, (size_t)n)) || (rc = dalloc(&c->d_bf, (size_t)n))))
+    return fail(rc);
   if (cudaMemcpy(c->d_rowptr, rp32.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_col, ci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_val, va.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_pmap, pt.data(), sizeof(int) * n, cudaMemcpyHostToDevice) != cudaSuccess)
     return fail(ECG_ECUDA);
+  if (mixed) {
+    k_vals_to_float<<<std::max(1, std::min(8 * c->num_sms, (int)((nnz + 255) / 256))), 256, 0, c->stream>>>(
+        nnz, c->d_val, c->d_valf);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(ECG_ECUDA);
+  }
   if (cudaMemset(c->d_sx, 0, sizeof(double) * n) != cudaSuccess ||
       cudaMemset(c->d_sr, 0, sizeof(double) * n) != cudaSuccess)
     return fail(ECG_ECUDA);
@@ -688,6 +865,8 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
   if (!c || !b || !x_out) return ECG_EINVAL;
   if (!(tol >= 0.0) || maxit < 0) return ECG_EINVAL;
   const int n = c->n, t = c->t;
+  const bool mixed = (c->opts.precision == ECG_MIXED);
+  const size_t elem = mixed ? sizeof(float) : sizeof(double);
   const int kmax = std::max(maxit, 1);
   const int cap = c->opts.trunc > 0 ? c->opts.trunc : std::max(kmax - 1, 1);
   cudaStream_t s = c->stream;
@@ -702,10 +881,10 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
     c->slot_cap = 0;
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
-    double need = 2.0 * (double)cap * (double)n * (double)t * sizeof(double);
+    double need = 2.0 * (double)cap * (double)n * (double)t * (double)elem;
     if (need > 0.92 * (double)freeb) return ECG_ENOMEM;
-    if ((rc = dalloc(&c->d_slotW, (size_t)cap * n * t)) || (rc = dalloc(&c->d_slotV, (size_t)cap * n * t)) ||
-        (rc = dalloc(&c->d_desc, (size_t)cap))) {
+    if ((rc = dalloc_bytes(&c->d_slotW, (size_t)cap * n * t * elem)) ||
+        (rc = dalloc_bytes(&c->d_slotV, (size_t)cap * n * t * elem)) || (rc = dalloc(&c->d_desc, (size_t)cap))) {
       dfree(c->d_slotW);
       dfree(c->d_slotV);
       dfree(c->d_desc);
@@ -737,91 +916,89 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
   } else {
     CK(cudaMemsetAsync(c->d_x, 0, sizeof(double) * n, s));
   }
-  DevState init;
-  std::memset(&init, 0, sizeof(init));
-  init.kmax = kmax;
-  init.variant = c->opts.variant;
-  init.cap = cap;
-  init.t = t;
-  init.eps = tol;
-  init.switch_tol = c->opts.switch_tol;
-  CK(cudaMemcpyAsync(c->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   CK(cudaEventRecord(c->e0, s));
-  KP P = make_kp(c, c->d_st, c->d_desc);
-  prof_mark(c, -1);
-  k_residual<<<c->gx, kThreads, 0, s>>>(P, x0 ? c->d_x : nullptr, c->d_r, c->d_rho_part, nullptr);
-  k_start<<<1, kThreads, 0, s>>>(P, c->gx);
-  prof_mark(c, 9);
-  CK(cudaGetLastError());
-  // ---- iterations: groups of check_every, polled one group behind.  The
-  // host never issues iteration k_max or later; after the flexible switch it
-  // rewinds its count to the device's k (the group in flight, issued for
-  // the old width, does nothing).
-  const int chunk = c->opts.check_every;
-  int W = t;
-  int khost = 1;  // next iteration the host issues
-  auto issue = [&](int slot) -> int {
-    const int nit = std::min(chunk, kmax - khost);
-    if (nit > 0) {
-      int r2 = enqueue_group(c, W, nit, cap, khost);
-      if (r2) return r2;
-      khost += nit;
+  int iters = 0, status = ECG_ENOCONV, switch_it = 0, restarts = 0;
+  long long mem = 0;
+  double relres = 0.0;
+  if (!mixed) {
+    DevState fin;
+    if ((rc = run_solve(c, false, kmax, cap, tol, 0, x0 != nullptr, &fin))) return rc;
+    iters = fin.iters;
+    status = fin.status;
+    switch_it = fin.switch_it;
+    restarts = fin.restarts;
+    mem = fin.mem;
+    relres = fin.rho0 > 0.0 ? fin.rho_prev / fin.rho0 : fin.rho_prev;
+    c->h_hist.assign((size_t)iters + 1, 0.0);
+    CK(cudaMemcpy(c->h_hist.data(), c->d_hist, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));
+  } else {
+    // FP64 iterative refinement around FP32 inner solves.
+    double rr = 0.0, bb = 0.0;
+    if ((rc = true_residual(c, true, &rr, &bb))) return rc;
+    const double rho0 = std::sqrt(rr);
+    double rho = rho0;
+    c->h_hist.assign(1, rho0);
+    const int gcv = std::max(1, std::min(8 * c->num_sms, (n + 255) / 256));
+    for (int outer = 0;; outer++) {
+      if (!(rho > tol * rho0)) {
+        status = ECG_OK;
+        break;
+      }
+      if (iters >= kmax - 1 || outer >= kMaxOuter) {
+        status = ECG_ENOCONV;
+        break;
+      }
+      // the inner solve needs to reach only what is left of the tolerance
+      const double need = 0.1 * tol * rho0 / rho;
+      const double eps_in = std::min(0.5, std::max(c->opts.inner_tol, need));
+      k_to_float_scaled<<<gcv, 256, 0, s>>>(n, c->d_r, c->d_bf, 1.0 / rho);
+      CK(cudaMemsetAsync(c->d_xf, 0, sizeof(float) * n, s));
+      DevState fin;
+      if ((rc = run_solve(c, true, kmax - iters, cap, eps_in, iters, false, &fin))) return rc;
+      const int it = fin.iters;
+      if (fin.mem > mem) mem = fin.mem;
+      if (fin.switch_it > 0 && switch_it == 0) switch_it = iters + fin.switch_it;
+      restarts += fin.restarts;
+      std::vector<double> seg((size_t)it + 1);
+      CK(cudaMemcpy(seg.data(), c->d_hist + iters, sizeof(double) * (it + 1), cudaMemcpyDeviceToHost));
+      if (it == 0) {
+        status = (fin.status == ECG_EBREAKDOWN) ? ECG_EBREAKDOWN : ECG_ENOCONV;
+        break;
+      }
+      k_axpy_from_float<<<gcv, 256, 0, s>>>(n, c->d_x, c->d_xf, rho);
+      CK(cudaGetLastError());
+      if ((rc = true_residual(c, true, &rr, &bb))) return rc;
+      const double rho_new = std::sqrt(rr);
+      for (int k = 1; k <= it; k++) c->h_hist.push_back(rho * seg[k]);
+      c->h_hist.back() = rho_new;  // the true FP64 residual at the refinement point
+      iters += it;
+      if (!(rho_new < rho)) {  // no progress: stagnation of the inner solves
+        rho = rho_new;
+        status = (rho_new > tol * rho0) ? ECG_ENOCONV : ECG_OK;
+        break;
+      }
+      rho = rho_new;
     }
-    CK(cudaMemcpyAsync(&c->h_flags[slot], c->d_st, sizeof(DevState), cudaMemcpyDeviceToHost, s));
-    CK(cudaEventRecord(c->ev[slot], s));
-    return ECG_OK;
-  };
-  if ((rc = issue(0))) return rc;
-  int cur = 0;
-  long long polls = 0;
-  const long long max_polls = 4LL * ((long long)kmax / chunk + 4);
-  while (true) {
-    if ((rc = issue(1 - cur))) return rc;
-    CK(cudaEventSynchronize(c->ev[cur]));
-    const DevState f = c->h_flags[cur];
-    if (f.stop) break;
-    if (f.width != W) {
-      if (width_index(f.width) < 0) return ECG_ECUDA;
-      W = f.width;
-      khost = f.k;
-    }
-    cur = 1 - cur;
-    if (++polls > max_polls) {  // the device never stopped: not expected
-      cudaStreamSynchronize(s);
-      return ECG_ECUDA;
-    }
+    relres = rho0 > 0.0 ? rho / rho0 : rho;
   }
   CK(cudaEventRecord(c->e1, s));
-  // ---- results
-  DevState fin;
-  CK(cudaMemcpyAsync(&fin, c->d_st, sizeof(fin), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   prof_collect(c);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->e0, c->e1);
-  const int iters = fin.iters;
-  c->h_hist.assign((size_t)iters + 1, 0.0);
-  CK(cudaMemcpy(c->h_hist.data(), c->d_hist, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost));
   // true residual ||b - A x|| / ||b||
-  k_residual<<<c->gx, kThreads, 0, s>>>(P, c->d_x, nullptr, c->d_rho_part, c->d_bb_part);
-  CK(cudaGetLastError());
-  std::vector<double> prr(c->gx), pbb(c->gx);
-  CK(cudaMemcpyAsync(prr.data(), c->d_rho_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(pbb.data(), c->d_bb_part, sizeof(double) * c->gx, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(x_out, c->d_x, sizeof(double) * n, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
   double srr = 0.0, sbb = 0.0;
-  for (int i = 0; i < c->gx; i++) {
-    srr += prr[i];
-    sbb += pbb[i];
-  }
-  const int status = fin.status;
+  if ((rc = true_residual(c, false, &srr, &sbb))) return rc;
+  CK(cudaMemcpyAsync(x_out, c->d_x, sizeof(double) * n, dev_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     s));
+  CK(cudaStreamSynchronize(s));
   if (res) {
     res->iters = iters;
-    res->switch_it = fin.switch_it;
+    res->switch_it = switch_it;
+    res->restarts = restarts;
     res->status = status;
-    res->mem_vectors = fin.mem;
-    res->relres = fin.rho0 > 0.0 ? fin.rho_prev / fin.rho0 : fin.rho_prev;
+    res->mem_vectors = mem;
+    res->relres = relres;
     res->relres_true = sbb > 0.0 ? std::sqrt(srr / sbb) : std::sqrt(srr);
     res->device_ms = ms;
     res->history = c->h_hist.data();
@@ -854,7 +1031,7 @@ int ecg_op_split(ecg_ctx* c, const double* r, double* W, int half) {
   const int w = half ? c->t / 2 : c->t;
   int rc;
   if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   P.X = W;
   P.r = const_cast<double*>(r);
   if ((rc = dispatch_w<RunGenerate>(w, c, P))) return rc;
@@ -865,7 +1042,7 @@ int ecg_op_spmm(ecg_ctx* c, const double* X, double* Y, int w) {
   if (!c || !X || !Y || width_index(w) < 0) return ECG_EINVAL;
   int rc;
   if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   if ((rc = dispatch_w<RunSpmm>(w, c, P, X, Y))) return rc;
   return finish_op(c, nullptr);
 }
@@ -889,7 +1066,7 @@ int ecg_op_tdot(ecg_ctx* c, int m, const double* const* X, const int* wx, const 
   if ((rc = ensure_part(c, (size_t)gy * window_gx(c, gy) * kChunk * wy))) return rc;
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, wy, m, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   if ((rc = dispatch_w<RunTdot>(wy, c, P, wy, Y, gy, C))) return rc;
   return finish_op(c, nullptr);
 }
@@ -915,7 +1092,7 @@ int ecg_op_cgs2(ecg_ctx* c, int m, const double* const* Q, const double* const* 
   if ((rc = ensure_C(c, (size_t)gy * kChunk * w))) return rc;
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, w, m, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   for (int pass = 0; pass < 2; pass++) {
     if ((rc = dispatch_w<RunTdot>(w, c, P, w, (const double*)W, gy, c->d_C))) return rc;
     if ((rc = dispatch_w<RunUpdate>(w, c, P, W, (const double*)c->d_C))) return rc;
@@ -928,7 +1105,7 @@ static int op_orth(ecg_ctx* c, double* W, double* V, int w, double* x, double* r
   int rc;
   if ((rc = ensure_part(c, (size_t)c->gx * (w * (w + 1) / 2 + w)))) return rc;
   if ((rc = put_op_state(c, op_state(c, w, 0, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   P.r = r;
   P.want_beta = 0;
   if ((rc = dispatch_w<RunOrth>(w, c, P, W, V, x, r))) return rc;
@@ -968,7 +1145,7 @@ int ecg_op_msdo_generate(ecg_ctx* c, const double* r, const double* P_prev, cons
   if ((rc = ensure_part(c, (size_t)window_gx(c, 1) * kChunk))) return rc;
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, 1, 1, GEN_SPLIT)))) return rc;
-  KP P = make_kp(c, c->d_opst, c->d_opdesc);
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   if ((rc = dispatch_w<RunTdot>(1, c, P, 1, r, 1, c->d_small + kSmallG))) return rc;
   k_neg_copy<<<1, 64, 0, c->stream>>>(c->d_small + kSmallG, c->d_small + kSmallBe, w);
   if ((rc = put_op_state(c, op_state(c, w, 1, GEN_MSDO)))) return rc;
@@ -991,8 +1168,8 @@ int ecg_op_msdo_generate(ecg_ctx* c, const double* r, const double* P_prev, cons
 // cudaGetSymbolAddress, once per device, in noalloc_setup().
 
 namespace {
-constexpr int kNoAllocMaxBlocks = 64;     // blocks X_j per call
-constexpr int kNoAllocMaxCols = 256;      // sum of their widths
+constexpr int kNoAllocMaxBlocks = 64;         // blocks X_j per call
+constexpr int kNoAllocMaxCols = 256;          // sum of their widths
 constexpr size_t kNoAllocScratch = 1u << 19;  // doubles of partial sums (4 MiB)
 }  // namespace
 
@@ -1035,7 +1212,7 @@ int noalloc_setup(NoAllocDevice** out) {
 
 template <int WB>
 void noalloc_launch(KP P, const double* Y, int gxw, int gy, double* C, cudaStream_t s) {
-  k_tdot_window<WB><<<dim3(gxw, gy), kThreads, smem_tdot<WB>(), s>>>(P, WB, Y);
+  k_tdot_window<double, WB><<<dim3(gxw, gy), kThreads, smem_tdot<double, WB>(), s>>>(P, WB, Y);
   k_reduce_C<WB><<<dim3((kChunk * WB * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, WB, gxw, C);
 }
 

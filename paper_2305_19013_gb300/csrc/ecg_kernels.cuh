@@ -1,4 +1,4 @@
-// ecg_kernels.cuh -- sm_103a kernels of the enlarged CG iteration (FP64).
+// ecg_kernels.cuh -- sm_103a kernels of the enlarged CG iteration.
 //
 // Method: S. Moufawad, "Flexibly Enlarged Conjugate Gradient methods"
 // (arXiv 2305.19013), Algorithms 1-4.  One iteration k is the kernel chain
@@ -22,14 +22,20 @@
 // width W (which happens right after the flexible switch, until the host
 // moves to the t/2 kernels).
 //
-// GB300 has about 1.2 TFLOP/s of FP64 against 6.7 TB/s of HBM, so every
-// n x t block pass here is bound by FP64 FMA issue, not by memory.  The
-// kernels therefore stage row tiles in shared memory and give each thread
-// distinct output entries, so that every DFMA issued is a useful one
-// (symmetric Grams compute their upper triangle only).  Reductions over
-// rows are two-stage and fixed-order: each CTA writes its partial sums and
-// a second kernel adds them in CTA order, so repeated solves are bitwise
-// identical.
+// The block kernels are templates on the scalar type T of the n x t blocks,
+// the vectors x, r, b and the matrix values: double for the FP64 method,
+// float for the inner solves of the mixed-precision method.  Everything
+// small stays FP64 in both: per-CTA partial sums, the t x t Gram matrices,
+// their Cholesky factors and inverses, alpha, beta and the residual norms.
+//
+// GB300 has about 1.2 TFLOP/s of FP64 against 6.7 TB/s of HBM, so with
+// T = double every n x t block pass is bound by FP64 FMA issue, not by
+// memory.  The kernels therefore stage row tiles in shared memory and give
+// each thread distinct output entries, so that every FMA issued is a useful
+// one (symmetric Grams compute their upper triangle only).  With T = float
+// the same passes are bound by HBM.  Reductions over rows are two-stage and
+// fixed-order: each CTA writes its partial sums and a second kernel adds
+// them in CTA order, so repeated solves are bitwise identical.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -38,17 +44,16 @@ namespace ecg {
 
 constexpr int kThreads = 256;
 constexpr int kChunk = 64;  // window columns per CGS chunk
-constexpr double kBreakdownRatio = 1e-14;
 
 enum Gen { GEN_SPLIT = 0, GEN_SRE = 1, GEN_MSDO = 2 };
 enum Status { ST_OK = 0, ST_ENOCONV = 1, ST_EBREAKDOWN = -4 };
 
 struct BlockDesc {
-  double* W;  // A-orthonormal block W_j (n x w)
-  double* V;  // A W_j (n x w)
-  int w;      // width
-  int off;    // first column of this block in the concatenated window
-  int slot;   // storage slot index
+  void* W;  // A-orthonormal block W_j (n x w, scalar type of the solve)
+  void* V;  // A W_j (n x w)
+  int w;    // width
+  int off;  // first column of this block in the concatenated window
+  int slot; // storage slot index
   int pad;
 };
 
@@ -67,8 +72,18 @@ struct DevState {
   int cap;        // window capacity (blocks)
   int t;
   int next_slot;  // storage slot for the block of iteration k
+  int hist_off;   // history index of rho_0 for this solve
+  int restarts;   // restarts performed (Section 3)
+  int restart_every;      // j >= 2: restart at k with k mod j == 1 (0: off)
+  int restart_max;        // restarts allowed by restart_tol (0: unlimited)
+  int restart_at_switch;  // 1: the flexible switch also restarts
+  int pad1;
+  double restart_tol;     // > 0: restart when rtol1 < restart_tol
+  double rho_cycle;       // residual norm at the start of the current cycle
+  double rtol1;           // |rho_k - rho_{k-1}| / rho_cycle
   long long mem;  // largest number of stored basis vectors
   double eps, switch_tol;
+  double breakdown_ratio;  // Cholesky pivot test: pivot > ratio * diagonal
   double rho0, rho_prev, tol1, rho;
 };
 
@@ -84,25 +99,64 @@ struct KP {
   int n, t;
   const int* rowptr;
   const int* col;
-  const double* val;
+  const double* val;   // matrix values, FP64
+  const float* valf;   // matrix values rounded to FP32 (mixed precision)
   const int* part;
-  double* X;  // raw block of the iteration (n x W)
-  double* Y;  // A X (n x W)
-  double* x;
-  double* r;
-  const double* b;
+  void* X;  // raw block of the iteration (n x W)
+  void* Y;  // A X (n x W)
+  void* x;
+  void* r;
+  const void* b;
   DevState* st;
   BlockDesc* desc;   // window, oldest first
-  double* slotW;     // window storage, slot s at slotW + s * slot_stride
-  double* slotV;
+  void* slotW;       // window storage, slot s at slotW + s * slot_stride elements
+  void* slotV;
   long long slot_stride;
   double* C;         // CGS coefficients, (window columns) x W
   double* part_buf;  // per-CTA partial sums
   double* small;     // small matrices, see kSmall*
-  double* history;   // rho_k, k = 0..kmax-1
+  double* history;   // rho_k at history[hist_off + k]
   double* rho_part;  // per-CTA partial ||r||^2
   double* beta_part; // per-CTA partial V^T r (64 per CTA)
   int want_beta;     // accumulate beta partials in k_final (MSDO-CG)
+};
+
+template <typename T>
+__device__ __forceinline__ const T* values(const KP& P);
+template <>
+__device__ __forceinline__ const double* values<double>(const KP& P) {
+  return P.val;
+}
+template <>
+__device__ __forceinline__ const float* values<float>(const KP& P) {
+  return P.valf;
+}
+
+// Sum over the rows of one CTA.  FP64 accumulates one FMA chain across all
+// tiles.  FP32 sums each row tile in FP32 and adds the tile sums into an
+// FP32 (hi, lo) pair with an exact two-sum, so the long accumulation over a
+// CTA's rows loses no more than one FP32 rounding per tile.
+template <typename T>
+struct RowAcc;
+template <>
+struct RowAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ double begin() const { return s; }
+  __device__ __forceinline__ void end(double v) { s = v; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct RowAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ float begin() const { return 0.f; }
+  __device__ __forceinline__ void end(float v) {
+    const float s = hi + v;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (v - bp);
+    hi = s;
+    lo += err;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
 };
 
 __device__ __forceinline__ bool skip(const DevState* st, int w) {
@@ -154,18 +208,18 @@ __device__ __forceinline__ void upper_ab(int e, int w, int& a, int& b) {
 // y2 = sum_{a<=b2} x_a U_{a,b2}.  Every pair costs W+1 FMAs per input row, so
 // all lanes of a warp run the same trip count (one column per lane would
 // leave lane b idle for W-1-b of the W steps).  Two rows (x, z) share U.
-template <int W>
-__device__ __forceinline__ void tri_pair2(const double* x, const double* z, const double* U, int bp,
-                                          double& x1, double& x2, double& z1, double& z2) {
+template <typename T, int W>
+__device__ __forceinline__ void tri_pair2(const T* x, const T* z, const T* U, int bp, T& x1, T& x2, T& z1,
+                                          T& z2) {
   const int b1 = bp, b2 = W - 1 - bp;
-  double sx1 = 0.0, sx2 = 0.0, sz1 = 0.0, sz2 = 0.0;
+  T sx1 = 0, sx2 = 0, sz1 = 0, sz2 = 0;
 #pragma unroll 4
   for (int j = 0; j <= W; j++) {
     const bool first = (j <= b1);
     const int a = first ? j : j - b1 - 1;
-    const double u = U[a * W + (first ? b1 : b2)];
-    const double vx = fma(x[a], u, first ? sx1 : sx2);
-    const double vz = fma(z[a], u, first ? sz1 : sz2);
+    const T u = U[a * W + (first ? b1 : b2)];
+    const T vx = fma(x[a], u, first ? sx1 : sx2);
+    const T vz = fma(z[a], u, first ? sz1 : sz2);
     if (first) {
       sx1 = vx;
       sz1 = vz;
@@ -197,25 +251,60 @@ __device__ __forceinline__ void cta_reduce_partials(const double* in, long long 
   }
 }
 
+// Sum of the per-CTA partials in[c * nent + e], c < count, into out[e], one
+// warp per entry across as many CTAs as needed (lanes split c; each lane
+// keeps 8 loads in flight; a fixed shuffle tree adds the lanes, so the result
+// is the same on every run).  Turns the ~600-deep dependent load chain a
+// single CTA would walk into a few memory round trips.
+__device__ __forceinline__ double warp_sum_partials(const double* in, long long stride, int count, int lane) {
+  double s = 0.0;
+  for (int c0 = lane; c0 < count; c0 += 32 * 8) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+      const int c = c0 + 32 * u;
+      v[u] = (c < count) ? in[(long long)c * stride] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; u++) s += v[u];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_reduce_partials(const DevState* st, int gw, const double* in,
+                                                               int count, int nent, double* out) {
+  if (skip(st, gw)) return;
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= nent) return;
+  const double s = warp_sum_partials(in + e, nent, count, lane);
+  if (lane == 0) out[e] = s;
+}
+
 // ----------------------------------------------------------------- setup
 
-// r = b - A x (or r = b when x is null); per-CTA partial ||r||^2 and ||b||^2.
-__global__ void __launch_bounds__(kThreads) k_residual(KP P, const double* x, double* rout,
-                                                        double* part_rr, double* part_bb) {
+// r = b - A x (or r = b when x is null); per-CTA partial ||r||^2 and ||b||^2
+// (each row's square in FP64).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_residual(KP P, const T* x, T* rout, const T* b, double* part_rr,
+                                                        double* part_bb) {
   __shared__ double sbuf[kThreads];
+  const T* val = values<T>(P);
   int r0, r1;
   cta_rows(P.n, r0, r1);
   double rr = 0.0, bb = 0.0;
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double y = 0.0;
+    T y = 0;
     if (x) {
-      for (int p = P.rowptr[i]; p < P.rowptr[i + 1]; p++) y += P.val[p] * x[P.col[p]];
+      for (int p = P.rowptr[i]; p < P.rowptr[i + 1]; p++) y += val[p] * x[P.col[p]];
     }
-    double bi = P.b[i];
-    double ri = bi - y;
+    const T bi = b[i];
+    const T ri = bi - y;
     if (rout) rout[i] = ri;
-    rr += ri * ri;
-    bb += bi * bi;
+    rr += (double)ri * (double)ri;
+    bb += (double)bi * (double)bi;
   }
   rr = block_sum(rr, sbuf);
   bb = block_sum(bb, sbuf);
@@ -238,6 +327,8 @@ __global__ void k_start(KP P, int nparts) {
     st->rho_prev = rho0;
     st->rho = rho0;
     st->tol1 = 1.0;
+    st->rtol1 = 1.0;
+    st->rho_cycle = rho0;
     st->k = 1;
     st->width = st->t;
     st->gen = GEN_SPLIT;
@@ -247,9 +338,10 @@ __global__ void k_start(KP P, int nparts) {
     st->iters = 0;
     st->next_slot = 0;
     st->mem = 0;
+    st->restarts = 0;
     st->stop = 0;
     st->status = ST_ENOCONV;
-    P.history[0] = rho0;
+    P.history[st->hist_off] = rho0;
     if (!(rho0 > st->eps * rho0)) {
       st->stop = 1;
       st->status = ST_OK;
@@ -263,7 +355,7 @@ __global__ void k_start(KP P, int nparts) {
 // ------------------------------------------------------------ generation
 
 // Raw block of iteration k (Algorithms 1-4, lines 3-11).
-template <int W>
+template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_generate(KP P, int gw) {
   const DevState* st = P.st;
   if (skip(st, gw)) return;
@@ -271,31 +363,33 @@ __global__ void __launch_bounds__(kThreads) k_generate(KP P, int gw) {
   const bool half = (W != P.t);  // after the switch: [T^{t/2}(r)]
   const long long total = (long long)P.n * W;
   const BlockDesc* last = (st->nq > 0) ? &P.desc[st->nq - 1] : nullptr;
-  const double* vprev = last ? last->V : nullptr;
-  const double* pprev = last ? last->W : nullptr;
+  const T* vprev = last ? (const T*)last->V : nullptr;
+  const T* pprev = last ? (const T*)last->W : nullptr;
   const double* beta = P.small + kSmallBe;
+  const T* r = (const T*)P.r;
+  T* X = (T*)P.X;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e / W);
     int j = (int)(e % W);
-    double v;
+    T v;
     if (gen == GEN_SRE) {
       v = vprev[e];  // W_k = A W_{k-1}
     } else {
       int pj = half ? (P.part[i] >> 1) : P.part[i];
-      v = (j == pj) ? P.r[i] : 0.0;
-      if (gen == GEN_MSDO) v += pprev[e] * beta[j];
+      v = (j == pj) ? r[i] : T(0);
+      if (gen == GEN_MSDO) v += pprev[e] * (T)beta[j];
     }
-    P.X[e] = v;
+    X[e] = v;
   }
 }
 
 // ------------------------------------------------------------------ CGS2
 
 // Partial sums of C = [V_0 .. V_{nq-1}]^T B over this CTA's rows, for the 64
-// window columns of chunk blockIdx.y.  B is n x WB (P.X).
-template <int WB>
-__global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const double* B) {
+// window columns of chunk blockIdx.y.  B is n x WB.
+template <typename T, int WB>
+__global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T* B) {
   constexpr int R = Tile<WB>::R;
   constexpr int EPT = (kChunk * WB + kThreads - 1) / kThreads;
   const DevState* st = P.st;
@@ -307,11 +401,11 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const do
   const int c0 = blockIdx.y * kChunk;
   if (c0 >= wtot) return;
   const int ncol = min(kChunk, wtot - c0);
-  __shared__ const double* cptr[kChunk];
+  __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
-  extern __shared__ double smem[];
-  double* sA = smem;             // R x kChunk
-  double* sB = sA + R * kChunk;  // R x WB
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sA = (T*)smem_raw;          // R x kChunk
+  T* sB = sA + R * kChunk;       // R x WB
   if (threadIdx.x < ncol) {
     int cg = c0 + threadIdx.x;
     int lo = 0, hi = nq - 1;
@@ -320,13 +414,11 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const do
       if (D[mid].off <= cg) lo = mid;
       else hi = mid - 1;
     }
-    cptr[threadIdx.x] = D[lo].V + (cg - D[lo].off);
+    cptr[threadIdx.x] = (const T*)D[lo].V + (cg - D[lo].off);
     cstr[threadIdx.x] = D[lo].w;
   }
   const int E = ncol * WB;
-  double acc[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; q++) acc[q] = 0.0;
+  RowAcc<T> acc[EPT];
   int r0, r1;
   cta_rows(P.n, r0, r1);
   __syncthreads();
@@ -334,11 +426,11 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const do
     const int nr = min(R, r1 - row0);
     for (int idx = threadIdx.x; idx < R * ncol; idx += blockDim.x) {
       int r = idx / ncol, cc = idx - r * ncol;
-      sA[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : 0.0;
+      sA[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
     }
     for (int idx = threadIdx.x; idx < R * WB; idx += blockDim.x) {
       int r = idx / WB;
-      sB[idx] = (r < nr) ? B[(long long)row0 * WB + idx] : 0.0;
+      sB[idx] = (r < nr) ? B[(long long)row0 * WB + idx] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -346,9 +438,9 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const do
       int e = threadIdx.x + q * kThreads;
       if (e < E) {
         int a = e / WB, bb = e - a * WB;
-        double s = acc[q];
+        T s = acc[q].begin();
         for (int r = 0; r < nr; r++) s = fma(sA[r * kChunk + a], sB[r * WB + bb], s);
-        acc[q] = s;
+        acc[q].end(s);
       }
     }
     __syncthreads();
@@ -357,7 +449,7 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const do
 #pragma unroll
   for (int q = 0; q < EPT; q++) {
     int e = threadIdx.x + q * kThreads;
-    if (e < E) out[e] = acc[q];
+    if (e < E) out[e] = acc[q].value();
   }
 }
 
@@ -377,16 +469,13 @@ __global__ void __launch_bounds__(kThreads) k_reduce_C(KP P, int gw, int gxw, do
   const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= ncol * WB) return;
   const double* in = P.part_buf + (long long)blockIdx.y * gxw * (kChunk * WB) + e;
-  double s = 0.0;
-  for (int c = lane; c < gxw; c += 32) s += in[(long long)c * (kChunk * WB)];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  const double s = warp_sum_partials(in, kChunk * WB, gxw, lane);
   if (lane == 0) Cout[(long long)c0 * WB + e] = s;
 }
 
 // X -= [Q_0 .. Q_{nq-1}] C over the whole window (CGS update).
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, double* Xio, const double* Cin) {
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const double* Cin) {
   constexpr int R = Tile<W>::R;
   constexpr int EPT = (R * W + kThreads - 1) / kThreads;
   const DevState* st = P.st;
@@ -396,21 +485,21 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, double* Xio, 
   const BlockDesc* D = P.desc;
   const int wtot = D[nq - 1].off + D[nq - 1].w;
   const int nch = (wtot + kChunk - 1) / kChunk;
-  __shared__ const double* cptr[kChunk];
+  __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
-  extern __shared__ double smem[];
-  double* sQ = smem;                 // R x kChunk
-  double* sC = sQ + R * kChunk;      // kChunk x W
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sQ = (T*)smem_raw;          // R x kChunk
+  T* sC = sQ + R * kChunk;       // kChunk x W
   int r0, r1;
   cta_rows(P.n, r0, r1);
   for (int row0 = r0; row0 < r1; row0 += R) {
     const int nr = min(R, r1 - row0);
-    double acc[EPT];
+    T acc[EPT];
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
       int e = threadIdx.x + q * kThreads;
       int r = e / W;
-      acc[q] = (e < R * W && r < nr) ? Xio[(long long)row0 * W + e] : 0.0;
+      acc[q] = (e < R * W && r < nr) ? Xio[(long long)row0 * W + e] : T(0);
     }
     for (int ch = 0; ch < nch; ch++) {
       const int c0 = ch * kChunk;
@@ -424,15 +513,14 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, double* Xio, 
           if (D[mid].off <= cg) lo = mid;
           else hi = mid - 1;
         }
-        cptr[threadIdx.x] = D[lo].W + (cg - D[lo].off);
+        cptr[threadIdx.x] = (const T*)D[lo].W + (cg - D[lo].off);
         cstr[threadIdx.x] = D[lo].w;
       }
-      for (int idx = threadIdx.x; idx < ncol * W; idx += blockDim.x)
-        sC[idx] = Cin[(long long)c0 * W + idx];
+      for (int idx = threadIdx.x; idx < ncol * W; idx += blockDim.x) sC[idx] = (T)Cin[(long long)c0 * W + idx];
       __syncthreads();
       for (int idx = threadIdx.x; idx < R * ncol; idx += blockDim.x) {
         int r = idx / ncol, cc = idx - r * ncol;
-        sQ[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : 0.0;
+        sQ[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -440,7 +528,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, double* Xio, 
         int e = threadIdx.x + q * kThreads;
         if (e < R * W) {
           int r = e / W, bb = e - r * W;
-          double s = acc[q];
+          T s = acc[q];
           for (int a = 0; a < ncol; a++) s = fma(-sQ[r * kChunk + a], sC[a * W + bb], s);
           acc[q] = s;
         }
@@ -459,14 +547,14 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, double* Xio, 
 // ------------------------------------------------------- orthonormalisation
 
 // Partial upper-triangle Gram X^T X (Euclidean step of Pre-CholQR).
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const double* Xin) {
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* Xin) {
   constexpr int R = Tile<W>::R;
   constexpr int E = W * (W + 1) / 2;
   constexpr int EPT = (E + kThreads - 1) / kThreads;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
-  __shared__ double sB[R * W];
+  __shared__ T sB[R * W];
   int ea[EPT], eb[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; q++) {
@@ -474,22 +562,20 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const doub
     if (e < E) upper_ab(e, W, ea[q], eb[q]);
     else ea[q] = eb[q] = 0;
   }
-  double acc[EPT];
-#pragma unroll
-  for (int q = 0; q < EPT; q++) acc[q] = 0.0;
+  RowAcc<T> acc[EPT];
   int r0, r1;
   cta_rows(P.n, r0, r1);
   for (int row0 = r0; row0 < r1; row0 += R) {
     const int nr = min(R, r1 - row0);
     for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x)
-      sB[idx] = (idx / W < nr) ? Xin[(long long)row0 * W + idx] : 0.0;
+      sB[idx] = (idx / W < nr) ? Xin[(long long)row0 * W + idx] : T(0);
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
       if (threadIdx.x + q * kThreads < E) {
-        double s = acc[q];
+        T s = acc[q].begin();
         for (int r = 0; r < nr; r++) s = fma(sB[r * W + ea[q]], sB[r * W + eb[q]], s);
-        acc[q] = s;
+        acc[q].end(s);
       }
     }
     __syncthreads();
@@ -498,15 +584,15 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const doub
 #pragma unroll
   for (int q = 0; q < EPT; q++) {
     int e = threadIdx.x + q * kThreads;
-    if (e < E) out[e] = acc[q];
+    if (e < E) out[e] = acc[q].value();
   }
 }
 
 // Cholesky G = R^T R of the W x W matrix in sG (full symmetric storage) into
-// sR (upper), with the pivot test pivot <= 1e-14 * G_jj.  Returns false on
+// sR (upper), with the pivot test pivot <= ratio * G_jj.  Returns false on
 // breakdown.  sG is destroyed.  All threads of the CTA must call it.
 template <int W>
-__device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag) {
+__device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag, double ratio) {
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) sR[i] = 0.0;
   for (int i = threadIdx.x; i < W; i += blockDim.x) sD[i] = sG[i * W + i];
   if (threadIdx.x == 0) *sflag = 0;
@@ -514,7 +600,7 @@ __device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag) {
   for (int j = 0; j < W; j++) {
     if (threadIdx.x == 0) {
       double d = sG[j * W + j];
-      if (!(d > kBreakdownRatio * sD[j]) || !isfinite(d)) *sflag = 1;
+      if (!(d > ratio * sD[j]) || !isfinite(d)) *sflag = 1;
       else sR[j * W + j] = sqrt(d);
     }
     __syncthreads();
@@ -554,20 +640,23 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
   constexpr int E = W * (W + 1) / 2;
   DevState* st = P.st;
   if (skip(st, gw)) return;
-  extern __shared__ double smem[];
-  double* sG = smem;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sG = (double*)smem_raw;
   double* sR = sG + W * W;
   double* sRi = sR + W * W;
   double* sD = sRi + W * W;
   __shared__ int sflag;
-  cta_reduce_partials(P.part_buf, E, gx, E, [&](int e, double s) {
+  const double* red = P.small + kSmallG;  // X^T X reduced by k_reduce_partials
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
     int a, b;
     upper_ab(e, W, a, b);
+    const double s = red[e];
     sG[a * W + b] = s;
     sG[b * W + a] = s;
-  });
+  }
+  (void)gx;
   __syncthreads();
-  if (!cta_cholesky<W>(sG, sR, sD, &sflag)) {
+  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
@@ -580,34 +669,35 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
 
 // Y = A X; with GRAM, per-CTA partials of G = q^T (A q) (upper) and
 // g = q^T r, q = X R_e^{-1} when PRE (else q = X).
-template <int W, bool GRAM, bool PRE>
-__global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const double* Xin, double* Yout) {
+template <typename T, int W, bool GRAM, bool PRE>
+__global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const T* Xin, T* Yout) {
   constexpr int R = Tile<W>::R;
   constexpr int E = W * (W + 1) / 2;
   constexpr int EPT = (E + kThreads - 1) / kThreads;
   constexpr int EPT2 = (R * W + kThreads - 1) / kThreads;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
-  extern __shared__ double smem[];
-  double* sX = smem;              // R x W
-  double* sY = sX + R * W;        // R x W
-  double* sQ = sY + R * W;        // R x W (PRE)
-  double* sV = sQ + R * W;        // R x W (PRE)
-  double* sRe = sV + R * W;       // W x W (PRE)
-  double* sr = sRe + W * W;       // R
+  const T* val = values<T>(P);
+  const T* rvec = (const T*)P.r;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sX = (T*)smem_raw;           // R x W
+  T* sY = sX + R * W;             // R x W
+  T* sQ = sY + R * W;             // R x W (PRE)
+  T* sV = sQ + R * W;             // R x W (PRE)
+  T* sRe = sV + R * W;            // W x W (PRE)
+  T* sr = sRe + W * W;            // R
   int ea[EPT], eb[EPT];
-  double acc[EPT];
-  double accg = 0.0;
+  RowAcc<T> acc[EPT];
+  RowAcc<T> accg;
   if (GRAM) {
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
       int e = threadIdx.x + q * kThreads;
       if (e < E) upper_ab(e, W, ea[q], eb[q]);
       else ea[q] = eb[q] = 0;
-      acc[q] = 0.0;
     }
     if (PRE) {
-      for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRe[i] = P.small[kSmallRe + i];
+      for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRe[i] = (T)P.small[kSmallRe + i];
     }
   }
   int r0, r1;
@@ -619,11 +709,11 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const doub
       int idx = threadIdx.x + q * kThreads;
       if (idx < R * W) {
         int r = idx / W, bb = idx - r * W;
-        double y = 0.0, xv = 0.0;
+        T y = 0, xv = 0;
         if (r < nr) {
           const int i = row0 + r;
           const int pe = P.rowptr[i + 1];
-          for (int p = P.rowptr[i]; p < pe; p++) y = fma(P.val[p], Xin[(long long)P.col[p] * W + bb], y);
+          for (int p = P.rowptr[i]; p < pe; p++) y = fma(val[p], Xin[(long long)P.col[p] * W + bb], y);
           Yout[(long long)i * W + bb] = y;
           xv = Xin[(long long)i * W + bb];
         }
@@ -632,10 +722,10 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const doub
       }
     }
     if (GRAM) {
-      for (int r = threadIdx.x; r < R; r += blockDim.x) sr[r] = (r < nr) ? P.r[row0 + r] : 0.0;
+      for (int r = threadIdx.x; r < R; r += blockDim.x) sr[r] = (r < nr) ? rvec[row0 + r] : T(0);
       __syncthreads();
-      const double* q_ = sX;
-      const double* v_ = sY;
+      const T* q_ = sX;
+      const T* v_ = sY;
       if (PRE) {
         if (W == 1) {
           for (int r = threadIdx.x; r < R; r += blockDim.x) {
@@ -646,8 +736,8 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const doub
           constexpr int H = (W > 1) ? W / 2 : 1;
           for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
             const int r = idx / H, bp = idx - r * H;
-            double q1, q2, v1, v2;
-            tri_pair2<W>(sX + r * W, sY + r * W, sRe, bp, q1, q2, v1, v2);
+            T q1, q2, v1, v2;
+            tri_pair2<T, W>(sX + r * W, sY + r * W, sRe, bp, q1, q2, v1, v2);
             sQ[r * W + bp] = q1;
             sQ[r * W + W - 1 - bp] = q2;
             sV[r * W + bp] = v1;
@@ -658,18 +748,18 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const doub
         q_ = sQ;
         v_ = sV;
       }
-      #pragma unroll
+#pragma unroll
       for (int q = 0; q < EPT; q++) {
         if (threadIdx.x + q * kThreads < E) {
-          double s = acc[q];
+          T s = acc[q].begin();
           for (int r = 0; r < nr; r++) s = fma(q_[r * W + ea[q]], v_[r * W + eb[q]], s);
-          acc[q] = s;
+          acc[q].end(s);
         }
       }
       if (threadIdx.x < W) {
-        double s = accg;
+        T s = accg.begin();
         for (int r = 0; r < nr; r++) s = fma(q_[r * W + threadIdx.x], sr[r], s);
-        accg = s;
+        accg.end(s);
       }
       __syncthreads();
     }
@@ -679,9 +769,9 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const doub
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
       int e = threadIdx.x + q * kThreads;
-      if (e < E) out[e] = acc[q];
+      if (e < E) out[e] = acc[q].value();
     }
-    if (threadIdx.x < W) out[E + threadIdx.x] = accg;
+    if (threadIdx.x < W) out[E + threadIdx.x] = accg.value();
   }
 }
 
@@ -692,14 +782,16 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   constexpr int E = W * (W + 1) / 2;
   DevState* st = P.st;
   if (skip(st, gw)) return;
-  extern __shared__ double smem[];
-  double* sG = smem;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sG = (double*)smem_raw;
   double* sR = sG + W * W;
   double* sSi = sR + W * W;
   double* sD = sSi + W * W;
   double* sg = sD + W;
   __shared__ int sflag;
-  cta_reduce_partials(P.part_buf, E + W, gx, E + W, [&](int e, double s) {
+  const double* red = P.small + kSmallG;  // [G upper | g] reduced by k_reduce_partials
+  for (int e = threadIdx.x; e < E + W; e += blockDim.x) {
+    const double s = red[e];
     if (e < E) {
       int a, b;
       upper_ab(e, W, a, b);
@@ -708,9 +800,10 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
     } else {
       sg[e - E] = s;
     }
-  });
+  }
+  (void)gx;
   __syncthreads();
-  if (!cta_cholesky<W>(sG, sR, sD, &sflag)) {
+  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
@@ -740,43 +833,44 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
 
 // W_k = X R^{-1}, V_k = Y R^{-1} (written to Wout / Vout), x += W_k alpha,
 // r -= V_k alpha; per-CTA ||r_k||^2 and, for MSDO-CG, V_k^T r_k partials.
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const double* Xin, const double* Yin,
-                                                     double* Wout, double* Vout, double* xio, double* rio) {
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, const T* Yin, T* Wout, T* Vout,
+                                                     T* xio, T* rio) {
   constexpr int R = Tile<W>::R;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   if (Wout == nullptr) {  // the solver's window slot
     const long long s = st->next_slot;
-    Wout = P.slotW + s * P.slot_stride;
-    Vout = P.slotV + s * P.slot_stride;
+    Wout = (T*)P.slotW + s * P.slot_stride;
+    Vout = (T*)P.slotV + s * P.slot_stride;
   }
-  extern __shared__ double smem[];
-  double* sX = smem;            // R x W
-  double* sY = sX + R * W;      // R x W
-  double* sWa = sY + R * W;     // R x W
-  double* sVa = sWa + R * W;    // R x W
-  double* sVk = sVa + R * W;    // R x W
-  double* sRi = sVk + R * W;    // W x W
-  double* sal = sRi + W * W;    // W
-  double* srn = sal + W;        // R
-  double* sbuf = srn + R;       // kThreads
-  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = P.small[kSmallRi + i];
-  for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = P.small[kSmallAl + i];
-  double rho_acc = 0.0, beta_acc = 0.0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sbuf = (double*)smem_raw;  // kThreads
+  T* sX = (T*)(sbuf + kThreads);     // R x W
+  T* sY = sX + R * W;                // R x W
+  T* sWa = sY + R * W;               // R x W
+  T* sVa = sWa + R * W;              // R x W
+  T* sVk = sVa + R * W;              // R x W
+  T* sRi = sVk + R * W;              // W x W
+  T* sal = sRi + W * W;              // W
+  T* srn = sal + W;                  // R
+  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = (T)P.small[kSmallRi + i];
+  for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = (T)P.small[kSmallAl + i];
+  double rho_acc = 0.0;
+  RowAcc<T> beta_acc;
   int r0, r1;
   cta_rows(P.n, r0, r1);
   for (int row0 = r0; row0 < r1; row0 += R) {
     const int nr = min(R, r1 - row0);
     for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
       bool in = idx / W < nr;
-      sX[idx] = in ? Xin[(long long)row0 * W + idx] : 0.0;
-      sY[idx] = in ? Yin[(long long)row0 * W + idx] : 0.0;
+      sX[idx] = in ? Xin[(long long)row0 * W + idx] : T(0);
+      sY[idx] = in ? Yin[(long long)row0 * W + idx] : T(0);
     }
     __syncthreads();
     if (W == 1) {
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        const double wk = sX[r] * sRi[0], vk = sY[r] * sRi[0];
+        const T wk = sX[r] * sRi[0], vk = sY[r] * sRi[0];
         if (r < nr) {
           Wout[row0 + r] = wk;
           Vout[row0 + r] = vk;
@@ -789,8 +883,8 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const double* 
       constexpr int H = (W > 1) ? W / 2 : 1;
       for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
         const int r = idx / H, bp = idx - r * H;
-        double w1, w2, v1, v2;
-        tri_pair2<W>(sX + r * W, sY + r * W, sRi, bp, w1, w2, v1, v2);
+        T w1, w2, v1, v2;
+        tri_pair2<T, W>(sX + r * W, sY + r * W, sRi, bp, w1, w2, v1, v2);
         const int b1 = bp, b2 = W - 1 - bp;
         if (r < nr) {
           const long long o = (long long)(row0 + r) * W;
@@ -809,9 +903,9 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const double* 
     }
     __syncthreads();
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
-      double rn = 0.0;
+      T rn = 0;
       if (r < nr) {
-        double dx = 0.0, dr = 0.0;
+        T dx = 0, dr = 0;
         for (int bb = 0; bb < W; bb++) {
           dx += sWa[r * W + bb];
           dr += sVa[r * W + bb];
@@ -820,25 +914,26 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const double* 
         xio[i] += dx;
         rn = rio[i] - dr;
         rio[i] = rn;
-        rho_acc = fma(rn, rn, rho_acc);
+        rho_acc += (double)rn * (double)rn;
       }
       srn[r] = rn;
     }
     __syncthreads();
     if (P.want_beta && threadIdx.x < W) {
-      double s = beta_acc;
+      T s = beta_acc.begin();
       for (int r = 0; r < nr; r++) s = fma(sVk[r * W + threadIdx.x], srn[r], s);
-      beta_acc = s;
+      beta_acc.end(s);
     }
     __syncthreads();
   }
   double tot = block_sum(rho_acc, sbuf);
   if (threadIdx.x == 0) P.rho_part[blockIdx.x] = tot;
-  if (P.want_beta && threadIdx.x < W) P.beta_part[(long long)blockIdx.x * 64 + threadIdx.x] = beta_acc;
+  if (P.want_beta && threadIdx.x < W) P.beta_part[(long long)blockIdx.x * 64 + threadIdx.x] = beta_acc.value();
 }
 
 // End of iteration k: rho_k, tol1, window push, stop and switch tests.
-__global__ void k_finish(KP P, int gw, int gx) {
+// elem_bytes is the size of the solve's scalar type (slot addresses).
+__global__ void k_finish(KP P, int gw, int gx, int elem_bytes) {
   __shared__ double sbuf[kThreads];
   DevState* st = P.st;
   if (skip(st, gw)) return;
@@ -846,17 +941,20 @@ __global__ void k_finish(KP P, int gw, int gx) {
   for (int c = threadIdx.x; c < gx; c += blockDim.x) s += P.rho_part[c];
   s = block_sum(s, sbuf);
   const int W = st->width;
-  if (P.want_beta && threadIdx.x < W) {
-    double bsum = 0.0;
-    for (int c = 0; c < gx; c++) bsum += P.beta_part[(long long)c * 64 + threadIdx.x];
-    P.small[kSmallBe + threadIdx.x] = -bsum;  // beta_{k+1} = -V_k^T r_k
+  if (P.want_beta) {  // beta_{k+1} = -V_k^T r_k, one warp per column
+    const int lane = threadIdx.x & 31;
+    for (int col = threadIdx.x >> 5; col < W; col += blockDim.x >> 5) {
+      const double bsum = warp_sum_partials(P.beta_part + col, 64, gx, lane);
+      if (lane == 0) P.small[kSmallBe + col] = -bsum;
+    }
   }
   if (threadIdx.x != 0) return;
   const int k = st->k;
   const double rho = sqrt(s);
   st->rho = rho;
-  P.history[k] = rho;
+  P.history[st->hist_off + k] = rho;
   st->tol1 = fabs(rho - st->rho_prev) / st->rho0;
+  st->rtol1 = fabs(rho - st->rho_prev) / st->rho_cycle;
   st->rho_prev = rho;
   st->iters = k;
   // memory count: the window used this iteration plus the new block
@@ -866,8 +964,8 @@ __global__ void k_finish(KP P, int gw, int gx) {
   // push (W_k, V_k), dropping the oldest block beyond the capacity
   BlockDesc nb;
   nb.slot = st->next_slot;
-  nb.W = P.slotW + (long long)nb.slot * P.slot_stride;
-  nb.V = P.slotV + (long long)nb.slot * P.slot_stride;
+  nb.W = (unsigned char*)P.slotW + (long long)nb.slot * P.slot_stride * elem_bytes;
+  nb.V = (unsigned char*)P.slotV + (long long)nb.slot * P.slot_stride * elem_bytes;
   nb.w = W;
   nb.pad = 0;
   if (st->nq < st->cap) {
@@ -893,13 +991,32 @@ __global__ void k_finish(KP P, int gw, int gx) {
   } else if (knext >= st->kmax) {
     st->stop = 1;
     st->status = ST_ENOCONV;
-  } else if (st->switch_tol > 0.0 && st->counter == 0 && st->tol1 < st->switch_tol) {
-    st->gen = GEN_SPLIT;  // W_k = [T^{t/2}(r_{k-1})]
-    st->width = W / 2;
-    st->counter = 1;
-    st->switch_it = k;
   } else {
-    st->gen = (st->variant == 0) ? GEN_SRE : (st->variant == 1 ? GEN_MSDO : GEN_SPLIT);
+    const bool do_switch = st->switch_tol > 0.0 && st->counter == 0 && st->tol1 < st->switch_tol;
+    // Section 3: fixed-cycle restarts (k mod j == 1), restarts on the
+    // residual-change test relative to the cycle's initial residual, and the
+    // restart at the switch (Tables 8, 9)
+    const bool do_restart =
+        (st->restart_every >= 2 && knext % st->restart_every == 1) ||
+        (st->restart_tol > 0.0 && st->rtol1 < st->restart_tol &&
+         (st->restart_max == 0 || st->restarts < st->restart_max)) ||
+        (do_switch && st->restart_at_switch);
+    if (do_restart) {  // discard the stored blocks; the next block is [T(r)]
+      st->nq = 0;
+      st->next_slot = 0;
+      st->restarts++;
+      st->rho_cycle = rho;  // the new cycle starts from r_k
+    }
+    if (do_switch) {
+      st->gen = GEN_SPLIT;  // W_k = [T^{t/2}(r_{k-1})]
+      st->width = W / 2;
+      st->counter = 1;
+      st->switch_it = k;
+    } else if (do_restart) {
+      st->gen = GEN_SPLIT;
+    } else {
+      st->gen = (st->variant == 0) ? GEN_SRE : (st->variant == 1 ? GEN_MSDO : GEN_SPLIT);
+    }
   }
 }
 
@@ -915,6 +1032,27 @@ __global__ void k_rho_only(KP P, int gx) {
 // dst[i] = -src[i], i < w (beta = -V^T r for the step-level MSDO generator).
 __global__ void k_neg_copy(const double* src, double* dst, int w) {
   if ((int)threadIdx.x < w) dst[threadIdx.x] = -src[threadIdx.x];
+}
+
+// ------------------------------------------------ iterative refinement
+
+// bf = (float)(r * scale): right-hand side of an FP32 inner solve.
+__global__ void k_to_float_scaled(int n, const double* r, float* bf, double scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    bf[i] = (float)(r[i] * scale);
+}
+
+// x += scale * (double)df: FP64 update by the FP32 inner correction.
+__global__ void k_axpy_from_float(int n, double* x, const float* df, double scale) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    x[i] = fma(scale, (double)df[i], x[i]);
+}
+
+// Matrix values rounded to FP32.
+__global__ void k_vals_to_float(long long nnz, const double* v, float* vf) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
+       i += (long long)gridDim.x * blockDim.x)
+    vf[i] = (float)v[i];
 }
 
 }  // namespace ecg

@@ -18,6 +18,7 @@ from . import build as _build
 OK, ENOCONV, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTSPD = 0, 1, -1, -2, -3, -4, -5
 SRE, MSDO, MODMSDO = 0, 1, 2
 PRE_CHOLQR, A_CHOLQR = 0, 1
+FP64, MIXED = 0, 1
 VARIANTS = {"sre": SRE, "msdo": MSDO, "modmsdo": MODMSDO}
 
 
@@ -46,6 +47,12 @@ class _Opts(C.Structure):
         ("ortho", C.c_int),
         ("check_every", C.c_int),
         ("use_graph", C.c_int),
+        ("precision", C.c_int),
+        ("inner_tol", C.c_double),
+        ("restart_every", C.c_int),
+        ("restart_tol", C.c_double),
+        ("restart_max", C.c_int),
+        ("restart_at_switch", C.c_int),
         ("stream", C.c_void_p),
     ]
 
@@ -54,6 +61,7 @@ class _Result(C.Structure):
     _fields_ = [
         ("iters", C.c_int),
         ("switch_it", C.c_int),
+        ("restarts", C.c_int),
         ("status", C.c_int),
         ("mem_vectors", C.c_int64),
         ("relres", C.c_double),
@@ -148,6 +156,7 @@ class SolveResult:
     relres_true: float
     device_ms: float
     history: np.ndarray
+    restarts: int = 0
 
 
 class Solver:
@@ -167,6 +176,12 @@ class Solver:
         ortho: int = PRE_CHOLQR,
         check_every: int = 16,
         use_graph: bool = True,
+        precision: int = FP64,
+        inner_tol: float = 0.0,
+        restart_every: int = 0,
+        restart_tol: float = 0.0,
+        restart_max: int = 0,
+        restart_at_switch: bool = False,
         stream=None,
     ):
         lib = load()
@@ -193,6 +208,12 @@ class Solver:
         o.ortho = int(ortho)
         o.check_every = int(check_every)
         o.use_graph = 1 if use_graph else 0
+        o.precision = int(precision)
+        o.inner_tol = float(inner_tol)
+        o.restart_every = int(restart_every)
+        o.restart_tol = float(restart_tol)
+        o.restart_max = int(restart_max)
+        o.restart_at_switch = 1 if restart_at_switch else 0
         o.stream = stream
         ctx = C.c_void_p()
         rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))
@@ -253,6 +274,7 @@ class Solver:
             relres_true=res.relres_true,
             device_ms=res.device_ms,
             history=hist,
+            restarts=res.restarts,
         )
 
     # ---------------------------------------------------------- profiling

@@ -221,6 +221,14 @@ SOLVE_CASES = [
     ("ragged_t8_trunc2", lambda: ragged(8, seed=13), dict(trunc=2), ENVELOPE),
     ("ragged_t64_trunc2", lambda: ragged(64, seed=16), dict(trunc=2), ENVELOPE),
     ("blocky64_t16_trunc2", lambda: W.blocky_diffusion2d(64, 16, blocks=8, seed=17), dict(trunc=2), ENVELOPE),
+    # restarted methods (Section 3)
+    ("poisson64_t4_restart20", lambda: W.poisson2d(64, 4, seed=1001), dict(restart_every=20), STRICT),
+    ("poisson64_t4_trunc3_restart10", lambda: W.poisson2d(64, 4, seed=1001), dict(restart_every=10, trunc=3), STRICT),
+    ("poisson64_t4_restart_tol", lambda: W.poisson2d(64, 4, seed=1001), dict(restart_tol=1e-3), STRICT),
+    ("poisson64_t4_restart_once", lambda: W.poisson2d(64, 4, seed=1001), dict(restart_tol=1e-5, restart_max=1), STRICT),
+    ("ragged_t8_restart_tol", lambda: ragged(8, seed=61), dict(restart_tol=1e-5), ENVELOPE),
+    ("ragged_t16_restart_flex", lambda: ragged(16, seed=62), dict(switch_tol=1e-4, restart_at_switch=True), ENVELOPE),
+    ("ragged_t4_msdo_restart15", lambda: ragged(4, seed=64), dict(restart_every=15, variant="msdo"), ENVELOPE),
 ]
 
 
@@ -230,6 +238,10 @@ def _oracle_kw(kw):
         trunc=kw.get("trunc", 0),
         switch_tol=kw.get("switch_tol", 0.0),
         ortho=kw.get("ortho", 0),
+        restart_every=kw.get("restart_every", 0),
+        restart_tol=kw.get("restart_tol", 0.0),
+        restart_max=kw.get("restart_max", 0),
+        restart_at_switch=kw.get("restart_at_switch", False),
     )
 
 
@@ -254,6 +266,7 @@ def test_solve_matches_oracle(name, make, kw, mode):
         assert abs(g.iters - o.iters) <= 1, (g.iters, o.iters)
         k = min(g.iters, o.iters)
         assert np.all(np.abs(g.history[: k + 1] - o.history[: k + 1]) <= 1e-8 * h0)
+        assert g.restarts == o.restarts, (g.restarts, o.restarts)
         if g.iters == o.iters:
             assert rel(xg, o.x) <= 1e-8
             if g.switch_it == o.switch_it:

@@ -496,3 +496,79 @@ def test_warm_start_is_honoured():
     x0 = p.x_star + 1e-3 * np.random.default_rng(0).standard_normal(p.n)
     r = O.ecg_solve(A, p.part, 4, p.b, x0=x0, maxit=500)
     assert r.status == 0 and rel(r.x, p.x_star) < 1e-6
+
+
+# ---------------------------------------------------------- restarts
+
+
+def test_fixed_cycle_restart_matches_brute_force():
+    """Restarted SRE-CG2 with cycle j (Section 3): iterations j+1.. restart
+    from x_j, so x_k = x_j + Galerkin over K_{k-j,t}(A, r_j) for the second
+    cycle; the first cycle is plain SRE-CG2."""
+    p, Am, bm = _tiny(seed=31)
+    j = 3
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=7, tol=0.0, restart_every=j, keep_x=True)
+    assert r.restarts == 1 and r.iters == 6
+    x0 = mp.matrix(p.n, 1)
+    T0 = BF.split_cols(p.part, p.t, bm)
+    xj = BF.galerkin(Am, x0, bm, BF.krylov_block(Am, T0, j))
+    rj = bm - Am * xj
+    Tj = BF.split_cols(p.part, p.t, rj)
+    for k in range(1, 7):
+        if k <= j:
+            xk = BF.galerkin(Am, x0, bm, BF.krylov_block(Am, T0, k))
+        else:
+            xk = BF.galerkin(Am, xj, rj, BF.krylov_block(Am, Tj, k - j))
+        assert rel(r.xhist[k - 1], BF.to_np(xk)) < 1e-10, k
+
+
+def test_restarted_flexibly_matches_brute_force():
+    """Restarted flexibly SRE-CG2 (Tables 8, 9): at the switch the stored
+    blocks are discarded and the iteration restarts from x_{k_F} with t/2
+    vectors, so x_k = x_{k_F} + Galerkin over K_{k-k_F,t/2}(A, r_{k_F})."""
+    p, Am, bm = _tiny(seed=32)
+    r = O.ecg_solve(p.scipy(), p.part, p.t, p.b, maxit=6, tol=0.0, switch_tol=1e30, restart_at_switch=True,
+                    keep_x=True)
+    assert r.switch_it == 1 and r.restarts == 1
+    x0 = mp.matrix(p.n, 1)
+    T0 = BF.split_cols(p.part, p.t, bm)
+    x1 = BF.galerkin(Am, x0, bm, T0)
+    r1 = bm - Am * x1
+    T1 = BF.split_cols(p.part, p.t // 2, r1, half=True)
+    assert rel(r.xhist[0], BF.to_np(x1)) < 1e-10
+    for k in range(2, 6):
+        xk = BF.galerkin(Am, x1, r1, BF.krylov_block(Am, T1, k - 1))
+        assert rel(r.xhist[k - 1], BF.to_np(xk)) < 1e-10, k
+
+
+def test_restart_equals_fresh_solve_from_the_restart_iterate():
+    """Section 3: a restart uses the last approximate solution as the initial
+    guess of a new cycle, while the stopping test keeps rho_0."""
+    p = W.random_spd_grid(16, 4, seed=33)
+    A = p.scipy()
+    j = 5
+    r = O.ecg_solve(A, p.part, 4, p.b, maxit=11, tol=0.0, restart_every=j, trunc=3, variant="msdo", keep_x=True)
+    f = O.ecg_solve(A, p.part, 4, p.b, x0=r.xhist[j - 1], maxit=j + 1, tol=0.0, trunc=3, variant="msdo", keep_x=True)
+    assert r.iters == 2 * j and r.restarts == 1
+    for k in range(j):  # iterations j+1 .. 2j of the restarted run = the fresh cycle
+        assert rel(r.xhist[j + k], f.xhist[k]) < 1e-12, k
+    assert np.allclose(r.history[j + 1 :], f.history[1:], rtol=1e-12, atol=0)
+
+
+def test_restart_tolerance_counts_and_limits():
+    p = W.random_spd_grid(20, 8, seed=34)
+    A = p.scipy()
+    many = O.ecg_solve(A, p.part, 8, p.b, maxit=2000, restart_tol=1e-2)
+    once = O.ecg_solve(A, p.part, 8, p.b, maxit=2000, restart_tol=1e-2, restart_max=1)
+    none = O.ecg_solve(A, p.part, 8, p.b, maxit=2000)
+    assert many.status == once.status == none.status == 0
+    assert many.restarts > 1 and once.restarts == 1 and none.restarts == 0
+    # a restart keeps at most one cycle of blocks
+    assert many.mem_vectors < none.mem_vectors
+
+
+def test_restart_options_are_validated():
+    p = W.random_spd_grid(8, 4, seed=35)
+    A = p.scipy()
+    assert O.ecg_solve(A, p.part, 4, p.b, restart_every=1).status == O.EINVAL
+    assert O.ecg_solve(A, p.part, 4, p.b, restart_at_switch=True).status == O.EINVAL
