@@ -347,6 +347,229 @@ typedef struct {
   int at_switch;
 } or_restart;
 
+/* ---------------------------------------------------- block-Jacobi factor */
+
+/* Block-Jacobi preconditioner M = L L^T with L = diag(L_1, ..., L_nb), L_i
+ * the lower-triangular factor of the diagonal block A_i = A(I_i, I_i) of
+ * the rows I_i of block i (Section 3 "Preconditioned versions", and the
+ * block Jacobi preconditioner of eq. (cholprec) in Section 5).  kind 0:
+ * the exact Cholesky factor of A_i; kind 1: the incomplete Cholesky factor
+ * with zero fill (IC(0)), which keeps the pattern of the lower triangle of
+ * A_i and matches A_i = L_i L_i^T on that pattern.  Both are computed by the
+ * same row-by-row Cholesky recurrence, on the full lower triangle for kind 0
+ * and on the pattern of A_i for kind 1.  Inside a block the rows keep
+ * increasing global order.
+ *
+ * Storage: position p = bptr[i] + (local index) enumerates the rows block
+ * by block; row p of L holds its entries in increasing local column order
+ * with the diagonal last. */
+typedef struct {
+  int64_t n;
+  int nb;
+  int kind;
+  int64_t* bptr;  /* nb + 1 */
+  int64_t* rows;  /* n: global row of position p */
+  int64_t* pos;   /* n: position of global row i */
+  int32_t* blk;   /* n: block of position p */
+  int64_t* lptr;  /* n + 1 */
+  int32_t* lcol;  /* local column */
+  double* lval;
+} or_prec;
+
+void or_prec_free(or_prec* pc) {
+  if (!pc) return;
+  free(pc->bptr); free(pc->rows); free(pc->pos); free(pc->blk);
+  free(pc->lptr); free(pc->lcol); free(pc->lval);
+  free(pc);
+}
+
+/* Entry (i, j) of A with global indices (0 when absent). */
+static double or_a_entry(const int64_t* rowptr, const int32_t* col, const double* val, int64_t i,
+                         int64_t j) {
+  double s = 0.0;
+  for (int64_t q = rowptr[i]; q < rowptr[i + 1]; q++) if (col[q] == j) s += val[q];
+  return s;
+}
+
+/* Builds the factor.  pblock[i] in [0, nb) is the block of row i; every
+ * block must be non-empty.  Returns OR_ENOTSPD when a pivot is not positive
+ * (IC(0) can break down on matrices that are not M-matrices). */
+int or_prec_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                  const int32_t* pblock, int nb, int kind, or_prec** out) {
+  *out = NULL;
+  if (n <= 0 || nb < 1 || (kind != 0 && kind != 1)) return OR_EINVAL;
+  or_prec* pc = (or_prec*)calloc(1, sizeof(or_prec));
+  if (!pc) return OR_ENOMEM;
+  pc->n = n;
+  pc->nb = nb;
+  pc->kind = kind;
+  pc->bptr = (int64_t*)calloc((size_t)nb + 1, sizeof(int64_t));
+  pc->rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  pc->pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  pc->blk = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+  pc->lptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!pc->bptr || !pc->rows || !pc->pos || !pc->blk || !pc->lptr) { or_prec_free(pc); return OR_ENOMEM; }
+  for (int64_t i = 0; i < n; i++) {
+    if (pblock[i] < 0 || pblock[i] >= nb) { or_prec_free(pc); return OR_EINVAL; }
+    pc->bptr[pblock[i] + 1]++;
+  }
+  for (int b = 0; b < nb; b++) {
+    if (pc->bptr[b + 1] == 0) { or_prec_free(pc); return OR_EINVAL; }
+    pc->bptr[b + 1] += pc->bptr[b];
+  }
+  {
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)nb);
+    if (!fill) { or_prec_free(pc); return OR_ENOMEM; }
+    for (int b = 0; b < nb; b++) fill[b] = pc->bptr[b];
+    for (int64_t i = 0; i < n; i++) { /* increasing i keeps each block sorted */
+      int64_t p = fill[pblock[i]]++;
+      pc->rows[p] = i;
+      pc->pos[i] = p;
+      pc->blk[p] = pblock[i];
+    }
+    free(fill);
+  }
+  /* pattern: local columns j <= i of the lower triangle (full for kind 0) */
+  for (int64_t p = 0; p < n; p++) {
+    const int b = pc->blk[p];
+    const int64_t li = p - pc->bptr[b];
+    int64_t cnt = 0;
+    if (kind == 0) {
+      cnt = li + 1;
+    } else {
+      const int64_t i = pc->rows[p];
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; q++) {
+        const int64_t j = col[q];
+        if (j == i || pblock[j] != b || pc->pos[j] >= p) continue;
+        /* count each distinct column once */
+        int seen = 0;
+        for (int64_t q2 = rowptr[i]; q2 < q; q2++) if (col[q2] == j) seen = 1;
+        if (!seen) cnt++;
+      }
+      cnt += 1; /* diagonal */
+    }
+    pc->lptr[p + 1] = pc->lptr[p] + cnt;
+  }
+  const int64_t nnz = pc->lptr[n];
+  pc->lcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)nnz);
+  pc->lval = (double*)malloc(sizeof(double) * (size_t)nnz);
+  if (!pc->lcol || !pc->lval) { or_prec_free(pc); return OR_ENOMEM; }
+  for (int64_t p = 0; p < n; p++) {
+    const int b = pc->blk[p];
+    const int64_t li = p - pc->bptr[b];
+    const int64_t i = pc->rows[p];
+    int64_t e = pc->lptr[p];
+    if (kind == 0) {
+      for (int64_t lj = 0; lj <= li; lj++) pc->lcol[e++] = (int32_t)lj;
+    } else {
+      for (int64_t q = rowptr[i]; q < rowptr[i + 1]; q++) {
+        const int64_t j = col[q];
+        if (j == i || pblock[j] != b || pc->pos[j] >= p) continue;
+        const int32_t lj = (int32_t)(pc->pos[j] - pc->bptr[b]);
+        int seen = 0;
+        for (int64_t e2 = pc->lptr[p]; e2 < e; e2++) if (pc->lcol[e2] == lj) seen = 1;
+        if (seen) continue;
+        /* insertion in increasing column order */
+        int64_t at = e;
+        while (at > pc->lptr[p] && pc->lcol[at - 1] > lj) { pc->lcol[at] = pc->lcol[at - 1]; at--; }
+        pc->lcol[at] = lj;
+        e++;
+      }
+      pc->lcol[e++] = (int32_t)li;
+    }
+  }
+  /* Row-by-row Cholesky on the pattern:
+   *   l_ij = (a_ij - sum_{k < j} l_ik l_jk) / l_jj   for j < i in the pattern,
+   *   l_ii = sqrt(a_ii - sum_{k < i} l_ik^2),
+   * the sums running over the columns k present in both rows. */
+  for (int64_t p = 0; p < n; p++) {
+    const int b = pc->blk[p];
+    const int64_t i = pc->rows[p];
+    const int64_t e0 = pc->lptr[p], e1 = pc->lptr[p + 1];
+    for (int64_t e = e0; e < e1 - 1; e++) {
+      const int64_t pj = pc->bptr[b] + pc->lcol[e];
+      double s = or_a_entry(rowptr, col, val, i, pc->rows[pj]);
+      /* merge row i's entries before e with row j's off-diagonal entries */
+      int64_t a = e0, c = pc->lptr[pj];
+      const int64_t cend = pc->lptr[pj + 1] - 1;
+      while (a < e && c < cend) {
+        if (pc->lcol[a] == pc->lcol[c]) { s -= pc->lval[a] * pc->lval[c]; a++; c++; }
+        else if (pc->lcol[a] < pc->lcol[c]) a++;
+        else c++;
+      }
+      pc->lval[e] = s / pc->lval[pc->lptr[pj + 1] - 1];
+    }
+    double d = or_a_entry(rowptr, col, val, i, i);
+    for (int64_t e = e0; e < e1 - 1; e++) d -= pc->lval[e] * pc->lval[e];
+    if (!(d > 0.0)) { or_prec_free(pc); return OR_ENOTSPD; }
+    pc->lval[e1 - 1] = sqrt(d);
+  }
+  *out = pc;
+  return OR_OK;
+}
+
+int64_t or_prec_nnz(const or_prec* pc) { return pc->lptr[pc->n]; }
+
+/* The factor in global coordinates: entry q is L[I[q], J[q]] = V[q]. */
+void or_prec_export(const or_prec* pc, int64_t* I, int64_t* J, double* V) {
+  for (int64_t p = 0; p < pc->n; p++) {
+    const int b = pc->blk[p];
+    for (int64_t e = pc->lptr[p]; e < pc->lptr[p + 1]; e++) {
+      I[e] = pc->rows[p];
+      J[e] = pc->rows[pc->bptr[b] + pc->lcol[e]];
+      V[e] = pc->lval[e];
+    }
+  }
+}
+
+/* X <- L^{-1} X for an n x w block (forward substitution in each block). */
+void or_prec_lsolve(const or_prec* pc, int w, double* X) {
+  for (int64_t p = 0; p < pc->n; p++) {
+    const int b = pc->blk[p];
+    const int64_t i = pc->rows[p];
+    const int64_t e1 = pc->lptr[p + 1];
+    for (int c = 0; c < w; c++) {
+      double s = X[i * w + c];
+      for (int64_t e = pc->lptr[p]; e < e1 - 1; e++)
+        s -= pc->lval[e] * X[pc->rows[pc->bptr[b] + pc->lcol[e]] * w + c];
+      X[i * w + c] = s / pc->lval[e1 - 1];
+    }
+  }
+}
+
+/* X <- L^{-T} X for an n x w block (backward substitution in each block,
+ * by columns of L: solve for the last unknown, then remove it). */
+void or_prec_ltsolve(const or_prec* pc, int w, double* X) {
+  for (int64_t p = pc->n - 1; p >= 0; p--) {
+    const int b = pc->blk[p];
+    const int64_t i = pc->rows[p];
+    const int64_t e1 = pc->lptr[p + 1];
+    for (int c = 0; c < w; c++) {
+      const double z = X[i * w + c] / pc->lval[e1 - 1];
+      X[i * w + c] = z;
+      for (int64_t e = pc->lptr[p]; e < e1 - 1; e++)
+        X[pc->rows[pc->bptr[b] + pc->lcol[e]] * w + c] -= pc->lval[e] * z;
+    }
+  }
+}
+
+/* X <- M^{-1} X = L^{-T} L^{-1} X. */
+void or_prec_apply(const or_prec* pc, int w, double* X) {
+  or_prec_lsolve(pc, w, X);
+  or_prec_ltsolve(pc, w, X);
+}
+
+/* W = L^{-T} [T(L^{-1} r)]: the preconditioned split of Algorithm 5 and eq.
+ * (zsre2), taken literally (half = 1: the t/2 split). */
+static void or_prec_split(const or_prec* pc, int64_t n, const int32_t* part, int t, int half,
+                          const double* r, double* tmp, double* W) {
+  memcpy(tmp, r, sizeof(double) * (size_t)n);
+  or_prec_lsolve(pc, 1, tmp);
+  if (half) or_split_half(n, part, t, tmp, W);
+  else or_split(n, part, t, tmp, W);
+  or_prec_ltsolve(pc, half ? t / 2 : t, W);
+}
+
 static double or_norm2(int64_t n, const double* v) {
   double s = 0.0;
   for (int64_t i = 0; i < n; i++) s += v[i] * v[i];
@@ -364,12 +587,19 @@ static double or_norm2(int64_t n, const double* v) {
  * for k = 0..iters.  xhist (n * (k_max - 1), may be NULL) receives x_k after
  * iteration k at offset (k-1)*n.  basis (may be NULL) receives every W_k
  * in order, block after block (n * sum of widths entries, capacity
- * basis_cap doubles); widths (k_max entries, may be NULL) their widths. */
+ * basis_cap doubles); widths (k_max entries, may be NULL) their widths.
+ * pc (may be NULL) is a block-Jacobi preconditioner M = L L^T: the
+ * generated blocks become those of Section 3 "Preconditioned versions"
+ * (eq. (zsre2), (zmsd2), Algorithm 5): every [T(r)] is replaced by
+ * L^{-T}[T(L^{-1} r)], W_k = A W_{k-1} by M^{-1} A W_{k-1}, and beta_k =
+ * -V_{k-1}^T (M^{-1} r_{k-1}); alpha_k, x_k, r_k and the A-orthonormalisation
+ * are unchanged, and rho_k stays the norm of the unpreconditioned
+ * residual. */
 int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
                  const int32_t* part, int t, int variant, int trunc, double switch_tol, int ortho,
                  const double* b, const double* x0, double eps, int kmax, double* x,
                  double* history, double* xhist, double* basis, int64_t basis_cap, int* widths,
-                 const or_restart* rs, or_result* res) {
+                 const or_restart* rs, const or_prec* pc, or_result* res) {
   memset(res, 0, sizeof(*res));
   or_restart rsz;
   memset(&rsz, 0, sizeof(rsz));
@@ -405,6 +635,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
   int* wq = (int*)calloc((size_t)cap, sizeof(int));
   double* r = (double*)malloc(sizeof(double) * (size_t)n);
   double* tmp = (double*)malloc(sizeof(double) * (size_t)n);
+  double* z = (double*)malloc(sizeof(double) * (size_t)n); /* M^{-1} r_{k-1} */
   double* W = (double*)malloc(sizeof(double) * (size_t)(n * t));
   double* Vn = (double*)malloc(sizeof(double) * (size_t)(n * t));
   double* Pprev = (double*)malloc(sizeof(double) * (size_t)(n * t)); /* P_{k-1} */
@@ -418,7 +649,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
   int64_t mem = 0;
   int status = OR_ENOCONV;
   int k = 1;
-  if (!Qb || !Vb || !wq || !r || !tmp || !W || !Vn || !Pprev || !Vprev || !alpha || !beta || !qs ||
+  if (!Qb || !Vb || !wq || !r || !tmp || !z || !W || !Vn || !Pprev || !Vprev || !alpha || !beta || !qs ||
       !vs || !ws) {
     status = OR_ENOMEM;
     goto out;
@@ -460,26 +691,36 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
     }
     if (k == 1) {
       width = t;
-      or_split(n, part, t, r, W); /* W_1 = [T^t(r_0)] */
+      /* W_1 = [T^t(r_0)], or L^{-T}[T^t(L^{-1} r_0)] */
+      if (pc) or_prec_split(pc, n, part, t, 0, r, tmp, W);
+      else or_split(n, part, t, r, W);
     } else if (do_switch) {
       width = t / 2;
-      or_split_half(n, part, t, r, W); /* W_k = [T^{t/2}(r_{k-1})] */
+      /* W_k = [T^{t/2}(r_{k-1})], or L^{-T}[T^{t/2}(L^{-1} r_{k-1})] */
+      if (pc) or_prec_split(pc, n, part, t, 1, r, tmp, W);
+      else or_split_half(n, part, t, r, W);
       counter = 1;
       res->switch_it = k - 1;
     } else if (do_restart) {
       width = wprev; /* [T(r_{k-1})] with the width in force */
-      if (width == t) or_split(n, part, t, r, W);
+      if (pc) or_prec_split(pc, n, part, t, width != t, r, tmp, W);
+      else if (width == t) or_split(n, part, t, r, W);
       else or_split_half(n, part, t, r, W);
     } else {
       width = wprev;
       if (variant == 0) {
         memcpy(W, Vprev, sizeof(double) * (size_t)(n * width)); /* W_k = A W_{k-1} */
+        if (pc) or_prec_apply(pc, width, W);                     /* M^{-1} A W_{k-1} */
       } else {
-        if (width == t) or_split(n, part, t, r, W);
+        if (pc) or_prec_split(pc, n, part, t, width != t, r, tmp, W);
+        else if (width == t) or_split(n, part, t, r, W);
         else or_split_half(n, part, t, r, W);
         if (variant == 1) {
-          /* beta_k = -V_{k-1}^T r_{k-1}; P_k = T(r_{k-1}) + P_{k-1} diag(beta_k). */
-          or_block_tdot(n, width, Vprev, 1, r, beta);
+          /* beta_k = -V_{k-1}^T r_{k-1} (-V_{k-1}^T M^{-1} r_{k-1} when
+           * preconditioned); P_k = T(r_{k-1}) + P_{k-1} diag(beta_k). */
+          memcpy(z, r, sizeof(double) * (size_t)n);
+          if (pc) or_prec_apply(pc, 1, z);
+          or_block_tdot(n, width, Vprev, 1, z, beta);
           for (int j = 0; j < width; j++) beta[j] = -beta[j];
           for (int64_t i = 0; i < n; i++)
             for (int j = 0; j < width; j++) W[i * width + j] += Pprev[i * width + j] * beta[j];
@@ -568,7 +809,7 @@ out:
   }
   if (Qb) for (int j = 0; j < cap; j++) free(Qb[j]);
   if (Vb) for (int j = 0; j < cap; j++) free(Vb[j]);
-  free(Qb); free(Vb); free(wq); free(r); free(tmp); free(W); free(Vn); free(Pprev); free(Vprev);
+  free(Qb); free(Vb); free(wq); free(r); free(tmp); free(z); free(W); free(Vn); free(Pprev); free(Vprev);
   free(alpha); free(beta); free(qs); free(vs); free(ws);
   return status;
 }

@@ -15,6 +15,10 @@ Conjugate Gradient methods", arXiv 2305.19013):
 - ``ecg_solve``: SRE-CG2, MSDO-CG, modified MSDO-CG, truncated and flexible
   forms (Algorithms 1-4, Section 3).
 - ``cg_solve``: classical CG (Section 1).
+- ``BlockJacobi``: the block Jacobi preconditioner M = L L^T of Section 3
+  ("Preconditioned versions") and Section 5, with exact Cholesky or IC(0)
+  diagonal blocks; ``ecg_solve(..., prec=...)`` runs the preconditioned
+  methods (eq. (zsre2), (zmsd2), Algorithm 5).
 - ``dense_spd_solve``: Cholesky solve of a small dense SPD system.
 
 Parity of the solver against the paper's own iteration counts is unpinned
@@ -93,8 +97,16 @@ def _load():
         "or_cgs2": (_INT, [_I64, _INT, _P, _P, _P, _INT, _P]),
         "or_ecg_solve": (
             _INT,
-            [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _D, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _I64, _P, _P, _P],
+            [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _D, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _I64, _P, _P, _P,
+             _P],
         ),
+        "or_prec_setup": (_INT, [_I64, _P, _P, _P, _P, _INT, _INT, C.POINTER(C.c_void_p)]),
+        "or_prec_free": (None, [_P]),
+        "or_prec_nnz": (_I64, [_P]),
+        "or_prec_export": (None, [_P, _P, _P, _P]),
+        "or_prec_lsolve": (None, [_P, _INT, _P]),
+        "or_prec_ltsolve": (None, [_P, _INT, _P]),
+        "or_prec_apply": (None, [_P, _INT, _P]),
         "or_cg_solve": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P, _P]),
         "or_mem_flexible": (_I64, [_INT, _INT, _INT]),
     }
@@ -265,10 +277,12 @@ def ecg_solve(
     restart_tol=0.0,
     restart_max=0,
     restart_at_switch=False,
+    prec=None,
 ):
     """Enlarged CG (Algorithms 1-4, their truncated and restarted forms of
-    Section 3).  ``maxit`` is the paper's k_max: at most maxit - 1
-    iterations run."""
+    Section 3, and with ``prec`` a ``BlockJacobi`` the preconditioned forms
+    of Section 3 and Algorithm 5).  ``maxit`` is the paper's k_max: at most
+    maxit - 1 iterations run."""
     rp, ci, va, n = _csr(A)
     part = np.ascontiguousarray(part, dtype=np.int32)
     b = _f64(b)
@@ -284,7 +298,8 @@ def ecg_solve(
     v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
     _load().or_ecg_solve(
         n, _p(rp), _p(ci), _p(va), _p(part), t, v, trunc, switch_tol, ortho, _p(b), _p(x0a), tol, maxit,
-        _p(x), _p(hist), _p(xh), _p(basis), cap, _p(widths), C.byref(rs), C.byref(res),
+        _p(x), _p(hist), _p(xh), _p(basis), cap, _p(widths), C.byref(rs),
+        None if prec is None else prec._h, C.byref(res),
     )
     blocks = None
     if keep_basis:
@@ -332,3 +347,61 @@ def cg_solve(A, b, x0=None, tol=1e-8, maxit=1000, keep_x=False):
 
 def mem_flexible(t, iters, switch_it):
     return int(_load().or_mem_flexible(t, iters, switch_it))
+
+
+PREC_CHOL, PREC_IC0 = 0, 1
+
+
+class BlockJacobi:
+    """Block Jacobi preconditioner M = L L^T, L = diag(L_1, ..., L_nb)
+    (Section 3 "Preconditioned versions"; eq. (cholprec), Section 5).
+    ``pblock[i]`` is the diagonal block of row i; ``kind`` is PREC_CHOL (the
+    exact Cholesky factor of each diagonal block) or PREC_IC0 (incomplete
+    Cholesky with zero fill)."""
+
+    def __init__(self, A, pblock, nb, kind=PREC_IC0):
+        rp, ci, va, n = _csr(A)
+        self.n = n
+        self._keep = (rp, ci, va)
+        pb = np.ascontiguousarray(pblock, dtype=np.int32)
+        h = C.c_void_p()
+        rc = _load().or_prec_setup(n, _p(rp), _p(ci), _p(va), _p(pb), int(nb), int(kind), C.byref(h))
+        if rc != OK:
+            raise ValueError(f"or_prec_setup failed: {rc}")
+        self._h = h
+        self.status = rc
+
+    def __del__(self):
+        try:
+            if self._h:
+                _load().or_prec_free(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def factor(self):
+        """L in global coordinates as (I, J, V) triplets."""
+        nnz = _load().or_prec_nnz(self._h)
+        I = np.zeros(nnz, dtype=np.int64)
+        J = np.zeros(nnz, dtype=np.int64)
+        V = np.zeros(nnz)
+        _load().or_prec_export(self._h, _p(I), _p(J), _p(V))
+        return I, J, V
+
+    def _run(self, name, X):
+        X = _f64(X).copy()
+        w = 1 if X.ndim == 1 else X.shape[1]
+        getattr(_load(), name)(self._h, w, _p(X))
+        return X
+
+    def lsolve(self, X):
+        """L^{-1} X."""
+        return self._run("or_prec_lsolve", X)
+
+    def ltsolve(self, X):
+        """L^{-T} X."""
+        return self._run("or_prec_ltsolve", X)
+
+    def apply(self, X):
+        """M^{-1} X = L^{-T} L^{-1} X."""
+        return self._run("or_prec_apply", X)

@@ -308,6 +308,32 @@ def _split3(t: int):
     return table[t]
 
 
+def jacobi_blocks(p: Problem, nb: int) -> np.ndarray:
+    """Diagonal blocks of a block Jacobi preconditioner for a grid problem:
+    nb rectangular (2D) or box (3D) blocks of the grid, split like the
+    subdomains (_split2 / _split3), returned in the problem's row order.
+
+    As in Section 5 (64 blocks for every t, each subdomain the union of 64/t
+    consecutive blocks), every block must lie inside one subdomain; a
+    ValueError says when nb does not refine the subdomain partition.
+    """
+    side = int(p.meta["side"])
+    perm = p.meta.get("perm", np.arange(p.n))
+    if side * side == p.n:
+        qx, qy = _split2(nb)
+        pb = block_partition2d(side, side, qx, qy)[perm]
+    elif side**3 == p.n:
+        qx, qy, qz = _split3(nb)
+        pb = block_partition3d(side, side, side, qx, qy, qz)[perm]
+    else:
+        raise ValueError("not a square or cubic grid problem")
+    pb = np.ascontiguousarray(pb, dtype=np.int32)
+    pairs = np.unique(pb.astype(np.int64) * p.t + p.part)
+    if len(np.unique(pairs // p.t)) != len(pairs):
+        raise ValueError(f"{nb} blocks do not refine the {p.t} subdomains")
+    return pb
+
+
 # Named workloads: the small parity case and the two large single-GPU cases.
 WORKLOADS = {
     "poisson2d_64_t4": lambda seed=1001: poisson2d(64, 4, seed),
