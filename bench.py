@@ -44,11 +44,11 @@ UNIT = "iterations/s"
 WORKLOAD = "diffusion2d_1024_t16"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one launch, from an ncu capture of the kernel
-# as it stands (profiles/k_tdot_window_16_diffusion2d_1024_t16.md): the
-# full-window launch (2 blocks) at n = 1,048,576, t = 16.  Reported only for
-# that kernel and shape; any other shape reports null.
-MEASURED_TRAFFIC = {("cgs_tdot", 16, 2): 402.8e6 + 3.9e6}
+# DRAM bytes (read + write) of one full-window launch of the dominant kernel
+# classes, from one ncu capture of the kernels as they stand
+# (profiles/k_tdot_window_16_diffusion2d_1024_t16.md), n = 1,048,576, t = 16,
+# window of 2 blocks.  Any other shape reports null.
+MEASURED_TRAFFIC = {("cgs_tdot", 16, 2): 402.71e6 + 5.04e6, ("cgs_update", 16, 2): 402.86e6 + 107.35e6}
 
 
 def peaks():
@@ -198,6 +198,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-tol", action="store_true", help="also solve to 1e-8 and report the time")
     ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
+    ap.add_argument("--time-to-tol-only", default="", help="only the time-to-tol runs whose name contains this")
+    ap.add_argument("--prec-blocks", type=int, default=64, help="block Jacobi blocks for the preconditioned runs")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -247,7 +249,10 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1)
     assert res.iters == K, res.iters
-    launches_per_iter = 13 if args.ortho == 0 else 11  # kernels of one iteration
+    # kernels of one iteration: generate, 2 x (coefficients, reduce, update),
+    # [Euclidean Gram, reduce, factor] for Pre-CholQR, A-Gram, reduce, factor,
+    # final update, finish
+    launches_per_iter = 15 if args.ortho == 0 else 12
     t_all = torch.tensor([ms], device="cuda")
     if dist is not None:
         dist.all_reduce(t_all, op=dist.ReduceOp.MAX)
@@ -285,8 +290,9 @@ def main():
         "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         "traffic": MEASURED_TRAFFIC.get((dom, 16, args.trunc)),
-        "traffic_note": "DRAM bytes per full-window launch of k_tdot_window<16> from one ncu capture; "
-        "algorithmic bytes per launch 3 x 8 x n x 16 = 402.7 MB read + 2.5 MB of partial sums",
+        "traffic_note": "DRAM bytes per full-window launch from one ncu capture of the current kernel; "
+        "algorithmic bytes per launch: cgs_tdot 3 x 8 x n x 16 = 402.7 MB read + 2.5 MB of partial sums, "
+        "cgs_update 3 x 8 x n x 16 read + 8 x n x 16 written = 536.9 MB (part of the write leaves L2 after the kernel)",
         "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
         "launches": dom_launch,
         "share": dom_ms / tot_ms,
@@ -340,15 +346,26 @@ def main():
     if args.time_to_tol:
         # time to the paper's tolerance, FP64 and FP32 inner solves with FP64 refinement
         ttt = {}
-        for name, prec in (("fp64", ecg.FP64), ("mixed", ecg.MIXED)):
+        pb = Wk.jacobi_blocks(p, args.prec_blocks)
+        runs = [("fp64", ecg.FP64, False), ("mixed", ecg.MIXED, False),
+                (f"fp64_ic0_{args.prec_blocks}", ecg.FP64, True), (f"mixed_ic0_{args.prec_blocks}", ecg.MIXED, True)]
+        for name, prec, pre in runs:
+            if args.time_to_tol_only and args.time_to_tol_only not in name:
+                continue
             with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
                                          stream=stream.cuda_stream) as sv:
+                ts = time.perf_counter()
+                if pre:  # block Jacobi IC(0) (Section 3, Algorithm 5); setup timed separately
+                    sv.set_preconditioner(pb, args.prec_blocks)
                 torch.cuda.synchronize()
+                t_setup = time.perf_counter() - ts
                 t0 = time.perf_counter()
                 r = sv.solve(b_dev, tol=1e-8, maxit=args.time_to_tol_maxit, x_out=x_dev)
                 torch.cuda.synchronize()
                 ttt[name] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status,
                              "relres_true": r.relres_true}
+                if pre:
+                    ttt[name]["setup_seconds"] = t_setup
         line["time_to_tol"] = ttt
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_oracle_sample(8, 1, args.trunc)

@@ -54,6 +54,10 @@ extern "C" {
 #define ECG_PRE_CHOLQR 0 /* Euclidean CholQR, then A-CholQR (the paper's choice in Section 5) */
 #define ECG_A_CHOLQR 1   /* A-CholQR alone */
 
+/* Preconditioner kinds (ecg_set_preconditioner) */
+#define ECG_PREC_NONE 0  /* no preconditioner */
+#define ECG_PREC_IC0 1   /* block Jacobi, IC(0) of every diagonal block */
+
 typedef struct ecg_ctx ecg_ctx; /* opaque */
 
 /* Sparse SPD matrix in CSR form, both triangles stored. */
@@ -144,6 +148,28 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
 int ecg_solve(ecg_ctx* ctx, const double* b, const double* x0, double* x_out, double tol,
               int maxit, ecg_result* res);
 
+/* Block Jacobi preconditioning (Section 3 "Preconditioned versions",
+ * Algorithm 5; the block Jacobi preconditioner of Section 5, eq. (cholprec)):
+ * M = L L^T with L = diag(L_1, ..., L_nb), L_i the incomplete Cholesky factor
+ * with zero fill (IC(0)) of the diagonal block A(I_i, I_i), I_i the rows
+ * with pblock[i] == block (in increasing order).  Every later ecg_solve on
+ * ctx runs the preconditioned method: the generated blocks become
+ * L^{-T}[T(L^{-1} r)] = [T(M^{-1} r)] (splits), M^{-1} A W_{k-1} (SRE-CG2) and
+ * [T(M^{-1} r)] + P_{k-1} diag(beta) with beta = -V_{k-1}^T M^{-1} r
+ * (MSDO-CG), while alpha, x, r, the A-orthonormalisation and the stopping
+ * test on ||r|| are unchanged.
+ *   pblock: n int32 block ids in [0, nblocks), host or device pointer,
+ *           copied; every block non-empty and inside one subdomain of the
+ *           partition (so that the split commutes with M^{-1}).
+ *   kind:   ECG_PREC_IC0, or ECG_PREC_NONE to remove the preconditioner
+ *           (pblock and nblocks are then ignored).
+ * The exact Cholesky factors of the paper's "Chol" variant are not offered:
+ * their fill makes the substitutions sequential along each block.
+ * Returns ECG_OK, ECG_EINVAL (bad ids, an empty block, a block across
+ * subdomains, bad kind), ECG_ENOTSPD (an IC(0) pivot is not positive; the
+ * context is left without a preconditioner), ECG_ENOMEM or ECG_ECUDA. */
+int ecg_set_preconditioner(ecg_ctx* ctx, const int32_t* pblock, int nblocks, int kind);
+
 /* Release every resource of ctx (NULL is accepted). */
 void ecg_destroy(ecg_ctx* ctx);
 
@@ -173,6 +199,11 @@ int ecg_op_split(ecg_ctx* ctx, const double* r, double* W, int half);
 
 /* Y = A X for an n x w block, 1 <= w <= 64 (Algorithm 1 line 6). */
 int ecg_op_spmm(ecg_ctx* ctx, const double* X, double* Y, int w);
+
+/* out = M^{-1} in = L^{-T} L^{-1} in for an n x w block, 1 <= w <= 64, with
+ * the preconditioner set by ecg_set_preconditioner (ECG_EINVAL without
+ * one).  in and out must not overlap. */
+int ecg_op_prec_apply(ecg_ctx* ctx, const double* in, double* out, int w);
 
 /* C = [X_0 ... X_{m-1}]^T Y: the block inner products of Sections 2-3
  * (CGS coefficients (A Q)^T W, beta = V^T r, W^T r).  X_j is n x wx[j]

@@ -57,9 +57,9 @@ struct Prof {
   long long launches[16];
 };
 
-const char* kProfNames[] = {"generate", "cgs_tdot", "cgs_update", "gram_e",   "small_e",
-                            "spmm_gram", "small_a", "final",      "finish",   "setup"};
-constexpr int kProfClasses = 10;
+const char* kProfNames[] = {"generate", "cgs_tdot", "cgs_update", "gram_e", "small_e", "spmm_gram",
+                            "small_a",  "final",    "finish",     "setup",  "precond"};
+constexpr int kProfClasses = 11;
 
 }  // namespace
 
@@ -104,6 +104,17 @@ struct ecg_ctx {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaGraphExec_t gexec[14] = {};  // [FP32 ? 7 : 0] + width index
   int graph_iters[14] = {};
+  // block Jacobi preconditioner (prec_nb == 0: none)
+  int prec_nb = 0;
+  int *d_pfblk = nullptr, *d_pflev = nullptr, *d_pfrows = nullptr;
+  int *d_pbblk = nullptr, *d_pblev = nullptr, *d_pbrows = nullptr;
+  int *d_lp = nullptr, *d_lc = nullptr, *d_up = nullptr, *d_uc = nullptr, *d_umap = nullptr;
+  double *d_lv = nullptr, *d_ld = nullptr, *d_uv = nullptr;
+  float *d_lvf = nullptr, *d_ldf = nullptr, *d_uvf = nullptr;
+  double* d_z = nullptr;
+  float* d_zf = nullptr;
+  double* d_ppart = nullptr;  // nb x 64
+  int* d_pflag = nullptr;
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // profiling event pool
   size_t pev_used = 0;
@@ -170,20 +181,8 @@ bool is_device_ptr(const void* p) {
 }
 
 template <typename T, int W>
-constexpr size_t smem_tdot() {
-  return sizeof(T) * (Tile<W>::R * kChunk + Tile<W>::R * W);
-}
-template <typename T, int W>
-constexpr size_t smem_update() {
-  return sizeof(T) * (Tile<W>::R * kChunk + kChunk * W);
-}
-template <typename T, int W>
 constexpr size_t smem_spmm() {
   return sizeof(T) * (4 * Tile<W>::R * W + W * W + Tile<W>::R);
-}
-template <typename T, int W>
-constexpr size_t smem_final() {
-  return sizeof(double) * kThreads + sizeof(T) * (5 * Tile<W>::R * W + W * W + W + Tile<W>::R);
 }
 template <int W>
 constexpr size_t smem_small() {
@@ -202,6 +201,8 @@ int set_smem_attrs_t() {
   CK(cudaFuncSetAttribute(k_spmm_gram<T, W, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem_spmm<T, W>()));
   CK(cudaFuncSetAttribute(k_final<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<T, W>()));
+  CK(cudaFuncSetAttribute(k_gram_self<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_gram_self<T, W>()));
   return ECG_OK;
 }
 
@@ -254,8 +255,31 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   P.history = c->d_hist;
   P.rho_part = c->d_rho_part;
   P.beta_part = c->d_beta_part;
-  P.want_beta = (c->opts.variant == ECG_MSDO) ? 1 : 0;
+  // the step-level entry points (own state) never precondition
+  P.prec = (c->prec_nb > 0 && st == c->d_st) ? 1 : 0;
+  P.want_beta = (c->opts.variant == ECG_MSDO && !P.prec) ? 1 : 0;
+  P.z = fp32 ? (void*)c->d_zf : (void*)c->d_z;
   return P;
+}
+
+PrecP make_precp(const ecg_ctx* c, bool fp32) {
+  PrecP Q;
+  Q.nb = c->prec_nb;
+  Q.fblk = c->d_pfblk;
+  Q.flev = c->d_pflev;
+  Q.frows = c->d_pfrows;
+  Q.bblk = c->d_pbblk;
+  Q.blev = c->d_pblev;
+  Q.brows = c->d_pbrows;
+  Q.lp = c->d_lp;
+  Q.lc = c->d_lc;
+  Q.up = c->d_up;
+  Q.uc = c->d_uc;
+  Q.lv = fp32 ? (const void*)c->d_lvf : (const void*)c->d_lv;
+  Q.ld = fp32 ? (const void*)c->d_ldf : (const void*)c->d_ld;
+  Q.uv = fp32 ? (const void*)c->d_uvf : (const void*)c->d_uv;
+  Q.part = c->d_ppart;
+  return Q;
 }
 
 // Row-CTAs for a window product with gy column chunks.
@@ -348,6 +372,14 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
   const long long tot = (long long)c->n * W;
   const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
   prof_mark(c, -1);
+  if (c->prec_nb > 0) {  // preconditioned generators (Section 3, Algorithm 5)
+    const PrecP Q = make_precp(c, fp32);
+    k_prec_solve<T, W><<<c->prec_nb, kThreads, 0, s>>>(P, Q, W, nullptr, nullptr, 0);
+    if (c->opts.variant == ECG_MSDO)
+      k_reduce_partials<<<(W * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(P.st, W, Q.part, c->prec_nb, W,
+                                                                               P.small + kSmallBe);
+    prof_mark(c, 10);
+  }
   k_generate<T, W><<<ggen, kThreads, 0, s>>>(P, W);
   prof_mark(c, 0);
   for (int pass = 0; pass < 2; pass++) {
@@ -358,7 +390,7 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
     prof_mark(c, 2);
   }
   if (pre) {
-    k_gram_self<T, W><<<c->gx, kThreads, 0, s>>>(P, W, X);
+    k_gram_self<T, W><<<c->gx, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
     prof_mark(c, 3);
     reduce_small(c, P, W, W * (W + 1) / 2);
     k_small_e<W><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
@@ -574,7 +606,7 @@ struct Ops {
     const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
     double* Y = c->d_Y;
     if (pre) {
-      k_gram_self<double, W><<<c->gx, kThreads, 0, c->stream>>>(P, W, Wio);
+      k_gram_self<double, W><<<c->gx, kThreads, smem_gram_self<double, W>(), c->stream>>>(P, W, Wio);
       reduce_small(c, P, W, W * (W + 1) / 2);
       k_small_e<W><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
       k_spmm_gram<double, W, true, true><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
@@ -611,6 +643,154 @@ template <int W> struct RunTdot {
 template <int W> struct RunUpdate { static void run(ecg_ctx* c, KP P, double* X, const double* Cin) { Ops<W>::update(c, P, X, Cin); } };
 template <int W> struct RunOrth {
   static void run(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) { Ops<W>::orth(c, P, Wio, V, x, r); }
+};
+
+// ------------------------------------------------ block Jacobi preconditioner
+
+void prec_free(ecg_ctx* c) {
+  invalidate_graphs(c);
+  c->prec_nb = 0;
+  dfree(c->d_pfblk);
+  dfree(c->d_pflev);
+  dfree(c->d_pfrows);
+  dfree(c->d_pbblk);
+  dfree(c->d_pblev);
+  dfree(c->d_pbrows);
+  dfree(c->d_lp);
+  dfree(c->d_lc);
+  dfree(c->d_up);
+  dfree(c->d_uc);
+  dfree(c->d_umap);
+  dfree(c->d_lv);
+  dfree(c->d_ld);
+  dfree(c->d_uv);
+  dfree(c->d_lvf);
+  dfree(c->d_ldf);
+  dfree(c->d_uvf);
+  dfree(c->d_z);
+  dfree(c->d_zf);
+  dfree(c->d_ppart);
+  dfree(c->d_pflag);
+}
+
+// Level lists of one substitution: rows grouped by block, then by level,
+// increasing row order inside a level.  blk[b] .. blk[b+1] index lev, and
+// lev[l] .. lev[l+1] index rows.
+void level_lists(int n, int nb, const std::vector<int>& pb, const std::vector<int>& level, std::vector<int>& blk,
+                 std::vector<int>& lev, std::vector<int>& rows) {
+  std::vector<int> nlev(nb, 0);
+  for (int i = 0; i < n; i++) nlev[pb[i]] = std::max(nlev[pb[i]], level[i] + 1);
+  blk.assign(nb + 1, 0);
+  for (int b = 0; b < nb; b++) blk[b + 1] = blk[b] + nlev[b];
+  lev.assign(blk[nb] + 1, 0);
+  for (int i = 0; i < n; i++) lev[blk[pb[i]] + level[i] + 1]++;
+  for (int l = 0; l < blk[nb]; l++) lev[l + 1] += lev[l];
+  std::vector<int> fill(lev.begin(), lev.end() - 1);
+  rows.assign(n, 0);
+  for (int i = 0; i < n; i++) rows[fill[blk[pb[i]] + level[i]]++] = i;
+}
+
+template <typename T>
+int upload(T** d, const std::vector<T>& h) {
+  int rc = dalloc(d, h.size());
+  if (rc) return rc;
+  if (!h.empty()) CK(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return ECG_OK;
+}
+
+// Symbolic analysis on the host (pattern, transpose, level lists), then the
+// IC(0) factorisation on the device.
+int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
+  const int n = c->n;
+  std::vector<int> rp(n + 1), ci(c->nnz), pt(n);
+  CK(cudaMemcpy(rp.data(), c->d_rowptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ci.data(), c->d_col, sizeof(int) * c->nnz, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(pt.data(), c->d_pmap, sizeof(int) * n, cudaMemcpyDeviceToHost));
+  // every block non-empty and inside one subdomain, so that
+  // L^{-T}[T(L^{-1} r)] = [T(M^{-1} r)] (and likewise for T^{t/2})
+  std::vector<int> owner(nb, -1);
+  for (int i = 0; i < n; i++) {
+    if (pb[i] < 0 || pb[i] >= nb) return ECG_EINVAL;
+    if (owner[pb[i]] < 0) owner[pb[i]] = pt[i];
+    else if (owner[pb[i]] != pt[i]) return ECG_EINVAL;
+  }
+  for (int b = 0; b < nb; b++)
+    if (owner[b] < 0) return ECG_EINVAL;
+  // pattern of L: columns j < i of row i in the same block
+  std::vector<int> lp(n + 1, 0), lc;
+  lc.reserve((size_t)c->nnz / 2 + 1);
+  std::vector<int> row;
+  for (int i = 0; i < n; i++) {
+    row.clear();
+    for (int a = rp[i]; a < rp[i + 1]; a++) {
+      const int j = ci[a];
+      if (j < i && pb[j] == pb[i]) row.push_back(j);
+    }
+    std::sort(row.begin(), row.end());
+    row.erase(std::unique(row.begin(), row.end()), row.end());
+    lc.insert(lc.end(), row.begin(), row.end());
+    lp[i + 1] = (int)lc.size();
+  }
+  const int nnzl = lp[n];
+  // L^T rows (entries of column i of L), with the map to L's entries
+  std::vector<int> up(n + 1, 0), uc(nnzl), umap(nnzl);
+  for (int e = 0; e < nnzl; e++) up[lc[e] + 1]++;
+  for (int i = 0; i < n; i++) up[i + 1] += up[i];
+  {
+    std::vector<int> fill(up.begin(), up.end() - 1);
+    for (int i = 0; i < n; i++)
+      for (int e = lp[i]; e < lp[i + 1]; e++) {
+        const int q = fill[lc[e]]++;
+        uc[q] = i;
+        umap[q] = e;
+      }
+  }
+  std::vector<int> levf(n, 0), levb(n, 0);
+  for (int i = 0; i < n; i++) {
+    int l = 0;
+    for (int e = lp[i]; e < lp[i + 1]; e++) l = std::max(l, levf[lc[e]] + 1);
+    levf[i] = l;
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    int l = 0;
+    for (int e = up[i]; e < up[i + 1]; e++) l = std::max(l, levb[uc[e]] + 1);
+    levb[i] = l;
+  }
+  std::vector<int> fblk, flev, frows, bblk, blev, brows;
+  level_lists(n, nb, pb, levf, fblk, flev, frows);
+  level_lists(n, nb, pb, levb, bblk, blev, brows);
+  const bool mixed = (c->opts.precision == ECG_MIXED);
+  int rc;
+  if ((rc = upload(&c->d_pfblk, fblk)) || (rc = upload(&c->d_pflev, flev)) || (rc = upload(&c->d_pfrows, frows)) ||
+      (rc = upload(&c->d_pbblk, bblk)) || (rc = upload(&c->d_pblev, blev)) || (rc = upload(&c->d_pbrows, brows)) ||
+      (rc = upload(&c->d_lp, lp)) || (rc = upload(&c->d_lc, lc)) || (rc = upload(&c->d_up, up)) ||
+      (rc = upload(&c->d_uc, uc)) || (rc = upload(&c->d_umap, umap)) || (rc = dalloc(&c->d_lv, (size_t)nnzl)) ||
+      (rc = dalloc(&c->d_ld, (size_t)n)) || (rc = dalloc(&c->d_uv, (size_t)nnzl)) ||
+      (rc = dalloc(&c->d_z, (size_t)n)) || (rc = dalloc(&c->d_ppart, (size_t)nb * 64)) ||
+      (rc = dalloc(&c->d_pflag, (size_t)1)))
+    return rc;
+  if (mixed && ((rc = dalloc(&c->d_lvf, (size_t)nnzl)) || (rc = dalloc(&c->d_ldf, (size_t)n)) ||
+                (rc = dalloc(&c->d_uvf, (size_t)nnzl)) || (rc = dalloc(&c->d_zf, (size_t)n))))
+    return rc;
+  c->prec_nb = nb;
+  const PrecP Q = make_precp(c, false);
+  CK(cudaMemsetAsync(c->d_pflag, 0, sizeof(int), c->stream));
+  k_ic0_factor<<<nb, kThreads, 0, c->stream>>>(Q, c->d_rowptr, c->d_col, c->d_val, c->d_lv, c->d_ld, c->d_pflag);
+  const int g = std::max(1, std::min(8 * c->num_sms, (std::max(nnzl, n) + 255) / 256));
+  k_prec_finish<<<g, 256, 0, c->stream>>>(n, nnzl, c->d_umap, c->d_lv, c->d_ld, c->d_uv, c->d_lvf, c->d_ldf,
+                                          c->d_uvf);
+  CK(cudaGetLastError());
+  int flag = 0;
+  CK(cudaMemcpyAsync(&flag, c->d_pflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (flag) return ECG_ENOTSPD;
+  return ECG_OK;
+}
+
+template <int W> struct RunPrec {
+  static void run(ecg_ctx* c, KP P, const double* in, double* out, int w) {
+    k_prec_solve<double, W><<<c->prec_nb, kThreads, 0, c->stream>>>(P, make_precp(c, false), W, in, out, w);
+  }
 };
 
 DevState op_state(const ecg_ctx* c, int width, int nq, int gen) {
@@ -703,8 +883,7 @@ void ecg_destroy(ecg_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->dev);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto& g : c->gexec)
-    if (g) cudaGraphExecDestroy(g);
+  invalidate_graphs(c);
   for (auto e : c->pev) cudaEventDestroy(e);
   for (auto e : c->ev)
     if (e) cudaEventDestroy(e);
@@ -738,6 +917,7 @@ void ecg_destroy(ecg_ctx* c) {
   dfree(c->d_rho_part);
   dfree(c->d_beta_part);
   dfree(c->d_bb_part);
+  prec_free(c);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
@@ -955,6 +1135,10 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
       CK(cudaMemsetAsync(c->d_xf, 0, sizeof(float) * n, s));
       DevState fin;
       if ((rc = run_solve(c, true, kmax - iters, cap, eps_in, iters, false, &fin))) return rc;
+      if (fin.status == ECG_ECUDA) {
+        status = ECG_ECUDA;
+        break;
+      }
       const int it = fin.iters;
       if (fin.mem > mem) mem = fin.mem;
       if (fin.switch_it > 0 && switch_it == 0) switch_it = iters + fin.switch_it;
@@ -1035,6 +1219,36 @@ int ecg_op_split(ecg_ctx* c, const double* r, double* W, int half) {
   P.X = W;
   P.r = const_cast<double*>(r);
   if ((rc = dispatch_w<RunGenerate>(w, c, P))) return rc;
+  return finish_op(c, nullptr);
+}
+
+int ecg_set_preconditioner(ecg_ctx* c, const int32_t* pblock, int nblocks, int kind) {
+  if (!c) return ECG_EINVAL;
+  if (kind == ECG_PREC_NONE) {
+    prec_free(c);
+    return ECG_OK;
+  }
+  if (kind != ECG_PREC_IC0 || !pblock || nblocks < 1 || nblocks > c->n) return ECG_EINVAL;
+  CK(cudaSetDevice(c->dev));
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<int> pb(c->n);
+  if (is_device_ptr(pblock)) {
+    CK(cudaMemcpy(pb.data(), pblock, sizeof(int32_t) * c->n, cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(pb.data(), pblock, sizeof(int32_t) * c->n);
+  }
+  prec_free(c);
+  const int rc = prec_build(c, pb, nblocks);
+  if (rc) prec_free(c);
+  return rc;
+}
+
+int ecg_op_prec_apply(ecg_ctx* c, const double* in, double* out, int w) {
+  if (!c || !in || !out || w < 1 || w > 64 || c->prec_nb == 0) return ECG_EINVAL;
+  int rc;
+  if ((rc = put_op_state(c, op_state(c, 1, 0, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
+  RunPrec<1>::run(c, P, in, out, w);
   return finish_op(c, nullptr);
 }
 
@@ -1268,6 +1482,8 @@ extern "C" int ecg_tdot_noalloc(int64_t n, int m, const double* const* X, const 
     case 64: noalloc_launch<64>(P, Y, gxw, gy, C, s); break;
   }
   CK(cudaGetLastError());
+  int fault = 0;  // a bounded wait on a bulk copy ran out
+  CK(cudaMemcpyAsync(&fault, &d->st->fault, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  return ECG_OK;
+  return fault ? ECG_ECUDA : ECG_OK;
 }

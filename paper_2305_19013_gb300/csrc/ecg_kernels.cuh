@@ -1,8 +1,11 @@
 // ecg_kernels.cuh -- sm_103a kernels of the enlarged CG iteration.
 //
 // Method: S. Moufawad, "Flexibly Enlarged Conjugate Gradient methods"
-// (arXiv 2305.19013), Algorithms 1-4.  One iteration k is the kernel chain
+// (arXiv 2305.19013), Algorithms 1-5.  One iteration k is the kernel chain
 //
+//   [k_prec_solve (+ k_reduce_partials)]   block Jacobi preconditioned forms
+//                   only (Section 3, Alg. 5): X = M^{-1} V_{k-1}, or
+//                   z = M^{-1} r_{k-1} and the MSDO beta = -V_{k-1}^T z
 //   k_generate      raw block X: [T^t(r)], [T^{t/2}(r)], A W_{k-1} or the
 //                   MSDO direction T(r) + P_{k-1} diag(beta)   (eq. (Tt), Alg. 1-4)
 //   2 x (k_tdot_window + k_reduce_C + k_update)
@@ -46,7 +49,7 @@ constexpr int kThreads = 256;
 constexpr int kChunk = 64;  // window columns per CGS chunk
 
 enum Gen { GEN_SPLIT = 0, GEN_SRE = 1, GEN_MSDO = 2 };
-enum Status { ST_OK = 0, ST_ENOCONV = 1, ST_EBREAKDOWN = -4 };
+enum Status { ST_OK = 0, ST_ENOCONV = 1, ST_ECUDA = -3, ST_EBREAKDOWN = -4 };
 
 struct BlockDesc {
   void* W;  // A-orthonormal block W_j (n x w, scalar type of the solve)
@@ -77,7 +80,7 @@ struct DevState {
   int restart_every;      // j >= 2: restart at k with k mod j == 1 (0: off)
   int restart_max;        // restarts allowed by restart_tol (0: unlimited)
   int restart_at_switch;  // 1: the flexible switch also restarts
-  int pad1;
+  int fault;              // 1: a bounded wait on a bulk copy ran out
   double restart_tol;     // > 0: restart when rtol1 < restart_tol
   double rho_cycle;       // residual norm at the start of the current cycle
   double rtol1;           // |rho_k - rho_{k-1}| / rho_cycle
@@ -119,6 +122,33 @@ struct KP {
   double* rho_part;  // per-CTA partial ||r||^2
   double* beta_part; // per-CTA partial V^T r (64 per CTA)
   int want_beta;     // accumulate beta partials in k_final (MSDO-CG)
+  int prec;          // 1: block Jacobi preconditioned generators (z = M^{-1} r)
+  void* z;           // M^{-1} r_{k-1} (n), written by k_prec_solve
+};
+
+// Block Jacobi preconditioner M = L L^T, L = diag(L_1 .. L_nb), L_i the
+// IC(0) factor of the diagonal block of A on the rows of block i.  Rows
+// keep their global numbering; inside a block they are taken in increasing
+// order, so L's entries in row i are the columns j < i of A's row i that
+// belong to the same block.  The substitutions run level by level: a row's
+// forward level is one more than the largest level of the rows its L entries
+// reference, its backward level likewise over the entries of L^T.
+struct PrecP {
+  int nb;
+  const int* fblk;   // nb + 1: block b's forward levels are [fblk[b], fblk[b+1])
+  const int* flev;   // level l's rows are frows[flev[l] .. flev[l+1])
+  const int* frows;  // all rows, by block then forward level
+  const int* bblk;   // backward levels, same layout
+  const int* blev;
+  const int* brows;
+  const int* lp;     // n + 1: off-diagonal entries of L's row i
+  const int* lc;     // their columns (global, increasing)
+  const void* lv;    // their values (T)
+  const void* ld;    // diagonal l_ii (T)
+  const int* up;     // n + 1: entries of L^T's row i (columns j > i)
+  const int* uc;
+  const void* uv;    // values (T), uv = L values through umap
+  double* part;      // nb x W partial -V_{k-1}^T z (MSDO-CG)
 };
 
 template <typename T>
@@ -283,6 +313,185 @@ __global__ void __launch_bounds__(kThreads) k_reduce_partials(const DevState* st
   if (lane == 0) out[e] = s;
 }
 
+
+// ------------------------------------------------------ bulk tile pipeline
+//
+// A row tile of a row-major n x w block is one contiguous range, so one bulk
+// copy (cp.async.bulk, executed by the TMA engine) moves a block's tile into
+// shared memory.  Thread 0 issues the copies of the next S = Stages<T>::S tiles ahead;
+// an mbarrier per stage counts the bytes that have landed, and every thread
+// waits on it with a bounded number of polls (a wait that runs out marks
+// DevState::fault, waits boundedly for the copies already issued, and the
+// CTA returns).  Usable when each block row is a multiple of 16 bytes and
+// every base is 16-byte aligned (FP64 w >= 2, FP32 w >= 4); otherwise the
+// kernels fall back to loads through registers.
+template <typename T>
+struct Stages {
+  // the FP64 kernels are FMA-bound and need little prefetch; the FP32 ones
+  // are bound by HBM and keep three tiles in flight
+  static constexpr int S = (sizeof(T) == 8) ? 2 : 3;
+};
+// a wait for one tile gives up after kWaitNs of wall time (the copies take
+// microseconds) or kWaitPolls polls, whichever comes first
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr long long kWaitPolls = 1LL << 26;
+constexpr int kMaxStreams = 16;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+struct BulkStream {
+  const unsigned char* base;  // block base address
+  int row_bytes;              // bytes of one block row
+  int dst_off;                // byte offset of this block's tile inside a stage
+};
+
+// The tiles [r0 + i R, min(r0 + (i+1) R, r1)) of up to kMaxStreams blocks.
+// Every thread of the CTA makes the same add() calls, so ns and stage_bytes
+// agree across the CTA; the stream table itself lives in shared memory and
+// is written and read by thread 0 alone.
+template <int S>
+struct BulkTiles {
+  BulkStream* st;        // kMaxStreams entries in shared memory
+  int ns = 0;
+  uint64_t* bar;         // S mbarriers
+  unsigned char* stage;  // S stages of stage_bytes
+  int stage_bytes = 0;
+  int r0 = 0, r1 = 0, R = 0, ntiles = 0;
+
+  __device__ bool add(const void* base, int row_bytes) {
+    if (ns >= kMaxStreams || (row_bytes & 15) || (((uintptr_t)base) & 15)) return false;
+    if (threadIdx.x == 0) {
+      st[ns].base = (const unsigned char*)base;
+      st[ns].row_bytes = row_bytes;
+      st[ns].dst_off = stage_bytes;
+    }
+    stage_bytes += R * row_bytes;
+    ns++;
+    return true;
+  }
+  __device__ int rows(int i) const { return min(R, r1 - (r0 + i * R)); }
+  // thread 0 only
+  __device__ void issue(int i) {
+    const int row0 = r0 + i * R, nr = rows(i), s = i % S;
+    uint32_t tx = 0;
+    for (int j = 0; j < ns; j++) tx += (uint32_t)(nr * st[j].row_bytes);
+    mbar_expect_tx(&bar[s], tx);
+    unsigned char* dst = stage + (long long)s * stage_bytes;
+    for (int j = 0; j < ns; j++)
+      bulk_g2s(dst + st[j].dst_off, st[j].base + (long long)row0 * st[j].row_bytes, (uint32_t)(nr * st[j].row_bytes),
+               &bar[s]);
+  }
+  __device__ bool wait(int i) {
+    const uint32_t parity = (uint32_t)((i / S) & 1);
+    if (mbar_try_wait(&bar[i % S], parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long p = 0; p < kWaitPolls; p += 64) {
+      for (int q = 0; q < 64; q++)
+        if (mbar_try_wait(&bar[i % S], parity)) return true;
+      if (global_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+  }
+  __device__ unsigned char* tile(int i) const { return stage + (long long)(i % S) * stage_bytes; }
+  // all threads: barriers ready and the first S tiles in flight
+  __device__ void start() {
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < S; s++) mbar_init(&bar[s], 1);
+      mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int i = 0; i < min(S, ntiles); i++) issue(i);
+  }
+  // thread 0, once every thread is done reading tile i (after a barrier):
+  // refill its stage with tile i+S
+  __device__ void refill(int i) {
+    if (threadIdx.x == 0 && i + S < ntiles) {
+      fence_proxy_async();
+      issue(i + S);
+    }
+  }
+  // all threads, after tile i was consumed
+  __device__ void next(int i) {
+    __syncthreads();
+    refill(i);
+  }
+  // all threads: wait for tile i; false (uniform over the CTA) after a
+  // bounded wait ran out, with the copies already issued drained (bounded)
+  __device__ bool ready(int i, DevState* st_) {
+    const bool ok = __syncthreads_and(wait(i));
+    if (ok) return true;
+    if (threadIdx.x == 0) {
+      st_->fault = 1;
+      st_->status = ST_ECUDA;
+      st_->stop = 1;
+      for (int j = i; j < min(i + S, ntiles); j++) wait(j);
+    }
+    __syncthreads();
+    return false;
+  }
+};
+
+// Dynamic shared memory of the tile kernels (bytes), for both the bulk-copy
+// pipeline and the fallback through registers.
+template <typename T, int W>
+constexpr size_t smem_tdot() {
+  return 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * (kChunk + W);
+}
+template <typename T, int W>
+constexpr size_t smem_update() {
+  return sizeof(T) * kChunk * W + 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * (kChunk + W);
+}
+template <typename T, int W>
+constexpr size_t smem_gram_self() {
+  return 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * W;
+}
+template <typename T, int W>
+constexpr size_t smem_final() {
+  return sizeof(double) * kThreads + 64 +
+         sizeof(T) * ((2 * Stages<T>::S + 3) * Tile<W>::R * W + W * W + W + Tile<W>::R);
+}
+
+// Row ranges aligned to the tile height, so that all but the last tile of
+// the last CTA are full.
+__device__ __forceinline__ void cta_rows_aligned(int n, int R, int& r0, int& r1) {
+  long long per = ((long long)n + gridDim.x - 1) / gridDim.x;
+  per = ((per + R - 1) / R) * R;
+  long long b = per * blockIdx.x;
+  long long e = b + per;
+  r0 = (int)(b < n ? b : n);
+  r1 = (int)(e < n ? e : n);
+}
+
 // ----------------------------------------------------------------- setup
 
 // r = b - A x (or r = b when x is null); per-CTA partial ||r||^2 and ||b||^2
@@ -366,7 +575,9 @@ __global__ void __launch_bounds__(kThreads) k_generate(KP P, int gw) {
   const T* vprev = last ? (const T*)last->V : nullptr;
   const T* pprev = last ? (const T*)last->W : nullptr;
   const double* beta = P.small + kSmallBe;
-  const T* r = (const T*)P.r;
+  // preconditioned: k_prec_solve wrote X = M^{-1} V_{k-1}, or z = M^{-1} r
+  if (P.prec && gen == GEN_SRE) return;
+  const T* r = (const T*)(P.prec ? P.z : P.r);
   T* X = (T*)P.X;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -392,6 +603,7 @@ template <typename T, int WB>
 __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T* B) {
   constexpr int R = Tile<WB>::R;
   constexpr int EPT = (kChunk * WB + kThreads - 1) / kThreads;
+  constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   const int nq = st->nq;
@@ -403,47 +615,100 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
   const int ncol = min(kChunk, wtot - c0);
   __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
+  __shared__ int cofs[kChunk];  // pipelined: element offset of (row 0, column) in a stage
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sA = (T*)smem_raw;          // R x kChunk
-  T* sB = sA + R * kChunk;       // R x WB
-  if (threadIdx.x < ncol) {
-    int cg = c0 + threadIdx.x;
+  const int E = ncol * WB;
+  RowAcc<T> acc[EPT];
+  // blocks of this chunk
+  auto find = [&](int cg) {
     int lo = 0, hi = nq - 1;
     while (lo < hi) {
       int mid = (lo + hi + 1) >> 1;
       if (D[mid].off <= cg) lo = mid;
       else hi = mid - 1;
     }
-    cptr[threadIdx.x] = (const T*)D[lo].V + (cg - D[lo].off);
-    cstr[threadIdx.x] = D[lo].w;
+    return lo;
+  };
+  const int jlo = find(c0), jhi = find(c0 + ncol - 1);
+  __shared__ BulkStream sst[kMaxStreams];
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = (uint64_t*)smem_raw;
+  bt.stage = smem_raw + 64;
+  bt.R = R;
+  int span = 0;
+  bool bulk = (jhi - jlo + 2 <= kMaxStreams);
+  for (int j = jlo; j <= jhi && bulk; j++) {
+    span += D[j].w;
+    bulk = bt.add(D[j].V, D[j].w * (int)sizeof(T));
   }
-  const int E = ncol * WB;
-  RowAcc<T> acc[EPT];
-  int r0, r1;
-  cta_rows(P.n, r0, r1);
-  __syncthreads();
-  for (int row0 = r0; row0 < r1; row0 += R) {
-    const int nr = min(R, r1 - row0);
-    for (int idx = threadIdx.x; idx < R * ncol; idx += blockDim.x) {
-      int r = idx / ncol, cc = idx - r * ncol;
-      sA[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
+  bulk = bulk && span <= kChunk && bt.add(B, WB * (int)sizeof(T));
+  if (bulk) {
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
+    // block j's tile starts R * (D[j].off - D[jlo].off) elements into a stage
+    if (threadIdx.x < ncol) {
+      const int cg = c0 + threadIdx.x;
+      const int j = find(cg);
+      cofs[threadIdx.x] = R * (D[j].off - D[jlo].off) + (cg - D[j].off);
+      cstr[threadIdx.x] = D[j].w;
     }
-    for (int idx = threadIdx.x; idx < R * WB; idx += blockDim.x) {
-      int r = idx / WB;
-      sB[idx] = (r < nr) ? B[(long long)row0 * WB + idx] : T(0);
-    }
-    __syncthreads();
+    const int bofs = R * span;
+    bt.start();  // includes a __syncthreads, so cofs/cstr are visible
+    for (int i = 0; i < bt.ntiles; i++) {
+      if (!bt.ready(i, (DevState*)st)) return;
+      const T* stg = (const T*)bt.tile(i);
+      const int nr = bt.rows(i);
+      const T* sB = stg + bofs;
 #pragma unroll
-    for (int q = 0; q < EPT; q++) {
-      int e = threadIdx.x + q * kThreads;
-      if (e < E) {
-        int a = e / WB, bb = e - a * WB;
-        T s = acc[q].begin();
-        for (int r = 0; r < nr; r++) s = fma(sA[r * kChunk + a], sB[r * WB + bb], s);
-        acc[q].end(s);
+      for (int q = 0; q < EPT; q++) {
+        int e = threadIdx.x + q * kThreads;
+        if (e < E) {
+          const int a = e / WB, bb = e - a * WB;
+          const T* sa = stg + cofs[a];
+          const int sd = cstr[a];
+          T s = acc[q].begin();
+          for (int r = 0; r < nr; r++) s = fma(sa[r * sd], sB[r * WB + bb], s);
+          acc[q].end(s);
+        }
       }
+      bt.next(i);
     }
+  } else {
+    T* sA = (T*)smem_raw;          // R x kChunk
+    T* sBt = sA + R * kChunk;      // R x WB
+    if (threadIdx.x < ncol) {
+      int cg = c0 + threadIdx.x;
+      int lo = find(cg);
+      cptr[threadIdx.x] = (const T*)D[lo].V + (cg - D[lo].off);
+      cstr[threadIdx.x] = D[lo].w;
+    }
+    int r0, r1;
+    cta_rows(P.n, r0, r1);
     __syncthreads();
+    for (int row0 = r0; row0 < r1; row0 += R) {
+      const int nr = min(R, r1 - row0);
+      for (int idx = threadIdx.x; idx < R * ncol; idx += blockDim.x) {
+        int r = idx / ncol, cc = idx - r * ncol;
+        sA[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
+      }
+      for (int idx = threadIdx.x; idx < R * WB; idx += blockDim.x) {
+        int r = idx / WB;
+        sBt[idx] = (r < nr) ? B[(long long)row0 * WB + idx] : T(0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < EPT; q++) {
+        int e = threadIdx.x + q * kThreads;
+        if (e < E) {
+          int a = e / WB, bb = e - a * WB;
+          T s = acc[q].begin();
+          for (int r = 0; r < nr; r++) s = fma(sA[r * kChunk + a], sBt[r * WB + bb], s);
+          acc[q].end(s);
+        }
+      }
+      __syncthreads();
+    }
   }
   double* out = P.part_buf + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (kChunk * WB);
 #pragma unroll
@@ -473,11 +738,14 @@ __global__ void __launch_bounds__(kThreads) k_reduce_C(KP P, int gw, int gxw, do
   if (lane == 0) Cout[(long long)c0 * WB + e] = s;
 }
 
-// X -= [Q_0 .. Q_{nq-1}] C over the whole window (CGS update).
+// X -= [Q_0 .. Q_{nq-1}] C over the whole window (CGS update).  A window of
+// at most kChunk columns (the truncated methods) takes the bulk-copy
+// pipeline, the X tile riding in the same stage as the window's tiles.
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const double* Cin) {
   constexpr int R = Tile<W>::R;
   constexpr int EPT = (R * W + kThreads - 1) / kThreads;
+  constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   const int nq = st->nq;
@@ -487,9 +755,62 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
   const int nch = (wtot + kChunk - 1) / kChunk;
   __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
+  __shared__ int cofs[kChunk];  // pipelined: element offset of (row 0, column) in a stage
+  __shared__ BulkStream sst[kMaxStreams];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sQ = (T*)smem_raw;          // R x kChunk
-  T* sC = sQ + R * kChunk;       // kChunk x W
+  T* sC = (T*)smem_raw;  // kChunk x W
+  unsigned char* rest = smem_raw + sizeof(T) * kChunk * W;
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = (uint64_t*)rest;
+  bt.stage = rest + 64;
+  bt.R = R;
+  bool bulk = (nch == 1 && nq + 1 <= kMaxStreams);
+  for (int j = 0; j < nq && bulk; j++) bulk = bt.add(D[j].W, D[j].w * (int)sizeof(T));
+  bulk = bulk && bt.add(Xio, W * (int)sizeof(T));
+  if (bulk) {
+    if (threadIdx.x < wtot) {
+      const int cg = threadIdx.x;
+      int lo = 0, hi = nq - 1;
+      while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (D[mid].off <= cg) lo = mid;
+        else hi = mid - 1;
+      }
+      cofs[cg] = R * D[lo].off + (cg - D[lo].off);
+      cstr[cg] = D[lo].w;
+    }
+    for (int idx = threadIdx.x; idx < wtot * W; idx += blockDim.x) sC[idx] = (T)Cin[idx];
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
+    const int xofs = R * wtot;
+    bt.start();
+    for (int i = 0; i < bt.ntiles; i++) {
+      if (!bt.ready(i, (DevState*)st)) return;
+      const T* stg = (const T*)bt.tile(i);
+      const int row0 = bt.r0 + i * R, nr = bt.rows(i);
+      T acc[EPT];
+#pragma unroll
+      for (int q = 0; q < EPT; q++) {
+        const int e = threadIdx.x + q * kThreads;
+        if (e < R * W) {
+          const int r = e / W, bb = e - r * W;
+          T sacc = stg[xofs + e];
+          for (int a = 0; a < wtot; a++) sacc = fma(-stg[cofs[a] + r * cstr[a]], sC[a * W + bb], sacc);
+          acc[q] = sacc;
+        }
+      }
+      __syncthreads();
+      bt.refill(i);
+#pragma unroll
+      for (int q = 0; q < EPT; q++) {
+        const int e = threadIdx.x + q * kThreads;
+        if (e < R * W && e / W < nr) Xio[(long long)row0 * W + e] = acc[q];
+      }
+    }
+    return;
+  }
+  T* sQ = (T*)rest;  // R x kChunk
   int r0, r1;
   cta_rows(P.n, r0, r1);
   for (int row0 = r0; row0 < r1; row0 += R) {
@@ -552,9 +873,11 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
   constexpr int R = Tile<W>::R;
   constexpr int E = W * (W + 1) / 2;
   constexpr int EPT = (E + kThreads - 1) / kThreads;
+  constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
-  __shared__ T sB[R * W];
+  __shared__ BulkStream sst[kMaxStreams];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   int ea[EPT], eb[EPT];
 #pragma unroll
   for (int q = 0; q < EPT; q++) {
@@ -563,13 +886,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
     else ea[q] = eb[q] = 0;
   }
   RowAcc<T> acc[EPT];
-  int r0, r1;
-  cta_rows(P.n, r0, r1);
-  for (int row0 = r0; row0 < r1; row0 += R) {
-    const int nr = min(R, r1 - row0);
-    for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x)
-      sB[idx] = (idx / W < nr) ? Xin[(long long)row0 * W + idx] : T(0);
-    __syncthreads();
+  auto accumulate = [&](const T* sB, int nr) {
 #pragma unroll
     for (int q = 0; q < EPT; q++) {
       if (threadIdx.x + q * kThreads < E) {
@@ -578,7 +895,33 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
         acc[q].end(s);
       }
     }
-    __syncthreads();
+  };
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = (uint64_t*)smem_raw;
+  bt.stage = smem_raw + 64;
+  bt.R = R;
+  if (bt.add(Xin, W * (int)sizeof(T))) {
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
+    bt.start();
+    for (int i = 0; i < bt.ntiles; i++) {
+      if (!bt.ready(i, (DevState*)st)) return;
+      accumulate((const T*)bt.tile(i), bt.rows(i));
+      bt.next(i);
+    }
+  } else {
+    T* sB = (T*)smem_raw;  // R x W
+    int r0, r1;
+    cta_rows(P.n, r0, r1);
+    for (int row0 = r0; row0 < r1; row0 += R) {
+      const int nr = min(R, r1 - row0);
+      for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x)
+        sB[idx] = (idx / W < nr) ? Xin[(long long)row0 * W + idx] : T(0);
+      __syncthreads();
+      accumulate(sB, nr);
+      __syncthreads();
+    }
   }
   double* out = P.part_buf + (long long)blockIdx.x * E;
 #pragma unroll
@@ -844,33 +1187,57 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
     Wout = (T*)P.slotW + s * P.slot_stride;
     Vout = (T*)P.slotV + s * P.slot_stride;
   }
+  constexpr int S = Stages<T>::S;
+  __shared__ BulkStream sst[kMaxStreams];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sbuf = (double*)smem_raw;  // kThreads
-  T* sX = (T*)(sbuf + kThreads);     // R x W
-  T* sY = sX + R * W;                // R x W
-  T* sWa = sY + R * W;               // R x W
-  T* sVa = sWa + R * W;              // R x W
-  T* sVk = sVa + R * W;              // R x W
-  T* sRi = sVk + R * W;              // W x W
-  T* sal = sRi + W * W;              // W
-  T* srn = sal + W;                  // R
+  double* sbuf = (double*)smem_raw;                       // kThreads
+  uint64_t* sbar = (uint64_t*)(sbuf + kThreads);          // 64 bytes
+  T* sX = (T*)((unsigned char*)sbar + 64);                // S stages of [R x W | R x W]
+  T* sWa = sX + S * 2 * R * W;                            // R x W
+  T* sVa = sWa + R * W;                                   // R x W
+  T* sVk = sVa + R * W;                                   // R x W
+  T* sRi = sVk + R * W;                                   // W x W
+  T* sal = sRi + W * W;                                   // W
+  T* srn = sal + W;                                       // R
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = (T)P.small[kSmallRi + i];
   for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = (T)P.small[kSmallAl + i];
   double rho_acc = 0.0;
   RowAcc<T> beta_acc;
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = sbar;
+  bt.stage = (unsigned char*)sX;
+  bt.R = R;
+  const bool bulk = bt.add(Xin, W * (int)sizeof(T)) && bt.add(Yin, W * (int)sizeof(T));
   int r0, r1;
-  cta_rows(P.n, r0, r1);
-  for (int row0 = r0; row0 < r1; row0 += R) {
+  if (bulk) {
+    cta_rows_aligned(P.n, R, r0, r1);
+    bt.r0 = r0;
+    bt.r1 = r1;
+    bt.ntiles = (r1 - r0 + R - 1) / R;
+    bt.start();
+  } else {
+    cta_rows(P.n, r0, r1);
+  }
+  for (int i = 0, row0 = r0; row0 < r1; i++, row0 += R) {
     const int nr = min(R, r1 - row0);
-    for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
-      bool in = idx / W < nr;
-      sX[idx] = in ? Xin[(long long)row0 * W + idx] : T(0);
-      sY[idx] = in ? Yin[(long long)row0 * W + idx] : T(0);
+    const T* tX = sX;
+    const T* tY = sX + R * W;
+    if (bulk) {
+      if (!bt.ready(i, (DevState*)st)) return;
+      tX = (const T*)bt.tile(i);
+      tY = tX + R * W;
+    } else {
+      for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x) {
+        bool in = idx / W < nr;
+        sX[idx] = in ? Xin[(long long)row0 * W + idx] : T(0);
+        sX[R * W + idx] = in ? Yin[(long long)row0 * W + idx] : T(0);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (W == 1) {
       for (int r = threadIdx.x; r < R; r += blockDim.x) {
-        const T wk = sX[r] * sRi[0], vk = sY[r] * sRi[0];
+        const T wk = tX[r] * sRi[0], vk = tY[r] * sRi[0];
         if (r < nr) {
           Wout[row0 + r] = wk;
           Vout[row0 + r] = vk;
@@ -884,7 +1251,7 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
       for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
         const int r = idx / H, bp = idx - r * H;
         T w1, w2, v1, v2;
-        tri_pair2<T, W>(sX + r * W, sY + r * W, sRi, bp, w1, w2, v1, v2);
+        tri_pair2<T, W>(tX + r * W, tY + r * W, sRi, bp, w1, w2, v1, v2);
         const int b1 = bp, b2 = W - 1 - bp;
         if (r < nr) {
           const long long o = (long long)(row0 + r) * W;
@@ -902,6 +1269,7 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
       }
     }
     __syncthreads();
+    if (bulk) bt.refill(i);  // tile i is no longer read
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
       T rn = 0;
       if (r < nr) {
@@ -929,6 +1297,151 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
   double tot = block_sum(rho_acc, sbuf);
   if (threadIdx.x == 0) P.rho_part[blockIdx.x] = tot;
   if (P.want_beta && threadIdx.x < W) P.beta_part[(long long)blockIdx.x * 64 + threadIdx.x] = beta_acc.value();
+}
+
+// ------------------------------------------------ block Jacobi preconditioner
+
+// IC(0) of every diagonal block (one CTA per block, rows level by level, one
+// thread per row):
+//   l_ij = (a_ij - sum_{k < j} l_ik l_jk) / l_jj   over the pattern of A,
+//   l_ii = sqrt(a_ii - sum_{k < i} l_ik^2).
+// The rows a row references sit on earlier levels, finished by the barrier
+// that closes each level.  *flag = 1 when a pivot is not positive.
+__global__ void __launch_bounds__(kThreads) k_ic0_factor(PrecP Q, const int* rowptr, const int* col,
+                                                         const double* val, double* lv, double* ld, int* flag) {
+  const int b = blockIdx.x;
+  for (int l = Q.fblk[b]; l < Q.fblk[b + 1]; l++) {
+    for (int q = Q.flev[l] + threadIdx.x; q < Q.flev[l + 1]; q += blockDim.x) {
+      const int i = Q.frows[q];
+      const int e0 = Q.lp[i], e1 = Q.lp[i + 1];
+      for (int e = e0; e < e1; e++) {
+        const int j = Q.lc[e];
+        double s = 0.0;
+        for (int a = rowptr[i]; a < rowptr[i + 1]; a++)
+          if (col[a] == j) s += val[a];
+        int u = e0, v = Q.lp[j];
+        const int vend = Q.lp[j + 1];
+        while (u < e && v < vend) {
+          const int cu = Q.lc[u], cv = Q.lc[v];
+          if (cu == cv) {
+            s -= lv[u] * lv[v];
+            u++;
+            v++;
+          } else if (cu < cv) {
+            u++;
+          } else {
+            v++;
+          }
+        }
+        lv[e] = s / ld[j];
+      }
+      double d = 0.0;
+      for (int a = rowptr[i]; a < rowptr[i + 1]; a++)
+        if (col[a] == i) d += val[a];
+      for (int e = e0; e < e1; e++) d -= lv[e] * lv[e];
+      if (!(d > 0.0)) {
+        *flag = 1;
+        d = 1.0;
+      }
+      ld[i] = sqrt(d);
+    }
+    __syncthreads();
+  }
+}
+
+// L^T values from L's through the transpose map, and FP32 copies.
+__global__ void k_prec_finish(int n, int nnz, const int* umap, const double* lv, const double* ld, double* uv,
+                              float* lvf, float* ldf, float* uvf) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    const double u = lv[umap[e]];
+    uv[e] = u;
+    if (lvf) {
+      lvf[e] = (float)lv[e];
+      uvf[e] = (float)u;
+    }
+  }
+  if (ldf)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) ldf[i] = (float)ld[i];
+}
+
+// out = M^{-1} in = L^{-T} (L^{-1} in) for an n x w block (w columns), one
+// CTA per diagonal block; out receives y = L^{-1} in first and is then
+// overwritten by z = L^{-T} y, each row after the rows it depends on.
+template <typename T>
+__device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int w) {
+  const T* lv = (const T*)Q.lv;
+  const T* ld = (const T*)Q.ld;
+  const T* uv = (const T*)Q.uv;
+  for (int l = Q.fblk[b]; l < Q.fblk[b + 1]; l++) {
+    const int q0 = Q.flev[l];
+    const int items = (Q.flev[l + 1] - q0) * w;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int q = it / w, c = it - q * w;
+      const int i = Q.frows[q0 + q];
+      T s = in[(long long)i * w + c];
+      for (int e = Q.lp[i]; e < Q.lp[i + 1]; e++) s -= lv[e] * out[(long long)Q.lc[e] * w + c];
+      out[(long long)i * w + c] = s / ld[i];
+    }
+    __syncthreads();
+  }
+  for (int l = Q.bblk[b]; l < Q.bblk[b + 1]; l++) {
+    const int q0 = Q.blev[l];
+    const int items = (Q.blev[l + 1] - q0) * w;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+      const int q = it / w, c = it - q * w;
+      const int i = Q.brows[q0 + q];
+      T s = out[(long long)i * w + c];
+      for (int e = Q.up[i]; e < Q.up[i + 1]; e++) s -= uv[e] * out[(long long)Q.uc[e] * w + c];
+      out[(long long)i * w + c] = s / ld[i];
+    }
+    __syncthreads();
+  }
+}
+
+// The preconditioned generators of Section 3 (eq. (zsre2), (zmsd2),
+// Algorithm 5) with diagonal blocks inside the subdomains, where
+// L^{-T}[T(L^{-1} r)] = [T(M^{-1} r)]:
+//   GEN_SRE:   X = M^{-1} V_{k-1}  (= M^{-1} A W_{k-1}),
+//   otherwise: z = M^{-1} r_{k-1}, split by k_generate; for GEN_MSDO also
+//              the partial sums of beta_k = -V_{k-1}^T z of this block.
+// With in != nullptr: out = M^{-1} in for an n x w block (step-level call).
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_prec_solve(KP P, PrecP Q, int gw, const T* in, T* out, int w) {
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  const int b = blockIdx.x;
+  if (in != nullptr) {
+    prec_solve_block<T>(Q, b, in, out, w);
+    return;
+  }
+  const int gen = st->gen;
+  const T* vprev = (st->nq > 0) ? (const T*)P.desc[st->nq - 1].V : nullptr;
+  if (gen == GEN_SRE) {
+    prec_solve_block<T>(Q, b, vprev, (T*)P.X, W);
+    return;
+  }
+  T* z = (T*)P.z;
+  prec_solve_block<T>(Q, b, (const T*)P.r, z, 1);
+  if (gen != GEN_MSDO) return;
+  // -V_{k-1}^T z over this block's rows: thread (g, c), c = column
+  __shared__ double sred[kThreads];
+  constexpr int G = kThreads / W;
+  const int c = threadIdx.x % W, g = threadIdx.x / W;
+  const int q0 = Q.flev[Q.fblk[b]], q1 = Q.flev[Q.fblk[b + 1]];
+  double acc = 0.0;
+  if (g < G)
+    for (int q = q0 + g; q < q1; q += G) {
+      const int i = Q.frows[q];
+      acc += (double)vprev[(long long)i * W + c] * (double)z[i];
+    }
+  sred[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < W) {
+    double s = 0.0;
+    for (int gg = 0; gg < G; gg++) s += sred[gg * W + threadIdx.x];
+    Q.part[(long long)b * W + threadIdx.x] = -s;
+  }
 }
 
 // End of iteration k: rho_k, tol1, window push, stop and switch tests.

@@ -93,7 +93,11 @@ SIGNATURES = {
     "ecg_op_block_update": (_I, [_P, _P, _P, _I, _P, _P, C.POINTER(C.c_double)]),
     "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
     "ecg_tdot_noalloc": (_I, [C.c_int64, _I, _P, _P, _P, _I, _P, _P]),
+    "ecg_set_preconditioner": (_I, [_P, _P, _I, _I]),
+    "ecg_op_prec_apply": (_I, [_P, _P, _P, _I]),
 }
+
+PREC_NONE, PREC_IC0 = 0, 1
 
 
 def library_path() -> str:
@@ -301,6 +305,32 @@ class Solver:
         if rc < 0:
             raise EcgError(rc, what)
         return rc
+
+    def set_preconditioner(self, pblock, nblocks: int, kind: int = PREC_IC0):
+        """Block Jacobi preconditioning with IC(0) diagonal blocks (Section 3,
+        Algorithm 5); kind=PREC_NONE removes it."""
+        import numpy as np
+
+        if kind == PREC_NONE:
+            self._rc(self._lib.ecg_set_preconditioner(self._ctx, None, 0, PREC_NONE), "ecg_set_preconditioner")
+            return
+        pb = np.ascontiguousarray(pblock, dtype=np.int32)
+        if pb.shape != (self.n,):
+            raise ValueError("pblock must have n entries")
+        self._rc(
+            self._lib.ecg_set_preconditioner(self._ctx, pb.ctypes.data_as(C.c_void_p), int(nblocks), int(kind)),
+            "ecg_set_preconditioner",
+        )
+
+    def prec_apply(self, X):
+        """M^{-1} X for an n-vector or an n x w block (step-level call)."""
+        import torch
+
+        w = 1 if X.dim() == 1 else X.shape[1]
+        _check_tensor(X, (self.n,) if X.dim() == 1 else (self.n, w), "X")
+        out = torch.empty_like(X)
+        self._rc(self._lib.ecg_op_prec_apply(self._ctx, _ptr(X), _ptr(out), int(w)), "ecg_op_prec_apply")
+        return out
 
     def split(self, r, half: bool = False):
         import torch

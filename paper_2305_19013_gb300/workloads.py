@@ -334,6 +334,26 @@ def jacobi_blocks(p: Problem, nb: int) -> np.ndarray:
     return pb
 
 
+def batch_diffusion2d(count: int = 64, side_lo: int = 128, side_hi: int = 512, t: int = 8, seed: int = 4000,
+                      sigma: float = 1.0) -> list[Problem]:
+    """A batch of independent 2D diffusion systems of uneven size: system q
+    has a side drawn uniformly from {side_lo, ..., side_hi}, iid log-normal
+    cell coefficients exp(sigma * N(0, 1)), t rectangular subdomains and
+    b ~ U[-1, 1].  At the defaults: 64 systems with n from 16K to 262K."""
+    rng = _rng(seed)
+    sides = rng.integers(side_lo, side_hi + 1, count)
+    out = []
+    for q, side in enumerate(sides):
+        side = int(side)
+        kappa = np.exp(sigma * rng.standard_normal((side, side)))
+        A = diffusion2d(kappa)
+        px, py = _split2(t)
+        part = block_partition2d(side, side, px, py)
+        b = rng.uniform(-1.0, 1.0, side * side)
+        out.append(_finish(f"batch{q}_2d_{side}_t{t}", A, part, t, b, None, {"side": side}, True))
+    return out
+
+
 # Named workloads: the small parity case and the two large single-GPU cases.
 WORKLOADS = {
     "poisson2d_64_t4": lambda seed=1001: poisson2d(64, 4, seed),

@@ -188,6 +188,35 @@ def test_msdo_generate(half):
     assert rel(Pg, Po) < 1e-13
 
 
+@pytest.mark.parametrize("nb,w", [(16, 1), (16, 4), (64, 16), (4, 64)])
+def test_prec_apply(nb, w):
+    # M^{-1} X of the block Jacobi IC(0) preconditioner against the oracle's
+    # factor and substitutions; rows are ragged (36 x 36 grid)
+    p = ragged(4, seed=21) if nb != 64 else ragged(16, seed=22)
+    pb = W.jacobi_blocks(p, nb)
+    pc = O.BlockJacobi(p.scipy(), pb, nb, O.PREC_IC0)
+    X = np.random.default_rng(3).standard_normal((p.n, w))
+    ref = pc.apply(X)
+    with ecg.Solver.from_problem(p) as s:
+        s.set_preconditioner(pb, nb)
+        got = host(s.prec_apply(dev(X)))
+        got1 = host(s.prec_apply(dev(X[:, 0]))) if w == 1 else None
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    if got1 is not None:
+        assert np.abs(got1 - ref[:, 0]).max() <= 1e-12 * scale
+
+
+def test_prec_rejects_blocks_across_subdomains():
+    p = ragged(4, seed=21)
+    bad = np.zeros(p.n, dtype=np.int32)  # one block spanning all subdomains
+    with ecg.Solver.from_problem(p) as s:
+        with pytest.raises(ecg.EcgError):
+            s.set_preconditioner(bad, 1)
+        with pytest.raises(ecg.EcgError):
+            s.prec_apply(dev(np.ones(p.n)))  # no preconditioner set
+
+
 # ------------------------------------------------------------ solves
 #
 # Two parity criteria.  STRICT (well-conditioned runs): iterations within
@@ -229,6 +258,22 @@ SOLVE_CASES = [
     ("ragged_t8_restart_tol", lambda: ragged(8, seed=61), dict(restart_tol=1e-5), ENVELOPE),
     ("ragged_t16_restart_flex", lambda: ragged(16, seed=62), dict(switch_tol=1e-4, restart_at_switch=True), ENVELOPE),
     ("ragged_t4_msdo_restart15", lambda: ragged(4, seed=64), dict(restart_every=15, variant="msdo"), ENVELOPE),
+    # block Jacobi IC(0) preconditioned methods (Section 3, Algorithm 5)
+    ("poisson64_t4_prec16", lambda: W.poisson2d(64, 4, seed=1001), dict(prec_nb=16), STRICT),
+    ("poisson64_t4_trunc2_prec16", lambda: W.poisson2d(64, 4, seed=1001), dict(trunc=2, prec_nb=16), STRICT),
+    ("poisson64_t4_msdo_trunc2_prec16", lambda: W.poisson2d(64, 4, seed=1001),
+     dict(variant="msdo", trunc=2, prec_nb=16), STRICT),
+    ("poisson64_t4_flex_prec16", lambda: W.poisson2d(64, 4, seed=1001), dict(switch_tol=1e-3, prec_nb=16), STRICT),
+    ("poisson64_t4_trunc3_restart10_prec16", lambda: W.poisson2d(64, 4, seed=1001),
+     dict(restart_every=10, trunc=3, prec_nb=16), STRICT),
+    ("ragged_t4_modmsdo_trunc3_prec16", lambda: ragged(4, seed=64), dict(variant="modmsdo", trunc=3, prec_nb=16),
+     STRICT),
+    ("ragged_t16_flex_msdo_prec64", lambda: ragged(16, seed=14), dict(variant="msdo", switch_tol=1e-4, prec_nb=64),
+     ENVELOPE),
+    ("blocky64_t16_trunc2_prec64", lambda: W.blocky_diffusion2d(64, 16, blocks=8, seed=17),
+     dict(trunc=2, prec_nb=64), ENVELOPE),
+    ("aniso3d_16_t16_trunc2_prec64", lambda: W.anisotropic_diffusion3d(16, 16, seed=19), dict(trunc=2, prec_nb=64),
+     ENVELOPE),
 ]
 
 
@@ -250,8 +295,16 @@ def test_solve_matches_oracle(name, make, kw, mode):
     p = make()
     maxit = 3000
     A = p.scipy()
-    o = O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, **_oracle_kw(kw))
+    kw = dict(kw)
+    nb = kw.pop("prec_nb", 0)
+    pc, pb = None, None
+    if nb:
+        pb = W.jacobi_blocks(p, nb)
+        pc = O.BlockJacobi(A, pb, nb, O.PREC_IC0)
+    o = O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, prec=pc, **_oracle_kw(kw))
     with ecg.Solver.from_problem(p, **kw) as s:
+        if nb:
+            s.set_preconditioner(pb, nb)
         g = s.solve(dev(p.b), tol=1e-8, maxit=maxit)
     xg = host(g.x)
     assert o.status == 0
@@ -277,10 +330,10 @@ def test_solve_matches_oracle(name, make, kw, mode):
     variants = []
     for _ in range(4):
         bp = p.b * (1.0 + 1e-15 * rng.standard_normal(p.n))
-        variants.append(O.ecg_solve(A, p.part, p.t, bp, tol=1e-8, maxit=maxit, **_oracle_kw(kw)))
+        variants.append(O.ecg_solve(A, p.part, p.t, bp, tol=1e-8, maxit=maxit, prec=pc, **_oracle_kw(kw)))
     okw = _oracle_kw(kw)
     okw["ortho"] = 1 - okw["ortho"]
-    variants.append(O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, **okw))
+    variants.append(O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, prec=pc, **okw))
     assert all(v.status == 0 for v in variants)
     its = [o.iters] + [v.iters for v in variants]
     lo, hi = min(its), max(its)
@@ -412,3 +465,19 @@ def test_full_size_solve_properties(diffusion1024):
     assert abs(true - g.relres_true) <= 1e-6 * true
     assert abs(g.relres - true) <= 1e-6 * true
     assert g.relres < 0.5
+
+
+def test_full_size_preconditioned_first_iterations_match_oracle(diffusion1024):
+    """The same workload with the block Jacobi IC(0) preconditioner on 64
+    diagonal blocks of 128 x 128 cells (each subdomain the union of 4, as in
+    Section 5): the first three iterates agree with the oracle's."""
+    p = diffusion1024
+    pb = W.jacobi_blocks(p, 64)
+    pc = O.BlockJacobi(p.scipy(), pb, 64, O.PREC_IC0)
+    o = O.ecg_solve(p.scipy(), p.part, 16, p.b, tol=0.0, maxit=4, trunc=2, prec=pc)
+    with ecg.Solver.from_problem(p, trunc=2) as s:
+        s.set_preconditioner(pb, 64)
+        g = s.solve(dev(p.b), tol=0.0, maxit=4)
+    assert g.iters == o.iters == 3
+    assert rel(host(g.x), o.x) < 1e-10
+    assert np.all(np.abs(g.history - o.history) <= 1e-10 * o.history[0])
