@@ -105,12 +105,16 @@ struct ecg_ctx {
   cudaGraphExec_t gexec[14] = {};  // [FP32 ? 7 : 0] + width index
   int graph_iters[14] = {};
   // block Jacobi preconditioner (prec_nb == 0: none)
+  struct Sweep {  // one substitution in level order (see PrecSweep)
+    int *blk = nullptr, *lev = nullptr, *rows = nullptr, *cnt = nullptr, *col = nullptr, *map = nullptr;
+    double *val = nullptr, *diag = nullptr;
+    float *valf = nullptr, *diagf = nullptr;
+    int K = 1;
+  };
   int prec_nb = 0;
-  int *d_pfblk = nullptr, *d_pflev = nullptr, *d_pfrows = nullptr;
-  int *d_pbblk = nullptr, *d_pblev = nullptr, *d_pbrows = nullptr;
-  int *d_lp = nullptr, *d_lc = nullptr, *d_up = nullptr, *d_uc = nullptr, *d_umap = nullptr;
-  double *d_lv = nullptr, *d_ld = nullptr, *d_uv = nullptr;
-  float *d_lvf = nullptr, *d_ldf = nullptr, *d_uvf = nullptr;
+  Sweep pf, pb;                                // forward and backward sweeps
+  int *d_lp = nullptr, *d_lc = nullptr;        // L by rows (factorisation)
+  double *d_lv = nullptr, *d_ld = nullptr;
   double* d_z = nullptr;
   float* d_zf = nullptr;
   double* d_ppart = nullptr;  // nb x 64
@@ -262,24 +266,43 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   return P;
 }
 
+PrecSweep make_sweep(const ecg_ctx::Sweep& w, bool fp32) {
+  PrecSweep S;
+  S.blk = w.blk;
+  S.lev = w.lev;
+  S.rows = w.rows;
+  S.cnt = w.cnt;
+  S.col = w.col;
+  S.val = fp32 ? (const void*)w.valf : (const void*)w.val;
+  S.diag = fp32 ? (const void*)w.diagf : (const void*)w.diag;
+  S.K = w.K;
+  return S;
+}
+
 PrecP make_precp(const ecg_ctx* c, bool fp32) {
   PrecP Q;
   Q.nb = c->prec_nb;
-  Q.fblk = c->d_pfblk;
-  Q.flev = c->d_pflev;
-  Q.frows = c->d_pfrows;
-  Q.bblk = c->d_pbblk;
-  Q.blev = c->d_pblev;
-  Q.brows = c->d_pbrows;
-  Q.lp = c->d_lp;
-  Q.lc = c->d_lc;
-  Q.up = c->d_up;
-  Q.uc = c->d_uc;
-  Q.lv = fp32 ? (const void*)c->d_lvf : (const void*)c->d_lv;
-  Q.ld = fp32 ? (const void*)c->d_ldf : (const void*)c->d_ld;
-  Q.uv = fp32 ? (const void*)c->d_uvf : (const void*)c->d_uv;
+  Q.f = make_sweep(c->pf, fp32);
+  Q.b = make_sweep(c->pb, fp32);
   Q.part = c->d_ppart;
   return Q;
+}
+
+// Entries per row bound of the substitution kernels (0: any).
+int prec_km(const ecg_ctx* c) {
+  const int K = std::max(c->pf.K, c->pb.K);
+  return K <= 2 ? 2 : (K <= 4 ? 4 : (K <= 8 ? 8 : 0));
+}
+
+template <typename T, int W>
+void launch_prec(ecg_ctx* c, const KP& P, const PrecP& Q, int gw, const T* in, T* out, int w) {
+  const dim3 grid(c->prec_nb, (std::max(W, w) + kPrecCols - 1) / kPrecCols);
+  switch (prec_km(c)) {
+    case 2: k_prec_solve<T, W, 2><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
+    case 4: k_prec_solve<T, W, 4><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
+    case 8: k_prec_solve<T, W, 8><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
+    default: k_prec_solve<T, W, 0><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
+  }
 }
 
 // Row-CTAs for a window product with gy column chunks.
@@ -374,7 +397,7 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
   prof_mark(c, -1);
   if (c->prec_nb > 0) {  // preconditioned generators (Section 3, Algorithm 5)
     const PrecP Q = make_precp(c, fp32);
-    k_prec_solve<T, W><<<c->prec_nb, kThreads, 0, s>>>(P, Q, W, nullptr, nullptr, 0);
+    launch_prec<T, W>(c, P, Q, W, nullptr, nullptr, 0);
     if (c->opts.variant == ECG_MSDO)
       k_reduce_partials<<<(W * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(P.st, W, Q.part, c->prec_nb, W,
                                                                                P.small + kSmallBe);
@@ -647,26 +670,29 @@ template <int W> struct RunOrth {
 
 // ------------------------------------------------ block Jacobi preconditioner
 
+void free_sweep(ecg_ctx::Sweep& w) {
+  dfree(w.blk);
+  dfree(w.lev);
+  dfree(w.rows);
+  dfree(w.cnt);
+  dfree(w.col);
+  dfree(w.map);
+  dfree(w.val);
+  dfree(w.diag);
+  dfree(w.valf);
+  dfree(w.diagf);
+  w.K = 1;
+}
+
 void prec_free(ecg_ctx* c) {
   invalidate_graphs(c);
   c->prec_nb = 0;
-  dfree(c->d_pfblk);
-  dfree(c->d_pflev);
-  dfree(c->d_pfrows);
-  dfree(c->d_pbblk);
-  dfree(c->d_pblev);
-  dfree(c->d_pbrows);
+  free_sweep(c->pf);
+  free_sweep(c->pb);
   dfree(c->d_lp);
   dfree(c->d_lc);
-  dfree(c->d_up);
-  dfree(c->d_uc);
-  dfree(c->d_umap);
   dfree(c->d_lv);
   dfree(c->d_ld);
-  dfree(c->d_uv);
-  dfree(c->d_lvf);
-  dfree(c->d_ldf);
-  dfree(c->d_uvf);
   dfree(c->d_z);
   dfree(c->d_zf);
   dfree(c->d_ppart);
@@ -759,26 +785,61 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
   std::vector<int> fblk, flev, frows, bblk, blev, brows;
   level_lists(n, nb, pb, levf, fblk, flev, frows);
   level_lists(n, nb, pb, levb, bblk, blev, brows);
+  // level-ordered ELL of both sweeps; map = index of the entry in L's rows
+  auto ell = [&](const std::vector<int>& rows, const std::vector<int>& ptr, const std::vector<int>& cols,
+                 const std::vector<int>* emap, int& K, std::vector<int>& cnt, std::vector<int>& col,
+                 std::vector<int>& map) {
+    K = 1;
+    for (int i = 0; i < n; i++) K = std::max(K, ptr[i + 1] - ptr[i]);
+    cnt.assign(n, 0);
+    col.assign((size_t)n * K, 0);
+    map.assign((size_t)n * K, 0);
+    for (int q = 0; q < n; q++) {
+      const int i = rows[q];
+      cnt[q] = ptr[i + 1] - ptr[i];
+      for (int k = 0; k < cnt[q]; k++) {
+        const int e = ptr[i] + k;
+        col[(size_t)q * K + k] = cols[e];
+        map[(size_t)q * K + k] = emap ? (*emap)[e] : e;
+      }
+    }
+  };
+  std::vector<int> fcnt, fcol, fmap, bcnt, bcol, bmap;
+  int Kf = 1, Kb = 1;
+  ell(frows, lp, lc, nullptr, Kf, fcnt, fcol, fmap);
+  ell(brows, up, uc, &umap, Kb, bcnt, bcol, bmap);
   const bool mixed = (c->opts.precision == ECG_MIXED);
+  auto put_sweep = [&](ecg_ctx::Sweep& w, const std::vector<int>& blk, const std::vector<int>& lev,
+                       const std::vector<int>& rows, const std::vector<int>& cnt, const std::vector<int>& col,
+                       const std::vector<int>& map, int K) {
+    int rc;
+    w.K = K;
+    if ((rc = upload(&w.blk, blk)) || (rc = upload(&w.lev, lev)) || (rc = upload(&w.rows, rows)) ||
+        (rc = upload(&w.cnt, cnt)) || (rc = upload(&w.col, col)) || (rc = upload(&w.map, map)) ||
+        (rc = dalloc(&w.val, col.size())) || (rc = dalloc(&w.diag, (size_t)n)))
+      return rc;
+    if (mixed && ((rc = dalloc(&w.valf, col.size())) || (rc = dalloc(&w.diagf, (size_t)n)))) return rc;
+    return ECG_OK;
+  };
   int rc;
-  if ((rc = upload(&c->d_pfblk, fblk)) || (rc = upload(&c->d_pflev, flev)) || (rc = upload(&c->d_pfrows, frows)) ||
-      (rc = upload(&c->d_pbblk, bblk)) || (rc = upload(&c->d_pblev, blev)) || (rc = upload(&c->d_pbrows, brows)) ||
-      (rc = upload(&c->d_lp, lp)) || (rc = upload(&c->d_lc, lc)) || (rc = upload(&c->d_up, up)) ||
-      (rc = upload(&c->d_uc, uc)) || (rc = upload(&c->d_umap, umap)) || (rc = dalloc(&c->d_lv, (size_t)nnzl)) ||
-      (rc = dalloc(&c->d_ld, (size_t)n)) || (rc = dalloc(&c->d_uv, (size_t)nnzl)) ||
+  if ((rc = put_sweep(c->pf, fblk, flev, frows, fcnt, fcol, fmap, Kf)) ||
+      (rc = put_sweep(c->pb, bblk, blev, brows, bcnt, bcol, bmap, Kb)) || (rc = upload(&c->d_lp, lp)) ||
+      (rc = upload(&c->d_lc, lc)) || (rc = dalloc(&c->d_lv, (size_t)nnzl)) || (rc = dalloc(&c->d_ld, (size_t)n)) ||
       (rc = dalloc(&c->d_z, (size_t)n)) || (rc = dalloc(&c->d_ppart, (size_t)nb * 64)) ||
       (rc = dalloc(&c->d_pflag, (size_t)1)))
     return rc;
-  if (mixed && ((rc = dalloc(&c->d_lvf, (size_t)nnzl)) || (rc = dalloc(&c->d_ldf, (size_t)n)) ||
-                (rc = dalloc(&c->d_uvf, (size_t)nnzl)) || (rc = dalloc(&c->d_zf, (size_t)n))))
-    return rc;
+  if (mixed && (rc = dalloc(&c->d_zf, (size_t)n))) return rc;
   c->prec_nb = nb;
   const PrecP Q = make_precp(c, false);
   CK(cudaMemsetAsync(c->d_pflag, 0, sizeof(int), c->stream));
-  k_ic0_factor<<<nb, kThreads, 0, c->stream>>>(Q, c->d_rowptr, c->d_col, c->d_val, c->d_lv, c->d_ld, c->d_pflag);
-  const int g = std::max(1, std::min(8 * c->num_sms, (std::max(nnzl, n) + 255) / 256));
-  k_prec_finish<<<g, 256, 0, c->stream>>>(n, nnzl, c->d_umap, c->d_lv, c->d_ld, c->d_uv, c->d_lvf, c->d_ldf,
-                                          c->d_uvf);
+  k_ic0_factor<<<nb, kThreads, 0, c->stream>>>(Q.f, c->d_lp, c->d_lc, c->d_rowptr, c->d_col, c->d_val, c->d_lv,
+                                               c->d_ld, c->d_pflag);
+  for (ecg_ctx::Sweep* w : {&c->pf, &c->pb}) {
+    const int nent = n * w->K;
+    const int g = std::max(1, std::min(8 * c->num_sms, (nent + 255) / 256));
+    k_prec_gather<<<g, 256, 0, c->stream>>>(n, nent, w->map, w->rows, c->d_lv, c->d_ld, w->val, w->diag, w->valf,
+                                            w->diagf);
+  }
   CK(cudaGetLastError());
   int flag = 0;
   CK(cudaMemcpyAsync(&flag, c->d_pflag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -789,7 +850,7 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
 
 template <int W> struct RunPrec {
   static void run(ecg_ctx* c, KP P, const double* in, double* out, int w) {
-    k_prec_solve<double, W><<<c->prec_nb, kThreads, 0, c->stream>>>(P, make_precp(c, false), W, in, out, w);
+    launch_prec<double, W>(c, P, make_precp(c, false), W, in, out, w);
   }
 };
 
@@ -875,6 +936,7 @@ const char* ecg_strerror(int code) {
     case ECG_ECUDA: return "CUDA error";
     case ECG_EBREAKDOWN: return "block became numerically rank deficient (breakdown)";
     case ECG_ENOTSPD: return "matrix has a non-positive diagonal entry";
+    case ECG_ETIMEOUT: return "a bounded device-side wait ran out";
   }
   return "unknown status";
 }

@@ -133,21 +133,25 @@ struct KP {
 // belong to the same block.  The substitutions run level by level: a row's
 // forward level is one more than the largest level of the rows its L entries
 // reference, its backward level likewise over the entries of L^T.
+//
+// Each substitution is stored in level order ("positions" q): position q
+// holds row rows[q], its cnt[q] <= K off-diagonal entries at col/val[q*K ..]
+// (ELL, padded) and the pivot diag[q] = l_ii, so a row's data needs no
+// indirection through the row index.
+struct PrecSweep {
+  const int* blk;   // nb + 1: block b's levels are [blk[b], blk[b+1])
+  const int* lev;   // level l's positions are [lev[l], lev[l+1])
+  const int* rows;  // row of each position
+  const int* cnt;   // entries of each position
+  const int* col;   // q * K + k: column (global row) of entry k
+  const void* val;  // q * K + k: value (T)
+  const void* diag; // q: l_ii (T)
+  int K;
+};
 struct PrecP {
   int nb;
-  const int* fblk;   // nb + 1: block b's forward levels are [fblk[b], fblk[b+1])
-  const int* flev;   // level l's rows are frows[flev[l] .. flev[l+1])
-  const int* frows;  // all rows, by block then forward level
-  const int* bblk;   // backward levels, same layout
-  const int* blev;
-  const int* brows;
-  const int* lp;     // n + 1: off-diagonal entries of L's row i
-  const int* lc;     // their columns (global, increasing)
-  const void* lv;    // their values (T)
-  const void* ld;    // diagonal l_ii (T)
-  const int* up;     // n + 1: entries of L^T's row i (columns j > i)
-  const int* uc;
-  const void* uv;    // values (T), uv = L values through umap
+  PrecSweep f;       // forward: y = L^{-1} x, entries l_ij, j < i
+  PrecSweep b;       // backward: z = L^{-T} y, entries l_ji, j > i
   double* part;      // nb x W partial -V_{k-1}^T z (MSDO-CG)
 };
 
@@ -1307,22 +1311,23 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
 //   l_ii = sqrt(a_ii - sum_{k < i} l_ik^2).
 // The rows a row references sit on earlier levels, finished by the barrier
 // that closes each level.  *flag = 1 when a pivot is not positive.
-__global__ void __launch_bounds__(kThreads) k_ic0_factor(PrecP Q, const int* rowptr, const int* col,
-                                                         const double* val, double* lv, double* ld, int* flag) {
+__global__ void __launch_bounds__(kThreads) k_ic0_factor(PrecSweep F, const int* lp, const int* lc,
+                                                         const int* rowptr, const int* col, const double* val,
+                                                         double* lv, double* ld, int* flag) {
   const int b = blockIdx.x;
-  for (int l = Q.fblk[b]; l < Q.fblk[b + 1]; l++) {
-    for (int q = Q.flev[l] + threadIdx.x; q < Q.flev[l + 1]; q += blockDim.x) {
-      const int i = Q.frows[q];
-      const int e0 = Q.lp[i], e1 = Q.lp[i + 1];
+  for (int l = F.blk[b]; l < F.blk[b + 1]; l++) {
+    for (int q = F.lev[l] + threadIdx.x; q < F.lev[l + 1]; q += blockDim.x) {
+      const int i = F.rows[q];
+      const int e0 = lp[i], e1 = lp[i + 1];
       for (int e = e0; e < e1; e++) {
-        const int j = Q.lc[e];
+        const int j = lc[e];
         double s = 0.0;
         for (int a = rowptr[i]; a < rowptr[i + 1]; a++)
           if (col[a] == j) s += val[a];
-        int u = e0, v = Q.lp[j];
-        const int vend = Q.lp[j + 1];
+        int u = e0, v = lp[j];
+        const int vend = lp[j + 1];
         while (u < e && v < vend) {
-          const int cu = Q.lc[u], cv = Q.lc[v];
+          const int cu = lc[u], cv = lc[v];
           if (cu == cv) {
             s -= lv[u] * lv[v];
             u++;
@@ -1349,54 +1354,77 @@ __global__ void __launch_bounds__(kThreads) k_ic0_factor(PrecP Q, const int* row
   }
 }
 
-// L^T values from L's through the transpose map, and FP32 copies.
-__global__ void k_prec_finish(int n, int nnz, const int* umap, const double* lv, const double* ld, double* uv,
-                              float* lvf, float* ldf, float* uvf) {
+// Level-ordered values of one sweep from the factor: val[e] = lv[map[e]],
+// diag[q] = ld[rows[q]], in FP64 and (when vf != nullptr) FP32.
+__global__ void k_prec_gather(int npos, int nent, const int* map, const int* rows, const double* lv,
+                              const double* ld, double* v, double* d, float* vf, float* df) {
   const int stride = gridDim.x * blockDim.x;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
-    const double u = lv[umap[e]];
-    uv[e] = u;
-    if (lvf) {
-      lvf[e] = (float)lv[e];
-      uvf[e] = (float)u;
-    }
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nent; e += stride) {
+    const double x = lv[map[e]];
+    v[e] = x;
+    if (vf) vf[e] = (float)x;
   }
-  if (ldf)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) ldf[i] = (float)ld[i];
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npos; q += stride) {
+    const double x = ld[rows[q]];
+    d[q] = x;
+    if (df) df[q] = (float)x;
+  }
 }
 
-// out = M^{-1} in = L^{-T} (L^{-1} in) for an n x w block (w columns), one
-// CTA per diagonal block; out receives y = L^{-1} in first and is then
-// overwritten by z = L^{-T} y, each row after the rows it depends on.
-template <typename T>
-__device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int w) {
-  const T* lv = (const T*)Q.lv;
-  const T* ld = (const T*)Q.ld;
-  const T* uv = (const T*)Q.uv;
-  for (int l = Q.fblk[b]; l < Q.fblk[b + 1]; l++) {
-    const int q0 = Q.flev[l];
-    const int items = (Q.flev[l + 1] - q0) * w;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int q = it / w, c = it - q * w;
-      const int i = Q.frows[q0 + q];
-      T s = in[(long long)i * w + c];
-      for (int e = Q.lp[i]; e < Q.lp[i + 1]; e++) s -= lv[e] * out[(long long)Q.lc[e] * w + c];
-      out[(long long)i * w + c] = s / ld[i];
+// One substitution sweep over the levels of block b for the columns
+// [c0, c0 + nc) of an n x w block: out_i = (src_i - sum_k val_k out_{col_k}) / diag
+// with src = in (forward) or out itself (backward, in place).  Rows of one
+// level are independent: each thread computes kU of them (all loads first,
+// then the stores), and a barrier closes the level.
+template <typename T, int KM, bool FWD>
+__device__ void prec_sweep(const PrecSweep& S, int b, const T* in, T* out, int w, int c0, int nc) {
+  constexpr int kU = 2;
+  const T* val = (const T*)S.val;
+  const T* diag = (const T*)S.diag;
+  const int K = S.K;
+  for (int l = S.blk[b]; l < S.blk[b + 1]; l++) {
+    const int q0 = S.lev[l];
+    const int items = (S.lev[l + 1] - q0) * nc;
+    for (int base = threadIdx.x; base < items; base += kU * blockDim.x) {
+      T sv[kU];
+      long long dst[kU];
+#pragma unroll
+      for (int u = 0; u < kU; u++) {
+        const int it = base + u * blockDim.x;
+        dst[u] = -1;
+        if (it < items) {
+          const int qi = it / nc;
+          const int q = q0 + qi;
+          const int c = c0 + (it - qi * nc);
+          const int i = S.rows[q];
+          const int cnt = S.cnt[q];
+          T acc = FWD ? in[(long long)i * w + c] : out[(long long)i * w + c];
+          if (KM > 0) {
+#pragma unroll
+            for (int k = 0; k < KM; k++)
+              if (k < cnt) acc -= val[(long long)q * K + k] * out[(long long)S.col[(long long)q * K + k] * w + c];
+          } else {
+            for (int k = 0; k < cnt; k++)
+              acc -= val[(long long)q * K + k] * out[(long long)S.col[(long long)q * K + k] * w + c];
+          }
+          sv[u] = acc / diag[q];
+          dst[u] = (long long)i * w + c;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kU; u++)
+        if (dst[u] >= 0) out[dst[u]] = sv[u];
     }
     __syncthreads();
   }
-  for (int l = Q.bblk[b]; l < Q.bblk[b + 1]; l++) {
-    const int q0 = Q.blev[l];
-    const int items = (Q.blev[l + 1] - q0) * w;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-      const int q = it / w, c = it - q * w;
-      const int i = Q.brows[q0 + q];
-      T s = out[(long long)i * w + c];
-      for (int e = Q.up[i]; e < Q.up[i + 1]; e++) s -= uv[e] * out[(long long)Q.uc[e] * w + c];
-      out[(long long)i * w + c] = s / ld[i];
-    }
-    __syncthreads();
-  }
+}
+
+// out = M^{-1} in = L^{-T} (L^{-1} in) for columns [c0, c0 + nc) of an n x w
+// block; out holds y = L^{-1} in after the first sweep.
+template <typename T, int KM>
+__device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int w, int c0, int nc) {
+  prec_sweep<T, KM, true>(Q.f, b, in, out, w, c0, nc);
+  prec_sweep<T, KM, false>(Q.b, b, in, out, w, c0, nc);
 }
 
 // The preconditioned generators of Section 3 (eq. (zsre2), (zmsd2),
@@ -1406,33 +1434,39 @@ __device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int
 //   otherwise: z = M^{-1} r_{k-1}, split by k_generate; for GEN_MSDO also
 //              the partial sums of beta_k = -V_{k-1}^T z of this block.
 // With in != nullptr: out = M^{-1} in for an n x w block (step-level call).
-template <typename T, int W>
+// Grid: blockIdx.x = diagonal block, blockIdx.y = group of kPrecCols
+// columns (the 1-column solves use blockIdx.y == 0 only).  KM bounds the
+// entries per row of both sweeps (0: any).
+constexpr int kPrecCols = 4;
+template <typename T, int W, int KM>
 __global__ void __launch_bounds__(kThreads) k_prec_solve(KP P, PrecP Q, int gw, const T* in, T* out, int w) {
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   const int b = blockIdx.x;
+  const int c0 = blockIdx.y * kPrecCols;
   if (in != nullptr) {
-    prec_solve_block<T>(Q, b, in, out, w);
+    if (c0 < w) prec_solve_block<T, KM>(Q, b, in, out, w, c0, min(kPrecCols, w - c0));
     return;
   }
   const int gen = st->gen;
   const T* vprev = (st->nq > 0) ? (const T*)P.desc[st->nq - 1].V : nullptr;
   if (gen == GEN_SRE) {
-    prec_solve_block<T>(Q, b, vprev, (T*)P.X, W);
+    if (c0 < W) prec_solve_block<T, KM>(Q, b, vprev, (T*)P.X, W, c0, min(kPrecCols, W - c0));
     return;
   }
+  if (blockIdx.y != 0) return;
   T* z = (T*)P.z;
-  prec_solve_block<T>(Q, b, (const T*)P.r, z, 1);
+  prec_solve_block<T, KM>(Q, b, (const T*)P.r, z, 1, 0, 1);
   if (gen != GEN_MSDO) return;
   // -V_{k-1}^T z over this block's rows: thread (g, c), c = column
   __shared__ double sred[kThreads];
   constexpr int G = kThreads / W;
   const int c = threadIdx.x % W, g = threadIdx.x / W;
-  const int q0 = Q.flev[Q.fblk[b]], q1 = Q.flev[Q.fblk[b + 1]];
+  const int q0 = Q.f.lev[Q.f.blk[b]], q1 = Q.f.lev[Q.f.blk[b + 1]];
   double acc = 0.0;
   if (g < G)
     for (int q = q0 + g; q < q1; q += G) {
-      const int i = Q.frows[q];
+      const int i = Q.f.rows[q];
       acc += (double)vprev[(long long)i * W + c] * (double)z[i];
     }
   sred[threadIdx.x] = acc;
