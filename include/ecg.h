@@ -38,6 +38,7 @@ extern "C" {
 #define ECG_ECUDA (-3)       /* a CUDA runtime call failed, or no device */
 #define ECG_EBREAKDOWN (-4)  /* a block became numerically rank deficient */
 #define ECG_ENOTSPD (-5)     /* a diagonal entry of A is not positive */
+#define ECG_ETIMEOUT (-6)    /* a bounded device-side wait ran out (batched solver) */
 
 /* Generator of the new block at iteration k (Sections 2-3). */
 #define ECG_SRE 0     /* SRE-CG2, Algorithm 1: W_k = A W_{k-1} */
@@ -260,6 +261,73 @@ int ecg_op_msdo_generate(ecg_ctx* ctx, const double* r, const double* P_prev,
  * other's results: issue them one after another. */
 int ecg_tdot_noalloc(int64_t n, int m, const double* const* X, const int* wx, const double* Y, int wy,
                      double* C, void* stream);
+
+
+/* ----------------------------------------------------------------------
+ * Batched solver.  Many independent systems A_s x_s = b_s of uneven size
+ * are solved together by truncated SRE-CG2 (Algorithm 1 with the window of
+ * Section 3: CGS2 against the last `trunc` blocks, then Pre-CholQR or
+ * A-CholQR) in ONE persistent cooperative kernel per solve (FP64) or per
+ * refinement round (mixed precision).  Each system gets a group of CTAs in
+ * proportion to its rows; the groups iterate independently, synchronised
+ * inside a group by bounded barriers.  The paper has no batched form: this
+ * is the per-system method of Algorithm 1 run side by side, with iterates
+ * equal (to rounding) to a separate solve of each system.  The matrices
+ * are stored in SELL-C-sigma form with slice height C and sort window sigma
+ * chosen by timing the product on the batch itself unless fixed in the
+ * options.
+ * ---------------------------------------------------------------------- */
+typedef struct ecg_batch ecg_batch;
+
+typedef struct {
+  int trunc;           /* window blocks, 1..4 (default 2: SRE-CG) */
+  int ortho;           /* ECG_PRE_CHOLQR (default) or ECG_A_CHOLQR */
+  int precision;       /* ECG_MIXED (default: FP32 inner solves, FP64 refinement) or ECG_FP64 */
+  double inner_tol;    /* mixed: lower bound of the inner relative tolerance (default 1e-5) */
+  int slice_height;    /* SELL slice height C in {8, 16, 32}; 0: autotune (default) */
+  int sort_window;     /* SELL sigma: rows sorted by length inside windows of sigma rows
+                          (1: no sorting); 0: autotune (default) */
+  int ctas_per_sm;     /* persistent CTAs per SM, 1..4 (0: as many as fit, at most 2) */
+  double wait_limit_s; /* bound of every device-side barrier wait (default 1.0) */
+  int debug_barrier_extra; /* testing only: > 0 makes every group barrier wait for that
+                              many arrivals that never come, so the first wait runs
+                              out after wait_limit_s and the solve returns
+                              ECG_ETIMEOUT (default 0) */
+  void* stream;        /* cudaStream_t; NULL: a stream the batch creates */
+} ecg_batch_opts;
+
+void ecg_batch_default_opts(ecg_batch_opts* opts);
+
+/* Create a batch of nsys systems.  A[s] and partition[s] as in ecg_create
+ * (host or device per A[s].on_device; copied).  All systems share t, which
+ * must be 4 or 8.  nsys must not exceed the number of persistent CTAs
+ * (ctas_per_sm x SMs).  Returns ECG_OK, ECG_EINVAL, ECG_ENOTSPD, ECG_ENOMEM
+ * or ECG_ECUDA; on error *out is NULL. */
+int ecg_batch_create(int nsys, const ecg_csr* A, const int32_t* const* partition, int t,
+                     const ecg_batch_opts* opts, ecg_batch** out);
+
+/* Solve every system: b[s], x0[s] (x0 may be NULL: all zero) and x_out[s]
+ * are n_s doubles, all host or all device pointers.  tol and maxit as in
+ * ecg_solve (FP64: rho_k <= tol rho_0 on the recursive residual; mixed:
+ * ||b - A x|| <= tol ||b - A x_0|| on the FP64 residual after a refinement
+ * round, maxit bounding the inner iterations of all rounds).  res (may be
+ * NULL) receives nsys results; their history arrays belong to the batch and
+ * stay valid until the next solve or destroy.  Returns ECG_OK when every
+ * system converged, else the first non-OK status (ECG_ENOCONV,
+ * ECG_EBREAKDOWN, ECG_ETIMEOUT), or ECG_EINVAL / ECG_ENOMEM / ECG_ECUDA. */
+int ecg_batch_solve(ecg_batch* batch, const double* const* b, const double* const* x0, double* const* x_out,
+                    double tol, int maxit, ecg_result* res);
+
+/* The layout the batch runs with: SELL slice height and sort window, the
+ * number of persistent CTAs, the autotuner's time of one product Y = A X
+ * over the whole batch in ms (0 when the layout was fixed), and whether the
+ * last solve replayed its rounds from a captured CUDA graph (1) or issued
+ * them directly because the capture was refused (0).  Any output pointer
+ * may be NULL. */
+int ecg_batch_layout(const ecg_batch* batch, int* slice_height, int* sort_window, int* ctas,
+                     double* spmm_ms, int* graph);
+
+void ecg_batch_destroy(ecg_batch* batch);
 
 #ifdef __cplusplus
 }

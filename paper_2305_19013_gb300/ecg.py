@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, ENOCONV, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTSPD = 0, 1, -1, -2, -3, -4, -5
+OK, ENOCONV, EINVAL, ENOMEM, ECUDA, EBREAKDOWN, ENOTSPD, ETIMEOUT = 0, 1, -1, -2, -3, -4, -5, -6
 SRE, MSDO, MODMSDO = 0, 1, 2
 PRE_CHOLQR, A_CHOLQR = 0, 1
 FP64, MIXED = 0, 1
@@ -57,6 +57,21 @@ class _Opts(C.Structure):
     ]
 
 
+class _BatchOpts(C.Structure):
+    _fields_ = [
+        ("trunc", C.c_int),
+        ("ortho", C.c_int),
+        ("precision", C.c_int),
+        ("inner_tol", C.c_double),
+        ("slice_height", C.c_int),
+        ("sort_window", C.c_int),
+        ("ctas_per_sm", C.c_int),
+        ("wait_limit_s", C.c_double),
+        ("debug_barrier_extra", C.c_int),
+        ("stream", C.c_void_p),
+    ]
+
+
 class _Result(C.Structure):
     _fields_ = [
         ("iters", C.c_int),
@@ -94,6 +109,11 @@ SIGNATURES = {
     "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
     "ecg_tdot_noalloc": (_I, [C.c_int64, _I, _P, _P, _P, _I, _P, _P]),
     "ecg_set_preconditioner": (_I, [_P, _P, _I, _I]),
+    "ecg_batch_default_opts": (None, [C.POINTER(_BatchOpts)]),
+    "ecg_batch_create": (_I, [_I, _P, _P, _I, C.POINTER(_BatchOpts), C.POINTER(_P)]),
+    "ecg_batch_solve": (_I, [_P, _P, _P, _P, _D, _I, _P]),
+    "ecg_batch_layout": (_I, [_P, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I), C.POINTER(_D), C.POINTER(_I)]),
+    "ecg_batch_destroy": (None, [_P]),
     "ecg_op_prec_apply": (_I, [_P, _P, _P, _I]),
 }
 
@@ -432,6 +452,114 @@ class Solver:
         )
         return P
 
+
+
+class BatchSolver:
+    """Many independent systems solved together by truncated SRE-CG2 in one
+    persistent launch per round (ecg_batch_* in include/ecg.h)."""
+
+    def __init__(
+        self,
+        problems,
+        trunc: int = 2,
+        ortho: int = PRE_CHOLQR,
+        precision: int = MIXED,
+        inner_tol: float = 1e-5,
+        slice_height: int = 0,
+        sort_window: int = 0,
+        ctas_per_sm: int = 0,
+        wait_limit_s: float = 1.0,
+        debug_barrier_extra: int = 0,
+        stream=None,
+    ):
+        self._lib = load()
+        self._ctx = None
+        ts = {int(p.t) for p in problems}
+        if len(ts) != 1:
+            raise ValueError("all systems of a batch share t")
+        self.t = ts.pop()
+        self.ns = [int(p.n) for p in problems]
+        self._keep = []
+        csrs = (_Csr * len(problems))()
+        parts = (C.c_void_p * len(problems))()
+        for k, p in enumerate(problems):
+            rp = np.ascontiguousarray(p.rowptr, dtype=np.int64)
+            ci = np.ascontiguousarray(p.col, dtype=np.int32)
+            va = np.ascontiguousarray(p.val, dtype=np.float64)
+            pt = np.ascontiguousarray(p.part, dtype=np.int32)
+            self._keep += [rp, ci, va, pt]
+            csrs[k] = _Csr(int(p.n), int(len(ci)), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0)
+            parts[k] = pt.ctypes.data
+        o = _BatchOpts()
+        self._lib.ecg_batch_default_opts(C.byref(o))
+        o.trunc, o.ortho, o.precision, o.inner_tol = int(trunc), int(ortho), int(precision), float(inner_tol)
+        o.slice_height, o.sort_window, o.ctas_per_sm = int(slice_height), int(sort_window), int(ctas_per_sm)
+        o.wait_limit_s, o.debug_barrier_extra = float(wait_limit_s), int(debug_barrier_extra)
+        o.stream = stream
+        ctx = C.c_void_p()
+        rc = self._lib.ecg_batch_create(len(problems), csrs, parts, self.t, C.byref(o), C.byref(ctx))
+        self._keep = []
+        if rc != OK:
+            raise EcgError(rc, "ecg_batch_create")
+        self._ctx = ctx
+
+    def layout(self) -> dict:
+        c, s, g, ms, gr = _I(), _I(), _I(), _D(), _I()
+        self._lib.ecg_batch_layout(self._ctx, C.byref(c), C.byref(s), C.byref(g), C.byref(ms), C.byref(gr))
+        return {"slice_height": c.value, "sort_window": s.value, "ctas": g.value, "spmm_ms": ms.value,
+                "graph": bool(gr.value)}
+
+    def solve(self, bs, x0s=None, tol: float = 1e-8, maxit: int = 1000, outs=None):
+        """bs: list of n_s arrays (numpy, or torch CUDA tensors).  Returns
+        (status of the batch, list of SolveResult)."""
+        ns = len(self.ns)
+        dev = _is_torch_cuda(bs[0])
+        if outs is None:
+            if dev:
+                import torch
+
+                outs = [torch.empty(n, dtype=torch.float64, device=bs[0].device) for n in self.ns]
+            else:
+                outs = [np.empty(n) for n in self.ns]
+        keep = [np.ascontiguousarray(b, dtype=np.float64) if not dev else b for b in bs]
+        bp = (C.c_void_p * ns)(*[_ptr(b) for b in keep])
+        xp = None
+        if x0s is not None:
+            keep0 = [np.ascontiguousarray(x, dtype=np.float64) if not dev else x for x in x0s]
+            xp = (C.c_void_p * ns)(*[_ptr(x) for x in keep0])
+        op = (C.c_void_p * ns)(*[_ptr(x) for x in outs])
+        res = (_Result * ns)()
+        rc = self._lib.ecg_batch_solve(self._ctx, bp, xp, op, float(tol), int(maxit), res)
+        if rc < 0 and rc not in (EBREAKDOWN, ETIMEOUT):
+            raise EcgError(rc, "ecg_batch_solve")
+        out = []
+        for k in range(ns):
+            r = res[k]
+            hist = np.ctypeslib.as_array(r.history, shape=(r.iters + 1,)).copy() if r.history else np.zeros(1)
+            out.append(
+                SolveResult(
+                    x=outs[k], iters=r.iters, switch_it=0, status=r.status, mem_vectors=r.mem_vectors,
+                    relres=r.relres, relres_true=r.relres_true, device_ms=r.device_ms, history=hist,
+                )
+            )
+        return rc, out
+
+    def close(self):
+        if self._ctx is not None:
+            self._lib.ecg_batch_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def tdot_noalloc(Xs, Y, out=None, stream=None):
