@@ -135,6 +135,57 @@ def algorithmic_counts(n, nnz, t, trunc, K):
     return fl, byts
 
 
+# Algorithmic DRAM bytes of one row-iteration of the batched kernel (FP32,
+# t = 8, window of 2, Pre-CholQR): P1 96, P2 192, P3 128, P4 64, P5 112,
+# P6 144 (each n x 8 FP32 row is 32 B; P5 counts the SELL entries and each
+# gathered row once).
+BATCH_BYTES_PER_ROW_ITER = 736
+
+
+def batch_run(torch):
+    """The batched workload: 64 independent 2D diffusion systems, sides
+    uniform in {128, ..., 512}, log-normal coefficients, t = 8, FP32 inner
+    solves with FP64 refinement to 1e-8, one persistent launch per round.
+    Timed after one untimed solve, device resident right-hand sides."""
+    from paper_2305_19013_gb300 import ecg
+    from paper_2305_19013_gb300 import workloads as Wk
+
+    ps = Wk.batch_diffusion2d(64)
+    t0 = time.perf_counter()
+    bs = ecg.BatchSolver(ps, precision=ecg.MIXED)
+    t_create = time.perf_counter() - t0
+    bd = [torch.from_numpy(p.b).cuda() for p in ps]
+    bs.solve(bd, tol=1e-8, maxit=30000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, res = bs.solve(bd, tol=1e-8, maxit=30000)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    row_iters = sum(p.n * g.iters for p, g in zip(ps, res))
+    achieved = BATCH_BYTES_PER_ROW_ITER * row_iters / dt / 1e9
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    out = {
+        "workload": "64 x 2D diffusion, sides 128..512, t=8, FP32 inner + FP64 refinement, tol 1e-8",
+        "status": rc,
+        "seconds": dt,
+        "systems_per_s": len(ps) / dt,
+        "rows": sum(p.n for p in ps),
+        "iters_min": min(g.iters for g in res),
+        "iters_max": max(g.iters for g in res),
+        "max_relres_true": max(g.relres_true for g in res),
+        "layout": bs.layout(),
+        "create_seconds": t_create,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if hbm else None,
+                     "algorithmic_bytes_per_row_iteration": BATCH_BYTES_PER_ROW_ITER,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if hbm else None},
+    }
+    bs.close()
+    return out
+
+
+
 def run_oracle_sample(K, W, trunc):
     """The FP64 CPU oracle (single thread) on a 1/16 row sample of the
     workload: the 256 x 256 version of the same coefficient layout (16 x 16
@@ -200,6 +251,8 @@ def main():
     ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
     ap.add_argument("--time-to-tol-only", default="", help="only the time-to-tol runs whose name contains this")
     ap.add_argument("--prec-blocks", type=int, default=64, help="block Jacobi blocks for the preconditioned runs")
+    ap.add_argument("--batch", action="store_true",
+                    help="also solve the batched workload (64 uneven 2D diffusion systems, t=8) and report it")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -367,6 +420,8 @@ def main():
                 if pre:
                     ttt[name]["setup_seconds"] = t_setup
         line["time_to_tol"] = ttt
+    if args.batch:
+        line["batch"] = batch_run(torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_oracle_sample(8, 1, args.trunc)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

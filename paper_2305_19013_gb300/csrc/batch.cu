@@ -209,23 +209,36 @@ BatchP make_bp(const ecg_batch* b, bool fp32) {
   return B;
 }
 
-template <typename T, int W>
-const void* inner_kernel(int m) {
-  switch (m) {
-    case 1: return (const void*)k_batch_sre<T, W, 1>;
-    case 2: return (const void*)k_batch_sre<T, W, 2>;
-    case 3: return (const void*)k_batch_sre<T, W, 3>;
-    case 4: return (const void*)k_batch_sre<T, W, 4>;
-  }
-  return nullptr;
+struct InnerK {
+  const void* fn = nullptr;
+  int smem = 0;  // dynamic shared memory (bytes)
+};
+
+template <typename T, int W, int MM>
+InnerK inner_k() {
+  InnerK k;
+  k.fn = (const void*)k_batch_sre<T, W, MM>;
+  k.smem = BGeom<T, W, MM>::SMEM;
+  return k;
 }
 
-const void* inner_kernel_for(bool fp32, int t, int m) {
+template <typename T, int W>
+InnerK inner_kernel(int m) {
+  switch (m) {
+    case 1: return inner_k<T, W, 1>();
+    case 2: return inner_k<T, W, 2>();
+    case 3: return inner_k<T, W, 3>();
+    case 4: return inner_k<T, W, 4>();
+  }
+  return InnerK();
+}
+
+InnerK inner_kernel_for(bool fp32, int t, int m) {
   switch (t) {
     case 4: return fp32 ? inner_kernel<float, 4>(m) : inner_kernel<double, 4>(m);
     case 8: return fp32 ? inner_kernel<float, 8>(m) : inner_kernel<double, 8>(m);
   }
-  return nullptr;
+  return InnerK();
 }
 
 // One cooperative launch of the persistent inner solve over G CTAs.
@@ -234,16 +247,17 @@ int launch_inner(ecg_batch* b, bool fp32) {
   void* args[] = {&B};
   cudaLaunchConfig_t cfg;
   std::memset(&cfg, 0, sizeof(cfg));
+  const InnerK k = inner_kernel_for(fp32, b->t, b->o.trunc);
   cfg.gridDim = dim3(b->G);
   cfg.blockDim = dim3(kBThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = (size_t)k.smem;
   cfg.stream = b->stream;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeCooperative;
   attr.val.cooperative = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  BCK(cudaLaunchKernelExC(&cfg, inner_kernel_for(fp32, b->t, b->o.trunc), args));
+  BCK(cudaLaunchKernelExC(&cfg, k.fn, args));
   return ECG_OK;
 }
 
@@ -302,30 +316,38 @@ int time_spmm(ecg_batch* b, const Sell& S, double* ms_out) {
   return ECG_OK;
 }
 
-// CTA groups: system s gets gsize_s CTAs in proportion to its rows (at
-// least one); CTA q of the group owns an even share of the rows and of the
-// SELL slices.
+// CTA groups: system s gets gsize_s CTAs (at least one) in proportion to
+// its expected work, rows times iterations.  The iterations of CG-type
+// methods grow like sqrt(kappa), and kappa like n for the 2D diffusion
+// systems the batch is built for, so the weight is n^{3/2}: on the 64-system
+// workload (n from 16K to 262K) the iteration counts span the same 4-5x as
+// sqrt(n).  CTA q of a group owns an even share of its rows and slices.
 void place_ctas(ecg_batch* b, const Sell& S) {
   const int ns = b->nsys, G = b->G;
   std::vector<int> gs(ns);
-  long long tot = 0;
-  for (int s = 0; s < ns; s++) tot += b->n[s];
+  std::vector<double> w(ns);
+  double tot = 0.0;
+  for (int s = 0; s < ns; s++) {
+    w[s] = (double)b->n[s] * std::sqrt((double)b->n[s]);
+    tot += w[s];
+  }
   int sum = 0;
   for (int s = 0; s < ns; s++) {
-    gs[s] = std::max(1, (int)((long long)G * b->n[s] / tot));
+    gs[s] = std::max(1, std::min(b->n[s], (int)((double)G * w[s] / tot)));
     sum += gs[s];
   }
-  while (sum > G) {  // take from the system with the most CTAs
+  while (sum > G) {  // take from the system with the least work per CTA
     int best = -1;
     for (int s = 0; s < ns; s++)
-      if (gs[s] > 1 && (best < 0 || gs[s] > gs[best])) best = s;
+      if (gs[s] > 1 && (best < 0 || w[s] / gs[s] < w[best] / gs[best])) best = s;
     gs[best]--;
     sum--;
   }
-  while (sum < G) {  // give to the system with the most rows per CTA
-    int best = 0;
-    for (int s = 1; s < ns; s++)
-      if ((double)b->n[s] / gs[s] > (double)b->n[best] / gs[best]) best = s;
+  while (sum < G) {  // give to the system with the most work per CTA
+    int best = -1;
+    for (int s = 0; s < ns; s++)
+      if (gs[s] < b->n[s] && (best < 0 || w[s] / gs[s] > w[best] / gs[best])) best = s;
+    if (best < 0) break;
     gs[best]++;
     sum++;
   }
@@ -517,14 +539,15 @@ int ecg_batch_create(int nsys, const ecg_csr* A, const int32_t* const* partition
     b->own_stream = true;
   }
   if (cudaEventCreate(&b->e0) != cudaSuccess || cudaEventCreate(&b->e1) != cudaSuccess) return fail(ECG_ECUDA);
-  // persistent CTAs: as many per SM as the larger (FP64) instantiation fits
+  // persistent CTAs: as many per SM as the inner solve's kernel fits
   int per_sm = 0;
-  for (int fp = 0; fp < 2; fp++) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, inner_kernel_for(fp == 1, t, o.trunc), kBThreads, 0) !=
-        cudaSuccess)
+  {
+    const InnerK k = inner_kernel_for(o.precision == ECG_MIXED, t, o.trunc);
+    if (cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, kBThreads, (size_t)k.smem) != cudaSuccess) {
+      cudaGetLastError();
       return fail(ECG_ECUDA);
-    per_sm = (fp == 0) ? nb : std::min(per_sm, nb);
+    }
   }
   if (per_sm < 1) return fail(ECG_ECUDA);
   const int want = o.ctas_per_sm ? o.ctas_per_sm : std::min(2, per_sm);

@@ -116,6 +116,8 @@ __device__ __forceinline__ unsigned b_ld_acquire(const unsigned* p) {
 // Barrier of one group: arrival count reaches epoch * gsize (+ bar_extra).
 // Returns false (uniformly over the CTA) when the wait ran out.
 __device__ bool b_group_barrier(const BatchP& B, const CtaInfo& ci, unsigned& epoch, int* sflag) {
+  // this thread's generic-proxy writes become visible to later bulk copies
+  asm volatile("fence.proxy.async.global;" ::: "memory");
   __syncthreads();
   epoch++;  // every thread keeps the count (it selects the partial buffers)
   if (threadIdx.x == 0) {
@@ -270,13 +272,74 @@ __device__ __forceinline__ void b_load_row(const T* base, long long i, T (&v)[W]
   }
 }
 
+// ------------------------------------------------------ bulk-copy row tiles
+//
+// The phases that stream whole n x W blocks over a CTA's own rows (P1-P4,
+// P6) receive them as row tiles through cp.async.bulk (the TMA engine) into
+// a shared-memory ring with one mbarrier per stage counting
+// the bytes.  The mbarriers are initialised once per launch; tiles are numbered by
+// a counter that runs across phases, so stage g % S completes its phase
+// with parity (g / S) & 1.  Every wait is bounded by
+// %globaltimer.  Generic-proxy writes of a block (X, Y, the window) are
+// made visible to later bulk copies by fence.proxy.async at every group
+// barrier.
+
+__device__ __forceinline__ uint32_t b_smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void b_mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void b_mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool b_mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(b_smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void b_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   b_smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(b_smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool b_mbar_wait(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (b_mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = b_globaltimer();
+  for (long long p = 0; p < (1LL << 30); p++) {
+    if (b_mbar_try_wait(bar, parity)) return true;
+    if ((p & 63) == 63 && b_globaltimer() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+
+// Rows of a tile (one per row group) and the shared memory of the kernel.
+template <typename T, int W, int MM>
+struct BGeom {
+  // columns per thread: the CGS coefficients a thread accumulates
+  // (MM x W x CPT) stay within 64 registers' worth
+  static constexpr int CPT = (MM * W * W <= 64) ? W : ((MM * W * (W / 2) <= 64) ? W / 2 : (W >= 4 ? W / 4 : 1));
+  static constexpr int SPL = W / CPT;          // threads per row
+  static constexpr int RG = kBThreads / SPL;   // rows per pass of the CTA = rows per tile
+  static constexpr int ROWB = W * (int)sizeof(T);
+  static constexpr int MAXS = 1 + 2 * MM;      // streams of the busiest phase (P2)
+  static constexpr int STAGE = MAXS * RG * ROWB;
+  // two stages: deeper rings took L1 capacity from the SpMM's gathers and
+  // ran slower on the 64-system workload
+  static constexpr int S = 2;
+  static constexpr int SMEM = 64 + S * STAGE;
+};
+
 // The persistent inner solve: SRE-CG2 truncated to M window blocks (M = B.m
 // at most MM), block width W, scalar T, for every system of the batch.
 template <typename T, int W, int MM>
-__global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
-  constexpr int CPT = (MM * W * W <= 64) ? W : ((MM * W * (W / 2) <= 64) ? W / 2 : (W >= 4 ? W / 4 : 1));
-  constexpr int SPL = W / CPT;      // threads per row
-  constexpr int RG = kBThreads / SPL;  // rows in flight per CTA
+__global__ void __launch_bounds__(kBThreads, sizeof(T) == 4 ? 2 : 1) k_batch_sre(BatchP B) {
+  using G_ = BGeom<T, W, MM>;
+  constexpr int CPT = G_::CPT, SPL = G_::SPL, RG = G_::RG, ROWB = G_::ROWB, kS = G_::S;
   constexpr int NA1 = MM * W * CPT;    // CGS accumulators per thread
   constexpr int NAG = W * CPT + CPT;   // Gram (+ rhs) accumulators per thread
   __shared__ double sred[(kBThreads / 32) * SPL * (NA1 > NAG ? NA1 : NAG)];
@@ -287,6 +350,9 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
   __shared__ T salpha[W];
   __shared__ int sflag;
   __shared__ double srho;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  uint64_t* pbar = (uint64_t*)bsm;
+  unsigned char* pstage = bsm + 64;
   const CtaInfo ci = B.cta[blockIdx.x];
   SysState* st = B.st + ci.sys;
   if (st->status != B_RUN) return;
@@ -303,11 +369,63 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
   auto fail = [&](int code) {
     if (threadIdx.x == 0) atomicCAS(&st->status, B_RUN, code);
   };
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kS; s++) b_mbar_init(&pbar[s]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  unsigned gt = 0;  // tiles issued in earlier phases (same in every thread)
+
+  // Stream nstr blocks (bases[j], n x W) over the CTA's rows in tiles of RG
+  // rows and call body(i, tile) for row i of every tile, tile(j) being row
+  // i of stream j in shared memory.  False after a wait ran out (the copies
+  // still in flight are waited for, boundedly).
+  auto stream_rows = [&](int nstr, const T* const* bases, auto&& body) -> bool {
+    const int ntiles = (ci.r1 - ci.r0 + RG - 1) / RG;
+    auto issue = [&](int t) {
+      const unsigned g = gt + (unsigned)t;
+      const int s = (int)(g % kS);
+      const int row0 = ci.r0 + t * RG;
+      const int nr = min(RG, ci.r1 - row0);
+      b_mbar_expect_tx(&pbar[s], (uint32_t)(nstr * nr * ROWB));
+      unsigned char* dst = pstage + (long long)s * G_::STAGE;
+      for (int j = 0; j < nstr; j++)
+        b_bulk_g2s(dst + (long long)j * RG * ROWB, (const unsigned char*)bases[j] + (long long)row0 * ROWB,
+                   (uint32_t)(nr * ROWB), &pbar[s]);
+    };
+    if (threadIdx.x == 0)
+      for (int t = 0; t < min(kS, ntiles); t++) issue(t);
+    bool ok = true;
+    for (int t = 0; t < ntiles; t++) {
+      const unsigned g = gt + (unsigned)t;
+      const bool w = b_mbar_wait(&pbar[g % kS], (g / kS) & 1u, B.wait_ns);
+      if (!__syncthreads_and(w)) {
+        if (threadIdx.x == 0)
+          for (int u = t; u < min(t + kS, ntiles); u++)
+            b_mbar_wait(&pbar[(gt + u) % kS], ((gt + u) / kS) & 1u, B.wait_ns);
+        __syncthreads();
+        ok = false;
+        break;
+      }
+      const int row0 = ci.r0 + t * RG;
+      const int nr = min(RG, ci.r1 - row0);
+      const T* stg = (const T*)(pstage + (long long)(g % kS) * G_::STAGE);
+      if (rg < nr) body(row0 + rg, [&](int j) { return stg + ((long long)j * RG + rg) * W; });
+      __syncthreads();
+      if (threadIdx.x == 0 && t + kS < ntiles) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        issue(t + kS);
+      }
+    }
+    gt += (unsigned)ntiles;
+    return ok;
+  };
+
   // local copies of the group's state, identical in every CTA
   int k = st->k, nq = st->nq, head = st->head;
   const int kmax = st->kmax;
   const double eps = st->eps;
-  double rho0, rho_prev;
+  double rho0;
   auto wslot = [&](int j) { return (head + j) % m; };
   auto QWb = [&](int slot) { return (T*)B.QW + (long long)slot * B.slot_stride; };
   auto QVb = [&](int slot) { return (T*)B.QV + (long long)slot * B.slot_stride; };
@@ -326,51 +444,43 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
     }
     __syncthreads();
     rho0 = srho;
-    rho_prev = rho0;
     if (ci.q == 0 && threadIdx.x == 0) {
       st->rho0 = rho0;
       st->rho = rho0;
       if (st->hist_off < B.hist_cap) B.hist[(long long)ci.sys * B.hist_cap + st->hist_off] = rho0 * st->scale;
     }
-    if (!(rho0 > 0.0) || !(rho_prev > eps * rho0) || k >= kmax) {
-      if (ci.q == 0 && threadIdx.x == 0) st->status = (rho_prev > eps * rho0) ? B_NOCONV : B_OK;
+    if (!(rho0 > 0.0) || !(rho0 > eps * rho0) || k >= kmax) {
+      if (ci.q == 0 && threadIdx.x == 0) st->status = (rho0 > eps * rho0) ? B_NOCONV : B_OK;
       return;
     }
   }
 
   for (;;) {
-    const bool split = (k == 1);
+    const int nwin = nq;  // window blocks used by CGS; k >= 2 <=> nwin >= 1
     const T* vprev = (nq > 0) ? QVb(wslot(nq - 1)) : nullptr;
-    const int nwin = nq;  // window blocks used by CGS
-    // generated row, my columns
-    auto gen = [&](int i, T (&xc)[CPT]) {
-      if (split) {
-        const int pj = B.part[i];
-        const T ri = r[i];
-#pragma unroll
-        for (int c = 0; c < CPT; c++) xc[c] = (c0 + c == pj) ? ri : T(0);
-      } else {
-#pragma unroll
-        for (int c = 0; c < CPT; c++) xc[c] = vprev[(long long)i * W + c0 + c];
-      }
-    };
-    // ---- P1, P2: CGS2 against the window
+    // ---- P1, P2: CGS2 against the window (X = V_{k-1} for k >= 2)
     if (nwin > 0) {
       for (int pass = 0; pass < 2; pass++) {
         T acc[NA1];
 #pragma unroll
         for (int e = 0; e < NA1; e++) acc[e] = T(0);
         if (pass == 1) b_group_sum<T>(B, ci, epoch, nwin * W * W, sC);
-        for (int i = ci.r0 + rg; i < ci.r1; i += RG) {
+        // streams: vprev, [Q_0 .. Q_{nwin-1}] (pass 1), V_0 .. V_{nwin-1}
+        const T* bases[G_::MAXS];
+        int ns = 0;
+        bases[ns++] = vprev;
+        if (pass == 1)
+          for (int j = 0; j < nwin; j++) bases[ns++] = QWb(wslot(j));
+        const int vbase = ns;
+        for (int j = 0; j < nwin; j++) bases[ns++] = QVb(wslot(j));
+        const bool ok = stream_rows(ns, bases, [&](int i, auto&& row) {
           T xc[CPT];
-          if (pass == 0) {
-            gen(i, xc);
-          } else {
-            gen(i, xc);  // X - Q C1 from the generator again (X is not stored in pass 1)
+          const T* g0 = row(0);
+#pragma unroll
+          for (int c = 0; c < CPT; c++) xc[c] = g0[c0 + c];
+          if (pass == 1) {  // X - Q C1, regenerated from V_{k-1}
             for (int j = 0; j < nwin; j++) {
-              const T* Qj = QWb(wslot(j));
-              T qr[W];
-              b_load_row<T, W>(Qj, i, qr);
+              const T* qr = row(1 + j);
 #pragma unroll
               for (int a = 0; a < W; a++)
 #pragma unroll
@@ -382,44 +492,27 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
 #pragma unroll
           for (int j = 0; j < MM; j++) {
             if (j < nwin) {
-              const T* Vj = QVb(wslot(j));
-              T vr[W];
-              b_load_row<T, W>(Vj, i, vr);
+              const T* vr = row(vbase + j);
 #pragma unroll
               for (int a = 0; a < W; a++)
 #pragma unroll
                 for (int c = 0; c < CPT; c++) acc[(j * W + a) * CPT + c] += vr[a] * xc[c];
             }
           }
-        }
+        });
+        if (!ok) return fail(B_TIMEOUT);
         b_cta_reduce<T, SPL, NA1>(acc, sred, b_part_w(B, epoch),
                                   [](int s, int e) { return (e / CPT) * W + s * CPT + (e % CPT); });
         if (!b_group_barrier(B, ci, epoch, &sflag)) return fail(B_TIMEOUT);
       }
     }
-    // ---- P3: X -= Q C2 (or X = generator when the window is empty); G_e
+    // ---- P3: X -= Q C2 (or X = [T(r)] at k = 1); G_e = X^T X
     {
       if (nwin > 0) b_group_sum<T>(B, ci, epoch, nwin * W * W, sC);
       T acc[NAG];
 #pragma unroll
       for (int e = 0; e < NAG; e++) acc[e] = T(0);
-      for (int i = ci.r0 + rg; i < ci.r1; i += RG) {
-        T xc[CPT];
-        if (nwin > 0) {
-#pragma unroll
-          for (int c = 0; c < CPT; c++) xc[c] = X[(long long)i * W + c0 + c];
-          for (int j = 0; j < nwin; j++) {
-            const T* Qj = QWb(wslot(j));
-            T qr[W];
-            b_load_row<T, W>(Qj, i, qr);
-#pragma unroll
-            for (int a = 0; a < W; a++)
-#pragma unroll
-              for (int c = 0; c < CPT; c++) xc[c] -= qr[a] * sC[(j * W + a) * W + c0 + c];
-          }
-        } else {
-          gen(i, xc);
-        }
+      auto finish_row = [&](int i, T (&xc)[CPT]) {
 #pragma unroll
         for (int c = 0; c < CPT; c++) X[(long long)i * W + c0 + c] = xc[c];
         if (B.pre) {
@@ -433,6 +526,36 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
           for (int a = 0; a < W; a++)
 #pragma unroll
             for (int c = 0; c < CPT; c++) acc[a * CPT + c] += xr[a] * xc[c];
+        }
+      };
+      if (nwin > 0) {
+        const T* bases[G_::MAXS];
+        int ns = 0;
+        bases[ns++] = X;
+        for (int j = 0; j < nwin; j++) bases[ns++] = QWb(wslot(j));
+        const bool ok = stream_rows(ns, bases, [&](int i, auto&& row) {
+          T xc[CPT];
+          const T* xr0 = row(0);
+#pragma unroll
+          for (int c = 0; c < CPT; c++) xc[c] = xr0[c0 + c];
+          for (int j = 0; j < nwin; j++) {
+            const T* qr = row(1 + j);
+#pragma unroll
+            for (int a = 0; a < W; a++)
+#pragma unroll
+              for (int c = 0; c < CPT; c++) xc[c] -= qr[a] * sC[(j * W + a) * W + c0 + c];
+          }
+          finish_row(i, xc);
+        });
+        if (!ok) return fail(B_TIMEOUT);
+      } else {  // k = 1: [T^t(r_0)]
+        for (int i = ci.r0 + rg; i < ci.r1; i += RG) {
+          T xc[CPT];
+          const int pj = B.part[i];
+          const T ri = r[i];
+#pragma unroll
+          for (int c = 0; c < CPT; c++) xc[c] = (c0 + c == pj) ? ri : T(0);
+          finish_row(i, xc);
         }
       }
       if (B.pre) {
@@ -449,21 +572,18 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
         if (ci.q == 0 && threadIdx.x == 0) atomicCAS(&st->status, B_RUN, B_BREAKDOWN);
         return;
       }
-      for (int i = ci.r0 + rg; i < ci.r1; i += RG) {
-        T xr[W];
-        b_load_row<T, W>(X, i, xr);
-        T q[CPT];
+      const T* bases[1] = {X};
+      const bool ok = stream_rows(1, bases, [&](int i, auto&& row) {
+        const T* xr = row(0);
 #pragma unroll
         for (int c = 0; c < CPT; c++) {
           T s = T(0);
 #pragma unroll
           for (int a = 0; a < W; a++) s += xr[a] * sRe[a * W + c0 + c];
-          q[c] = s;
+          X[(long long)i * W + c0 + c] = s;
         }
-        __syncwarp(gmask);  // all lanes of the row read X before any writes it
-#pragma unroll
-        for (int c = 0; c < CPT; c++) X[(long long)i * W + c0 + c] = q[c];
-      }
+      });
+      if (!ok) return fail(B_TIMEOUT);
       if (!b_group_barrier(B, ci, epoch, &sflag)) return fail(B_TIMEOUT);
     }
     // ---- P5: Y = A X over my slots; G = X^T Y, g = X^T r
@@ -520,10 +640,10 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
       T* Wn = QWb(newslot);
       T* Vn = QVb(newslot);
       double racc = 0.0;
-      for (int i = ci.r0 + rg; i < ci.r1; i += RG) {
-        T xr[W], yr[W];
-        b_load_row<T, W>(X, i, xr);
-        b_load_row<T, W>(Y, i, yr);
+      const T* bases[2] = {X, Y};
+      const bool ok = stream_rows(2, bases, [&](int i, auto&& row) {
+        const T* xr = row(0);
+        const T* yr = row(1);
         T dx = T(0), dr = T(0);
 #pragma unroll
         for (int c = 0; c < CPT; c++) {
@@ -549,7 +669,8 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
           r[i] = rn;
           racc += (double)rn * (double)rn;
         }
-      }
+      });
+      if (!ok) return fail(B_TIMEOUT);
       double accs[1] = {racc};
       b_cta_reduce<double, 1, 1>(accs, sred, b_part_w(B, epoch), [](int, int) { return 0; });
       if (!b_group_barrier(B, ci, epoch, &sflag)) return fail(B_TIMEOUT);
@@ -577,12 +698,10 @@ __global__ void __launch_bounds__(kBThreads) k_batch_sre(BatchP B) {
       if (st->hist_off + k < B.hist_cap) B.hist[(long long)ci.sys * B.hist_cap + st->hist_off + k] = rho * st->scale;
       if (status != B_RUN) atomicCAS(&st->status, B_RUN, status);
     }
-    rho_prev = rho;
     k = knext;
     if (status != B_RUN) return;
   }
 }
-
 
 // ------------------------------------------------------------ outer loop
 
