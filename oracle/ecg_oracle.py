@@ -15,6 +15,8 @@ Conjugate Gradient methods", arXiv 2305.19013):
 - ``ecg_solve``: SRE-CG2, MSDO-CG, modified MSDO-CG, truncated and flexible
   forms (Algorithms 1-4, Section 3).
 - ``cg_solve``: classical CG (Section 1).
+- ``becg_solve``: the block-residual enlarged CG mentioned in Section 1
+  (R_0 = [T^t(r_0)], x = x_0 + sum of the block solution's columns).
 - ``BlockJacobi``: the block Jacobi preconditioner M = L L^T of Section 3
   ("Preconditioned versions") and Section 5, with exact Cholesky or IC(0)
   diagonal blocks; ``ecg_solve(..., prec=...)`` runs the preconditioned
@@ -108,6 +110,7 @@ def _load():
         "or_prec_ltsolve": (None, [_P, _INT, _P]),
         "or_prec_apply": (None, [_P, _INT, _P]),
         "or_cg_solve": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P, _P]),
+        "or_becg_solve": (_INT, [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _P]),
         "or_mem_flexible": (_I64, [_INT, _INT, _INT]),
     }
     for name, (res, args) in sigs.items():
@@ -320,6 +323,37 @@ def ecg_solve(
         xhist=None if xh is None else xh[: res.iters].copy(),
         basis=blocks,
         restarts=res.restarts,
+    )
+
+
+def becg_solve(A, part, t, b, x0=None, tol=1e-8, maxit=1000, trunc=0, ortho=0, keep_x=False):
+    """Block-residual enlarged CG (Section 1): SRE-CG's direction blocks,
+    t x t coefficients alpha_k = W_k^T R_{k-1}, x = x_0 + X_k 1.  Returns an
+    OracleResult whose ``basis`` holds the final n x t block solution X."""
+    rp, ci, va, n = _csr(A)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    b = _f64(b)
+    x0a = None if x0 is None else _f64(x0)
+    x = np.empty(n)
+    hist = np.zeros(max(maxit, 1))
+    xh = np.zeros((max(maxit - 1, 1), n)) if keep_x else None
+    Xb = np.zeros((n, t))
+    res = _Res()
+    _load().or_becg_solve(
+        n, _p(rp), _p(ci), _p(va), _p(part), t, trunc, ortho, _p(b), _p(x0a), tol, maxit, _p(x), _p(hist), _p(xh),
+        _p(Xb), C.byref(res),
+    )
+    return OracleResult(
+        x=x,
+        iters=res.iters,
+        switch_it=0,
+        status=res.status,
+        mem_vectors=res.mem_vectors,
+        relres=res.relres,
+        relres_true=res.relres_true,
+        history=hist[: res.iters + 1].copy(),
+        xhist=None if xh is None else xh[: res.iters].copy(),
+        basis=[Xb],
     )
 
 

@@ -202,3 +202,47 @@ def test_prec_setup_rejects_bad_blocks():
     bad[0] = 5
     with pytest.raises(ValueError):
         O.BlockJacobi(p.scipy(), bad, 2, O.PREC_IC0)  # id out of range
+
+
+# ------------------------------------------------- block-residual ECG (Section 1)
+
+
+@pytest.mark.parametrize("trunc", [0, 2])
+def test_block_residual_sum_equals_sre(trunc):
+    # alpha_k 1 = W_k^T R_{k-1} 1 = W_k^T r_{k-1}: summing the block solution's
+    # columns gives the vector SRE-CG2 iterates (the same direction blocks)
+    p = W.random_spd_grid(14, 4, seed=31)
+    A = p.scipy()
+    ob = O.becg_solve(A, p.part, 4, p.b, tol=0.0, maxit=15, trunc=trunc, keep_x=True)
+    ov = O.ecg_solve(A, p.part, 4, p.b, tol=0.0, maxit=15, trunc=trunc, keep_x=True)
+    assert ob.iters == ov.iters == 14
+    for k in range(14):
+        np.testing.assert_allclose(ob.xhist[k], ov.xhist[k], rtol=0, atol=1e-10 * np.linalg.norm(ov.xhist[k]))
+
+
+def test_block_residual_columns_solve_their_subdomain_rhs():
+    # with the full window the method is block CG on A X = [T^t(r_0)]: at
+    # convergence column j solves A X_j = T_j(r_0), and the residual block is
+    # A-Galerkin-orthogonal per column (checked against a dense solve)
+    p = W.random_spd_grid(10, 4, seed=32)
+    A = p.scipy()
+    ob = O.becg_solve(A, p.part, 4, p.b, tol=1e-12, maxit=200, trunc=0)
+    assert ob.status == O.OK
+    X = ob.basis[0]
+    Ad = A.toarray()
+    for j in range(4):
+        rhs = np.where(p.part == j, p.b, 0.0)
+        ref = np.linalg.solve(Ad, rhs)
+        np.testing.assert_allclose(X[:, j], ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    np.testing.assert_allclose(ob.x, np.linalg.solve(Ad, p.b), rtol=0, atol=1e-9)
+
+
+def test_block_residual_t1_is_cg():
+    # t = 1: block CG with one column is CG (compared over the iterations
+    # before CG's own loss of orthogonality sets in on this 144-row system)
+    p = W.random_spd_grid(12, 1, seed=33)
+    A = p.scipy()
+    ob = O.becg_solve(A, np.zeros(p.n, dtype=np.int32), 1, p.b, tol=0.0, maxit=11, trunc=0, keep_x=True)
+    oc = O.cg_solve(A, p.b, tol=0.0, maxit=11, keep_x=True)
+    for k in range(10):
+        np.testing.assert_allclose(ob.xhist[k], oc.xhist[k], rtol=0, atol=1e-9 * np.linalg.norm(oc.xhist[k]))
