@@ -100,6 +100,12 @@ typedef struct {
   /* A restart discards the stored blocks and takes the next block from
      [T(r_{k-1})] with the width in force; x_{k-1} is kept and the stopping
      test keeps comparing with rho_0. */
+  int block_residual;   /* 1: the block-residual enlarged CG of Section 1:
+                           R_0 = [T^t(r_0)], t x t coefficients
+                           alpha_k = W_k^T R_{k-1}, R_k = R_{k-1} - V_k alpha_k,
+                           x_k = x_0 + X_k 1 and rho_k = ||R_k 1||.  SRE-CG2
+                           directions, FP64, no switch, restart or
+                           preconditioner (ECG_EINVAL otherwise) */
   void* stream;      /* cudaStream_t for all work; NULL: a stream the
                         context creates */
 } ecg_opts;

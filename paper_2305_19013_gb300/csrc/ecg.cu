@@ -118,6 +118,7 @@ struct ecg_ctx {
   double* d_z = nullptr;
   float* d_zf = nullptr;
   double* d_ppart = nullptr;  // nb x 64
+  double* d_Rb = nullptr;     // block residual (n x t), block-residual mode
   int* d_pflag = nullptr;
   bool profiling = false;
   std::vector<cudaEvent_t> pev;  // profiling event pool
@@ -263,6 +264,8 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   P.prec = (c->prec_nb > 0 && st == c->d_st) ? 1 : 0;
   P.want_beta = (c->opts.variant == ECG_MSDO && !P.prec) ? 1 : 0;
   P.z = fp32 ? (void*)c->d_zf : (void*)c->d_z;
+  P.block = (c->opts.block_residual && st == c->d_st) ? 1 : 0;
+  P.Rb = c->d_Rb;
   return P;
 }
 
@@ -430,6 +433,14 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
   }
   prof_mark(c, 6);
   k_final<T, W><<<c->gx, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
+  if constexpr (sizeof(T) == 8) {
+    if (P.block) {  // block-residual mode: alpha = W_k^T R, R -= V_k alpha, x, r = R 1
+      k_block_alpha<W><<<c->gx, kThreads, 0, s>>>(P, W);
+      k_reduce_partials<<<(W * W * 32 + kThreads - 1) / kThreads, kThreads, 0, s>>>(P.st, W, P.part_buf, c->gx,
+                                                                                   W * W, P.small + kSmallAb);
+      k_block_update<W><<<c->gx, kThreads, 0, s>>>(P, W);
+    }
+  }
   prof_mark(c, 7);
   k_finish<<<1, kThreads, 0, s>>>(P, W, c->gx, (int)sizeof(T));
   prof_mark(c, 8);
@@ -523,6 +534,11 @@ int run_solve(ecg_ctx* c, bool fp32, int kmax, int cap, double eps, int hist_off
                                                   nullptr);
   }
   k_start<<<1, kThreads, 0, s>>>(P, c->gx);
+  if (P.block) {  // R_0 = [T^t(r_0)]
+    const long long tot = (long long)c->n * c->t;
+    const int g = (int)std::max<long long>(1, std::min<long long>((tot + 255) / 256, 8LL * c->num_sms));
+    k_block_split<<<g, 256, 0, s>>>(P, c->d_r, c->d_Rb);
+  }
   prof_mark(c, 9);
   CK(cudaGetLastError());
   // Groups of check_every iterations, polled one group behind.  The host
@@ -602,6 +618,10 @@ int validate_opts(const ecg_opts* o, int t) {
   if (o->restart_every == 1 || o->restart_every < 0) return ECG_EINVAL;
   if (!(o->restart_tol >= 0.0) || o->restart_max < 0) return ECG_EINVAL;
   if (o->restart_at_switch && !(o->switch_tol > 0.0)) return ECG_EINVAL;
+  if (o->block_residual != 0 && o->block_residual != 1) return ECG_EINVAL;
+  if (o->block_residual && (o->variant != ECG_SRE || o->switch_tol > 0.0 || o->precision != ECG_FP64 ||
+                            o->restart_every || o->restart_tol > 0.0))
+    return ECG_EINVAL;
   return ECG_OK;
 }
 
@@ -924,6 +944,7 @@ void ecg_default_opts(ecg_opts* o) {
   o->restart_tol = 0.0;
   o->restart_max = 0;
   o->restart_at_switch = 0;
+  o->block_residual = 0;
   o->stream = nullptr;
 }
 
@@ -979,6 +1000,7 @@ void ecg_destroy(ecg_ctx* c) {
   dfree(c->d_rho_part);
   dfree(c->d_beta_part);
   dfree(c->d_bb_part);
+  dfree(c->d_Rb);
   prec_free(c);
   if (c->h_flags) cudaFreeHost(c->h_flags);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1146,7 +1168,12 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
   {
     const size_t gymax = ((size_t)cap * t + kChunk - 1) / kChunk;
     size_t need = std::max((4 * (size_t)c->num_sms + gymax) * kChunk * t, (size_t)c->gx * (t * (t + 1) / 2 + t));
+    if (c->opts.block_residual) need = std::max(need, (size_t)c->gx * t * t);
     if ((rc = ensure_part(c, need))) return rc;
+  }
+  if (c->opts.block_residual) {
+    if (c->prec_nb > 0) return ECG_EINVAL;  // no preconditioned block-residual form
+    if (!c->d_Rb && (rc = dalloc(&c->d_Rb, (size_t)n * t))) return rc;
   }
   // ---- inputs
   const bool dev_in = is_device_ptr(b);

@@ -96,7 +96,8 @@ constexpr int kSmallRe = kSmallG + 4096;   // R_e^{-1}
 constexpr int kSmallRi = kSmallRe + 4096;  // R^{-1} = R_e^{-1} S^{-1}
 constexpr int kSmallAl = kSmallRi + 4096;  // alpha
 constexpr int kSmallBe = kSmallAl + 64;    // beta
-constexpr int kSmallSize = kSmallBe + 64;
+constexpr int kSmallAb = kSmallBe + 64;    // block-residual alpha (t x t)
+constexpr int kSmallSize = kSmallAb + 4096;
 
 struct KP {
   int n, t;
@@ -124,6 +125,8 @@ struct KP {
   int want_beta;     // accumulate beta partials in k_final (MSDO-CG)
   int prec;          // 1: block Jacobi preconditioned generators (z = M^{-1} r)
   void* z;           // M^{-1} r_{k-1} (n), written by k_prec_solve
+  int block;         // 1: block-residual mode (k_final leaves x, r alone)
+  double* Rb;        // block residual R_k (n x t), block-residual mode
 };
 
 // Block Jacobi preconditioner M = L L^T, L = diag(L_1 .. L_nb), L_i the
@@ -1204,7 +1207,8 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
   T* sal = sRi + W * W;                                   // W
   T* srn = sal + W;                                       // R
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = (T)P.small[kSmallRi + i];
-  for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = (T)P.small[kSmallAl + i];
+  // block-residual mode: x and r are updated by k_block_update instead
+  for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = P.block ? T(0) : (T)P.small[kSmallAl + i];
   double rho_acc = 0.0;
   RowAcc<T> beta_acc;
   BulkTiles<S> bt;
@@ -1477,6 +1481,83 @@ __global__ void __launch_bounds__(kThreads) k_prec_solve(KP P, PrecP Q, int gw, 
     Q.part[(long long)b * W + threadIdx.x] = -s;
   }
 }
+
+// ------------------------------------------------ block-residual mode
+
+// R_0 = [T^t(r_0)] (n x t).
+__global__ void k_block_split(KP P, const double* r, double* Rb) {
+  const long long total = (long long)P.n * P.t;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e / P.t), j = (int)(e - (long long)i * P.t);
+    Rb[e] = (j == P.part[i]) ? r[i] : 0.0;
+  }
+}
+
+// Per-CTA partial sums of alpha_k = W_k^T R_{k-1} (W x W), W_k the block
+// k_final just wrote into the window slot; one thread per entry.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_block_alpha(KP P, int gw) {
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  const double* Wk = (const double*)P.slotW + (long long)st->next_slot * P.slot_stride;
+  int r0, r1;
+  cta_rows(P.n, r0, r1);
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
+    const int a = e / W, b = e - a * W;
+    double s = 0.0;
+    for (int i = r0; i < r1; i++) s = fma(Wk[(long long)i * W + a], P.Rb[(long long)i * W + b], s);
+    P.part_buf[(long long)blockIdx.x * W * W + e] = s;
+  }
+}
+
+// R_k = R_{k-1} - V_k alpha_k, x_k = x_{k-1} + W_k alpha_k 1, r_k = R_k 1,
+// partial ||r_k||^2 (one thread per row).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_block_update(KP P, int gw) {
+  __shared__ double sal[W * W];
+  __shared__ double sbuf[kThreads];
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  const long long slot = st->next_slot;
+  const double* Wk = (const double*)P.slotW + slot * P.slot_stride;
+  const double* Vk = (const double*)P.slotV + slot * P.slot_stride;
+  double* x = (double*)P.x;
+  double* r = (double*)P.r;
+  for (int e = threadIdx.x; e < W * W; e += blockDim.x) sal[e] = P.small[kSmallAb + e];
+  __syncthreads();
+  int r0, r1;
+  cta_rows(P.n, r0, r1);
+  double acc = 0.0;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    double w[W], v[W];
+#pragma unroll
+    for (int a = 0; a < W; a++) {
+      w[a] = Wk[(long long)i * W + a];
+      v[a] = Vk[(long long)i * W + a];
+    }
+    double dx = 0.0, rs = 0.0;
+#pragma unroll
+    for (int c = 0; c < W; c++) {
+      double sx = 0.0, sr = 0.0;
+#pragma unroll
+      for (int a = 0; a < W; a++) {
+        sx = fma(w[a], sal[a * W + c], sx);
+        sr = fma(v[a], sal[a * W + c], sr);
+      }
+      const double rn = P.Rb[(long long)i * W + c] - sr;
+      P.Rb[(long long)i * W + c] = rn;
+      dx += sx;
+      rs += rn;
+    }
+    x[i] += dx;
+    r[i] = rs;
+    acc += rs * rs;
+  }
+  const double tot = block_sum(acc, sbuf);
+  if (threadIdx.x == 0) P.rho_part[blockIdx.x] = tot;
+}
+
 
 // End of iteration k: rho_k, tol1, window push, stop and switch tests.
 // elem_bytes is the size of the solve's scalar type (slot addresses).

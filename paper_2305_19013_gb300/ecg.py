@@ -53,6 +53,7 @@ class _Opts(C.Structure):
         ("restart_tol", C.c_double),
         ("restart_max", C.c_int),
         ("restart_at_switch", C.c_int),
+        ("block_residual", C.c_int),
         ("stream", C.c_void_p),
     ]
 
@@ -206,6 +207,7 @@ class Solver:
         restart_tol: float = 0.0,
         restart_max: int = 0,
         restart_at_switch: bool = False,
+        block_residual: bool = False,
         stream=None,
     ):
         lib = load()
@@ -238,6 +240,7 @@ class Solver:
         o.restart_tol = float(restart_tol)
         o.restart_max = int(restart_max)
         o.restart_at_switch = 1 if restart_at_switch else 0
+        o.block_residual = 1 if block_residual else 0
         o.stream = stream
         ctx = C.c_void_p()
         rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))

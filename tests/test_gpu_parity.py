@@ -481,3 +481,48 @@ def test_full_size_preconditioned_first_iterations_match_oracle(diffusion1024):
     assert g.iters == o.iters == 3
     assert rel(host(g.x), o.x) < 1e-10
     assert np.all(np.abs(g.history - o.history) <= 1e-10 * o.history[0])
+
+
+# ------------------------------------------------- block-residual mode (Section 1)
+
+BLOCK_CASES = [
+    ("poisson64_t4_full", lambda: W.poisson2d(64, 4, seed=1001), 0, STRICT),
+    ("poisson64_t4_trunc2", lambda: W.poisson2d(64, 4, seed=1001), 2, STRICT),
+    ("ragged_t16_full", lambda: ragged(16, seed=71), 0, STRICT),
+    ("ragged_t8_trunc2", lambda: ragged(8, seed=72), 2, ENVELOPE),
+]
+
+
+@pytest.mark.parametrize("name,make,trunc,mode", BLOCK_CASES, ids=[c[0] for c in BLOCK_CASES])
+def test_block_residual_matches_oracle(name, make, trunc, mode):
+    p = make()
+    A = p.scipy()
+    maxit = 3000
+    o = O.becg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, trunc=trunc)
+    with ecg.Solver.from_problem(p, trunc=trunc, block_residual=True) as s:
+        g = s.solve(dev(p.b), tol=1e-8, maxit=maxit)
+    assert o.status == 0 and g.status == 0
+    h0 = o.history[0]
+    if mode == STRICT:
+        assert abs(g.iters - o.iters) <= 1, (g.iters, o.iters)
+        k = min(g.iters, o.iters)
+        assert np.all(np.abs(g.history[: k + 1] - o.history[: k + 1]) <= 1e-8 * h0)
+        if g.iters == o.iters:
+            assert rel(host(g.x), o.x) <= 1e-8
+    else:
+        # chaotic truncated run: the iteration count within the spread of the
+        # vector method's runs, the first iterates equal, and the solution
+        # meeting the tolerance
+        its = [O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=maxit, trunc=trunc, ortho=q).iters for q in (0, 1)]
+        lo, hi = min(its + [o.iters]), max(its + [o.iters])
+        width = max(2, hi - lo)
+        assert lo - width <= g.iters <= hi + width, (g.iters, its, o.iters)
+        assert np.all(np.abs(g.history[:11] - o.history[:11]) <= 1e-8 * h0)
+        assert g.relres_true <= 1e-7
+
+
+def test_block_residual_rejects_other_modes():
+    p = ragged(4, seed=73)
+    for kw in (dict(variant="msdo"), dict(switch_tol=1e-3), dict(precision=ecg.MIXED), dict(restart_every=5)):
+        with pytest.raises(ecg.EcgError):
+            ecg.Solver.from_problem(p, block_residual=True, **kw)
