@@ -186,6 +186,39 @@ def batch_run(torch):
 
 
 
+def warmstart_run(torch, side=64, ntrain=256, nheld=8, epochs=30):
+    """The learned warm start at a reduced scale: GRF diffusion problems
+    (side x side, correlation length 0.1, sigma 1, t = 16), ntrain training
+    solves, the U-Net trained with the energy-norm loss, and held-out solves
+    from x_0 = 0 against the smoothed proposal (16 Jacobi sweeps, fallback
+    to x_0 = 0), stopping rule ||r|| <= 1e-8 ||b||, SRE-CG (trunc 2)."""
+    from paper_2305_19013_gb300 import warmstart as WS
+
+    t0 = time.perf_counter()
+    train = WS.make_dataset(ntrain, side=side, t=16, seed0=7000, prec_blocks=16 if side <= 64 else 64)
+    t1 = time.perf_counter()
+    held = WS.make_dataset(nheld, side=side, t=16, seed0=9000, solve=False)
+    net = WS.WarmStartNet(side=side, batch=8, seed=2)
+    hist = WS.train(net, train, epochs=epochs, lr=3e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rows = WS.evaluate(net, held, tol=1e-8, trunc=2, sweeps=16)
+    return {
+        "workload": f"GRF diffusion {side}x{side}, t=16, {ntrain} training solves, {nheld} held-out problems",
+        "params": net.n_params(),
+        "data_seconds": t1 - t0,
+        "train_seconds": t2 - t1,
+        "energy_loss_first_last": [hist[0], hist[-1]],
+        "iters_zero_mean": float(np.mean([r["iters_zero"] for r in rows])),
+        "iters_warm_mean": float(np.mean([r["iters_net"] for r in rows])),
+        "seconds_zero_mean": float(np.mean([r["s_zero"] for r in rows])),
+        "seconds_warm_mean": float(np.mean([r["s_net"] for r in rows])),
+        "x0_relres_mean": float(np.mean([r["x0_relres"] for r in rows])),
+        "proposals_used": int(sum(r["used"] for r in rows)),
+    }
+
+
+
 def run_oracle_sample(K, W, trunc):
     """The FP64 CPU oracle (single thread) on a 1/16 row sample of the
     workload: the 256 x 256 version of the same coefficient layout (16 x 16
@@ -251,6 +284,8 @@ def main():
     ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
     ap.add_argument("--time-to-tol-only", default="", help="only the time-to-tol runs whose name contains this")
     ap.add_argument("--prec-blocks", type=int, default=64, help="block Jacobi blocks for the preconditioned runs")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="also train the warm-start network on GRF diffusion problems and compare solves")
     ap.add_argument("--batch", action="store_true",
                     help="also solve the batched workload (64 uneven 2D diffusion systems, t=8) and report it")
     args = ap.parse_args()
@@ -422,6 +457,8 @@ def main():
         line["time_to_tol"] = ttt
     if args.batch:
         line["batch"] = batch_run(torch)
+    if args.warmstart:
+        line["warmstart"] = warmstart_run(torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = run_oracle_sample(8, 1, args.trunc)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

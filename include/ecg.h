@@ -55,6 +55,10 @@ extern "C" {
 #define ECG_PRE_CHOLQR 0 /* Euclidean CholQR, then A-CholQR (the paper's choice in Section 5) */
 #define ECG_A_CHOLQR 1   /* A-CholQR alone */
 
+/* Stopping rules (ecg_opts.stop_rule) */
+#define ECG_STOP_R0 0 /* rho_k <= tol * ||b - A x_0||, the paper's test */
+#define ECG_STOP_B 1  /* rho_k <= tol * ||b|| */
+
 /* Preconditioner kinds (ecg_set_preconditioner) */
 #define ECG_PREC_NONE 0  /* no preconditioner */
 #define ECG_PREC_IC0 1   /* block Jacobi, IC(0) of every diagonal block */
@@ -100,6 +104,9 @@ typedef struct {
   /* A restart discards the stored blocks and takes the next block from
      [T(r_{k-1})] with the width in force; x_{k-1} is kept and the stopping
      test keeps comparing with rho_0. */
+  int stop_rule;        /* ECG_STOP_R0 (default): stop when rho_k <= tol rho_0
+                           (Algorithm 1); ECG_STOP_B: when rho_k <= tol ||b||,
+                           so that a good x_0 shortens the solve */
   int block_residual;   /* 1: the block-residual enlarged CG of Section 1:
                            R_0 = [T^t(r_0)], t x t coefficients
                            alpha_k = W_k^T R_{k-1}, R_k = R_{k-1} - V_k alpha_k,
@@ -176,6 +183,13 @@ int ecg_solve(ecg_ctx* ctx, const double* b, const double* x0, double* x_out, do
  * subdomains, bad kind), ECG_ENOTSPD (an IC(0) pivot is not positive; the
  * context is left without a preconditioner), ECG_ENOMEM or ECG_ECUDA. */
 int ecg_set_preconditioner(ecg_ctx* ctx, const int32_t* pblock, int nblocks, int kind);
+
+/* sweeps damped Jacobi sweeps on A x = b in place, x <- x + omega D^{-1}
+ * (b - A x), FP64 (b, x: n doubles, device pointers; 0 < omega < 2).  Not a
+ * step of the paper's methods: it removes the high-frequency error of an
+ * initial iterate proposed by the warm-start network (ecg_nn.h) before the
+ * solve starts from it. */
+int ecg_smooth(ecg_ctx* ctx, const double* b, double* x, int sweeps, double omega);
 
 /* Release every resource of ctx (NULL is accepted). */
 void ecg_destroy(ecg_ctx* ctx);

@@ -1,6 +1,7 @@
 """Build libecg.so in-tree with nvcc for sm_103a (GB300).
 
-Two translation units (the single-system solver and the batched solver),
+Three translation units (the single-system solver, the batched solver and
+the warm-start network),
 compiled in parallel with one -gencode each and linked into one library;
 the library links the CUDA runtime statically so that it loads next to any
 PyTorch build.
@@ -16,11 +17,12 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libecg.so")
-SOURCES = [os.path.join(CSRC, "ecg.cu"), os.path.join(CSRC, "batch.cu")]
+SOURCES = [os.path.join(CSRC, "ecg.cu"), os.path.join(CSRC, "batch.cu"), os.path.join(CSRC, "nn.cu")]
 DEPS = SOURCES + [
     os.path.join(CSRC, "ecg_kernels.cuh"),
     os.path.join(CSRC, "ecg_batch.cuh"),
     os.path.join(INCLUDE, "ecg.h"),
+    os.path.join(INCLUDE, "ecg_nn.h"),
 ]
 OBJDIR = os.path.join(HERE, "_build")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

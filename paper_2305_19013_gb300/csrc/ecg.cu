@@ -531,9 +531,11 @@ int run_solve(ecg_ctx* c, bool fp32, int kmax, int cap, double eps, int hist_off
                                                  nullptr);
   } else {
     k_residual<double><<<c->gx, kThreads, 0, s>>>(P, have_x0 ? c->d_x : nullptr, c->d_r, c->d_b, c->d_rho_part,
-                                                  nullptr);
+                                                  c->d_bb_part);
   }
-  k_start<<<1, kThreads, 0, s>>>(P, c->gx);
+  // ECG_STOP_B on the FP64 solve; the FP32 inner solves of mixed precision
+  // get their tolerance from the outer loop
+  k_start<<<1, kThreads, 0, s>>>(P, c->gx, (!fp32 && c->opts.stop_rule == ECG_STOP_B) ? c->d_bb_part : nullptr);
   if (P.block) {  // R_0 = [T^t(r_0)]
     const long long tot = (long long)c->n * c->t;
     const int g = (int)std::max<long long>(1, std::min<long long>((tot + 255) / 256, 8LL * c->num_sms));
@@ -619,6 +621,7 @@ int validate_opts(const ecg_opts* o, int t) {
   if (!(o->restart_tol >= 0.0) || o->restart_max < 0) return ECG_EINVAL;
   if (o->restart_at_switch && !(o->switch_tol > 0.0)) return ECG_EINVAL;
   if (o->block_residual != 0 && o->block_residual != 1) return ECG_EINVAL;
+  if (o->stop_rule != ECG_STOP_R0 && o->stop_rule != ECG_STOP_B) return ECG_EINVAL;
   if (o->block_residual && (o->variant != ECG_SRE || o->switch_tol > 0.0 || o->precision != ECG_FP64 ||
                             o->restart_every || o->restart_tol > 0.0))
     return ECG_EINVAL;
@@ -945,6 +948,7 @@ void ecg_default_opts(ecg_opts* o) {
   o->restart_max = 0;
   o->restart_at_switch = 0;
   o->block_residual = 0;
+  o->stop_rule = ECG_STOP_R0;
   o->stream = nullptr;
 }
 
@@ -1205,11 +1209,13 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
     double rr = 0.0, bb = 0.0;
     if ((rc = true_residual(c, true, &rr, &bb))) return rc;
     const double rho0 = std::sqrt(rr);
+    // the outer test: ||b - A x|| <= tol * ref, ref = rho_0 or ||b||
+    const double ref = (c->opts.stop_rule == ECG_STOP_B) ? std::sqrt(bb) : rho0;
     double rho = rho0;
     c->h_hist.assign(1, rho0);
     const int gcv = std::max(1, std::min(8 * c->num_sms, (n + 255) / 256));
     for (int outer = 0;; outer++) {
-      if (!(rho > tol * rho0)) {
+      if (!(rho > tol * ref)) {
         status = ECG_OK;
         break;
       }
@@ -1218,7 +1224,7 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
         break;
       }
       // the inner solve needs to reach only what is left of the tolerance
-      const double need = 0.1 * tol * rho0 / rho;
+      const double need = 0.1 * tol * ref / rho;
       const double eps_in = std::min(0.5, std::max(c->opts.inner_tol, need));
       k_to_float_scaled<<<gcv, 256, 0, s>>>(n, c->d_r, c->d_bf, 1.0 / rho);
       CK(cudaMemsetAsync(c->d_xf, 0, sizeof(float) * n, s));
@@ -1247,7 +1253,7 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
       iters += it;
       if (!(rho_new < rho)) {  // no progress: stagnation of the inner solves
         rho = rho_new;
-        status = (rho_new > tol * rho0) ? ECG_ENOCONV : ECG_OK;
+        status = (rho_new > tol * ref) ? ECG_ENOCONV : ECG_OK;
         break;
       }
       rho = rho_new;
@@ -1330,6 +1336,21 @@ int ecg_set_preconditioner(ecg_ctx* c, const int32_t* pblock, int nblocks, int k
   const int rc = prec_build(c, pb, nblocks);
   if (rc) prec_free(c);
   return rc;
+}
+
+int ecg_smooth(ecg_ctx* c, const double* b, double* x, int sweeps, double omega) {
+  if (!c || !b || !x || sweeps < 0 || !(omega > 0.0 && omega < 2.0)) return ECG_EINVAL;
+  if (sweeps == 0) return ECG_OK;
+  int rc;
+  if ((rc = put_op_state(c, op_state(c, 1, 0, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
+  const int g = std::max(1, std::min(8 * c->num_sms, (c->n + 255) / 256));
+  double* tmp = c->d_sx;  // scratch vector of the step-level calls
+  for (int k = 0; k < sweeps; k++) {
+    k_jacobi<<<g, 256, 0, c->stream>>>(P, x, b, omega, tmp);
+    CK(cudaMemcpyAsync(x, tmp, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  return finish_op(c, nullptr);
 }
 
 int ecg_op_prec_apply(ecg_ctx* c, const double* in, double* out, int w) {

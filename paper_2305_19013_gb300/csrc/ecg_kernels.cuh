@@ -531,14 +531,21 @@ __global__ void __launch_bounds__(kThreads) k_residual(KP P, const T* x, T* rout
 }
 
 // Algorithm 1 line 1: rho_0 and the loop state for k = 1.
-__global__ void k_start(KP P, int nparts) {
+// With part_bb (the stopping rule rho_k <= tol ||b||) the tolerance is
+// rescaled to the test rho_k <= eps rho_0 the loop uses.
+__global__ void k_start(KP P, int nparts, const double* part_bb) {
   __shared__ double sbuf[kThreads];
-  double s = 0.0;
-  for (int c = threadIdx.x; c < nparts; c += blockDim.x) s += P.rho_part[c];
+  double s = 0.0, sb = 0.0;
+  for (int c = threadIdx.x; c < nparts; c += blockDim.x) {
+    s += P.rho_part[c];
+    if (part_bb) sb += part_bb[c];
+  }
   s = block_sum(s, sbuf);
+  if (part_bb) sb = block_sum(sb, sbuf);
   if (threadIdx.x == 0) {
     DevState* st = P.st;
     double rho0 = sqrt(s);
+    if (part_bb && rho0 > 0.0) st->eps = st->eps * sqrt(sb) / rho0;
     st->rho0 = rho0;
     st->rho_prev = rho0;
     st->rho = rho0;
@@ -1677,6 +1684,20 @@ __global__ void k_axpy_from_float(int n, double* x, const float* df, double scal
 }
 
 // Matrix values rounded to FP32.
+// One damped Jacobi sweep on A x = b: xout = xin + omega D^{-1} (b - A xin)
+// (FP64; xin and xout distinct).
+__global__ void k_jacobi(KP P, const double* xin, const double* b, double omega, double* xout) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    double ax = 0.0, d = 0.0;
+    for (int p = P.rowptr[i]; p < P.rowptr[i + 1]; p++) {
+      const int j = P.col[p];
+      ax += P.val[p] * xin[j];
+      if (j == i) d += P.val[p];
+    }
+    xout[i] = xin[i] + omega * (b[i] - ax) / d;
+  }
+}
+
 __global__ void k_vals_to_float(long long nnz, const double* v, float* vf) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nnz;
        i += (long long)gridDim.x * blockDim.x)

@@ -53,6 +53,7 @@ class _Opts(C.Structure):
         ("restart_tol", C.c_double),
         ("restart_max", C.c_int),
         ("restart_at_switch", C.c_int),
+        ("stop_rule", C.c_int),
         ("block_residual", C.c_int),
         ("stream", C.c_void_p),
     ]
@@ -110,6 +111,7 @@ SIGNATURES = {
     "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
     "ecg_tdot_noalloc": (_I, [C.c_int64, _I, _P, _P, _P, _I, _P, _P]),
     "ecg_set_preconditioner": (_I, [_P, _P, _I, _I]),
+    "ecg_smooth": (_I, [_P, _P, _P, _I, _D]),
     "ecg_batch_default_opts": (None, [C.POINTER(_BatchOpts)]),
     "ecg_batch_create": (_I, [_I, _P, _P, _I, C.POINTER(_BatchOpts), C.POINTER(_P)]),
     "ecg_batch_solve": (_I, [_P, _P, _P, _P, _D, _I, _P]),
@@ -119,6 +121,7 @@ SIGNATURES = {
 }
 
 PREC_NONE, PREC_IC0 = 0, 1
+STOP_R0, STOP_B = 0, 1
 
 
 def library_path() -> str:
@@ -208,6 +211,7 @@ class Solver:
         restart_max: int = 0,
         restart_at_switch: bool = False,
         block_residual: bool = False,
+        stop_rule: int = 0,
         stream=None,
     ):
         lib = load()
@@ -241,6 +245,7 @@ class Solver:
         o.restart_max = int(restart_max)
         o.restart_at_switch = 1 if restart_at_switch else 0
         o.block_residual = 1 if block_residual else 0
+        o.stop_rule = int(stop_rule)
         o.stream = stream
         ctx = C.c_void_p()
         rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))
@@ -344,6 +349,14 @@ class Solver:
             self._lib.ecg_set_preconditioner(self._ctx, pb.ctypes.data_as(C.c_void_p), int(nblocks), int(kind)),
             "ecg_set_preconditioner",
         )
+
+    def smooth(self, b, x, sweeps: int, omega: float = 0.8):
+        """sweeps damped Jacobi sweeps on A x = b, x updated in place (device
+        tensors)."""
+        _check_tensor(b, (self.n,), "b")
+        _check_tensor(x, (self.n,), "x")
+        self._rc(self._lib.ecg_smooth(self._ctx, _ptr(b), _ptr(x), int(sweeps), float(omega)), "ecg_smooth")
+        return x
 
     def prec_apply(self, X):
         """M^{-1} X for an n-vector or an n x w block (step-level call)."""

@@ -354,6 +354,37 @@ def batch_diffusion2d(count: int = 64, side_lo: int = 128, side_hi: int = 512, t
     return out
 
 
+def gaussian_field(side: int, corr: float, rng: np.random.Generator) -> np.ndarray:
+    """Stationary Gaussian random field on the periodic unit square (side x
+    side cells), squared-exponential covariance exp(-d^2 / (2 corr^2)),
+    zero mean and unit variance, by spectral synthesis: white noise
+    filtered by the square root of the covariance's spectral density."""
+    k = np.fft.fftfreq(side, d=1.0 / side)  # integer wave numbers
+    kx, ky = np.meshgrid(k, k, indexing="xy")
+    spec = np.exp(-0.5 * (2.0 * np.pi * corr) ** 2 * (kx**2 + ky**2))
+    g = np.real(np.fft.ifft2(np.fft.fft2(rng.standard_normal((side, side))) * np.sqrt(spec)))
+    g -= g.mean()
+    return g / g.std()
+
+
+def grf_diffusion2d(side: int = 256, t: int = 16, seed: int = 5000, corr: float = 0.1, sigma: float = 1.0,
+                    b_corr: float = 0.2) -> Problem:
+    """2D diffusion whose coefficient is exp(sigma g), g a Gaussian random
+    field with correlation length corr (unit square), and whose right-hand
+    side is a smooth random field (correlation length b_corr, unit
+    variance); t rectangular subdomains, rows reordered by subdomain.  The
+    grid-ordered fields ride along in meta (logk, b_grid) for the warm-start
+    network."""
+    rng = _rng(seed)
+    logk = sigma * gaussian_field(side, corr, rng)
+    b = gaussian_field(side, b_corr, rng).ravel()
+    A = diffusion2d(np.exp(logk))
+    px, py = _split2(t)
+    part = block_partition2d(side, side, px, py)
+    meta = {"side": side, "logk": logk, "b_grid": b.copy()}
+    return _finish(f"grf2d_{side}_t{t}", A, part, t, b, None, meta, True)
+
+
 # Named workloads: the small parity case and the two large single-GPU cases.
 WORKLOADS = {
     "poisson2d_64_t4": lambda seed=1001: poisson2d(64, 4, seed),

@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function
-include/ecg.h declares.  No compute call is made (CPU-only test)."""
+include/*.h declares (ecg.h and ecg_nn.h).  No compute call is made
+(CPU-only test)."""
 import os
 import re
 
@@ -11,22 +12,27 @@ from paper_2305_19013_gb300 import ecg
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_functions():
+def declared_functions(only=None):
     names = []
     for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if only and fn != only:
+            continue
         if not fn.endswith(".h"):
             continue
         text = open(os.path.join(ROOT, "include", fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        names += re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(ecg_\w+)\s*\(", text, flags=re.M)
+        names += re.findall(r"^\s*(?:int|void|size_t|const char\s*\*)\s+(ecg_\w+)\s*\(", text, flags=re.M)
     return names
 
 
 def test_header_declares_the_boundary():
-    names = declared_functions()
+    names = declared_functions("ecg.h")
     for required in ("ecg_create", "ecg_solve", "ecg_destroy", "ecg_strerror"):
         assert required in names
     assert set(names) == set(ecg.SIGNATURES), "binding and header disagree"
+    from paper_2305_19013_gb300 import warmstart
+
+    assert set(declared_functions("ecg_nn.h")) == set(warmstart.SIGNATURES), "network binding and header disagree"
 
 
 def test_library_builds_loads_and_exports_every_symbol():
