@@ -206,6 +206,21 @@ struct Tile {
   static constexpr int R = (W >= 64) ? 16 : 32;
 };
 
+// Rows per tile of the CGS coefficients: FP32 tiles are 128 rows, so that
+// the per-tile waits and barriers are paid over enough rows to keep HBM
+// busy (FP64 is bound by its FMA rate at 32 rows).
+template <typename T, int WB>
+struct TdotTile {
+  static constexpr int R = (sizeof(T) == 4 && WB % 4 == 0) ? 128 : Tile<WB>::R;
+};
+
+// Rows per tile of the CGS update: FP32 threads own 2 rows x 4 columns, so
+// a tile of 2048 / W rows (at most 128) occupies all 256 threads.
+template <typename T, int W>
+struct UpdTile {
+  static constexpr int R = (sizeof(T) == 4) ? ((2048 / W) < 128 ? (2048 / W) : 128) : Tile<W>::R;
+};
+
 __device__ __forceinline__ void cta_rows(int n, int& r0, int& r1) {
   long long per = ((long long)n + gridDim.x - 1) / gridDim.x;
   long long b = per * blockIdx.x;
@@ -472,11 +487,14 @@ struct BulkTiles {
 // pipeline and the fallback through registers.
 template <typename T, int W>
 constexpr size_t smem_tdot() {
-  return 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * (kChunk + W);
+  // FP32 also sums its row slices there: kThreads x 16 doubles
+  return 64 + ((sizeof(T) * Stages<T>::S * TdotTile<T, W>::R * (kChunk + W)) > (sizeof(T) == 4 ? kThreads * 16 * 8 : 0)
+                   ? sizeof(T) * Stages<T>::S * TdotTile<T, W>::R * (kChunk + W)
+                   : (size_t)kThreads * 16 * 8);
 }
 template <typename T, int W>
 constexpr size_t smem_update() {
-  return sizeof(T) * kChunk * W + 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * (kChunk + W);
+  return sizeof(T) * kChunk * W + 64 + sizeof(T) * Stages<T>::S * UpdTile<T, W>::R * (kChunk + W);
 }
 template <typename T, int W>
 constexpr size_t smem_gram_self() {
@@ -615,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_generate(KP P, int gw) {
 // window columns of chunk blockIdx.y.  B is n x WB.
 template <typename T, int WB>
 __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T* B) {
-  constexpr int R = Tile<WB>::R;
+  constexpr int R = TdotTile<T, WB>::R;
   constexpr int EPT = (kChunk * WB + kThreads - 1) / kThreads;
   constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
@@ -668,6 +686,67 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
       cstr[threadIdx.x] = D[j].w;
     }
     const int bofs = R * span;
+    if constexpr (sizeof(T) == 4 && WB % 4 == 0) {
+      // FP32: each thread owns a 4 x 4 block of C and a slice of every
+      // tile's rows, reading 4 + 4 values (two 16-byte loads) per 16 FMAs;
+      // the slices are summed in shared memory at the end.  Needs every
+      // block width and the chunk a multiple of 4.
+      constexpr int BB = WB / 4;
+      bool w4 = (ncol % 4 == 0);
+      // widths multiple of 4 make every offset one too, so a thread's four
+      // columns lie in one block and start on a 16-byte boundary
+      for (int j = jlo; j <= jhi; j++) w4 = w4 && (D[j].w % 4 == 0);
+      const int EB = (ncol / 4) * BB;
+      if (w4 && EB <= kThreads) {
+        const int RS = kThreads / EB;
+        const int eb = threadIdx.x % EB, rs = threadIdx.x / EB;
+        const bool active = rs < RS;
+        const int a0 = (eb / BB) * 4, b0 = (eb % BB) * 4;
+        RowAcc<float> ra[16];
+        bt.start();
+        for (int i = 0; i < bt.ntiles; i++) {
+          if (!bt.ready(i, (DevState*)st)) return;
+          const float* stg = (const float*)bt.tile(i);
+          const int nr = bt.rows(i);
+          if (active) {
+            const float* sa = stg + cofs[a0];
+            const int sd = cstr[a0];
+            const float* sB = stg + bofs + b0;
+            float sv[16];
+#pragma unroll
+            for (int k = 0; k < 16; k++) sv[k] = 0.f;
+            for (int r = rs; r < nr; r += RS) {
+              const float4 av = *reinterpret_cast<const float4*>(sa + r * sd);
+              const float4 bv = *reinterpret_cast<const float4*>(sB + r * WB);
+              const float ax[4] = {av.x, av.y, av.z, av.w}, bx[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+              for (int u = 0; u < 4; u++)
+#pragma unroll
+                for (int v = 0; v < 4; v++) sv[u * 4 + v] = fmaf(ax[u], bx[v], sv[u * 4 + v]);
+            }
+#pragma unroll
+            for (int k = 0; k < 16; k++) ra[k].end(sv[k]);
+          }
+          bt.next(i);
+        }
+        // sum the row slices (the stages are free now)
+        double* red = reinterpret_cast<double*>(smem_raw + 64);
+        __syncthreads();
+        if (active)
+#pragma unroll
+          for (int k = 0; k < 16; k++) red[(rs * EB + eb) * 16 + k] = ra[k].value();
+        __syncthreads();
+        double* out = P.part_buf + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * (kChunk * WB);
+        for (int e = threadIdx.x; e < E; e += blockDim.x) {
+          const int a = e / WB, b = e - a * WB;
+          const int ebe = (a / 4) * BB + b / 4, k = (a % 4) * 4 + (b % 4);
+          double sum = 0.0;
+          for (int q = 0; q < RS; q++) sum += red[(q * EB + ebe) * 16 + k];
+          out[e] = sum;
+        }
+        return;
+      }
+    }
     bt.start();  // includes a __syncthreads, so cofs/cstr are visible
     for (int i = 0; i < bt.ntiles; i++) {
       if (!bt.ready(i, (DevState*)st)) return;
@@ -757,7 +836,7 @@ __global__ void __launch_bounds__(kThreads) k_reduce_C(KP P, int gw, int gxw, do
 // pipeline, the X tile riding in the same stage as the window's tiles.
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const double* Cin) {
-  constexpr int R = Tile<W>::R;
+  constexpr int R = UpdTile<T, W>::R;
   constexpr int EPT = (R * W + kThreads - 1) / kThreads;
   constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
@@ -798,6 +877,64 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
     cta_rows_aligned(P.n, R, bt.r0, bt.r1);
     bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
     const int xofs = R * wtot;
+    if constexpr (sizeof(T) == 4 && W % 4 == 0) {
+      // FP32: each thread owns 2 rows x 4 columns of the tile and reads, per
+      // 4 window columns, 2 + 4 16-byte vectors for 32 FMAs.  Needs every
+      // block width a multiple of 4.
+      bool w4 = true;
+      for (int j = 0; j < nq; j++) w4 = w4 && (D[j].w % 4 == 0);
+      if (w4) {
+        constexpr int CG = W / 4;
+        const int cg = threadIdx.x % CG, rp = threadIdx.x / CG;
+        const int b0 = cg * 4, rl0 = 2 * rp;
+        const bool active = rl0 < R;
+        bt.start();
+        for (int i = 0; i < bt.ntiles; i++) {
+          if (!bt.ready(i, (DevState*)st)) return;
+          const float* stg = (const float*)bt.tile(i);
+          const int row0 = bt.r0 + i * R, nr = bt.rows(i);
+          float acc[2][4];
+          if (active) {
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+              const float4 xv = *reinterpret_cast<const float4*>(stg + xofs + (rl0 + u) * W + b0);
+              acc[u][0] = xv.x;
+              acc[u][1] = xv.y;
+              acc[u][2] = xv.z;
+              acc[u][3] = xv.w;
+            }
+            for (int a = 0; a < wtot; a += 4) {
+              const float* qa = stg + cofs[a];
+              const int sd = cstr[a];
+              float4 qv[2];
+#pragma unroll
+              for (int u = 0; u < 2; u++) qv[u] = *reinterpret_cast<const float4*>(qa + (rl0 + u) * sd);
+#pragma unroll
+              for (int k = 0; k < 4; k++) {
+                const float4 cv = *reinterpret_cast<const float4*>(&sC[(a + k) * W + b0]);
+#pragma unroll
+                for (int u = 0; u < 2; u++) {
+                  const float q = (k == 0) ? qv[u].x : (k == 1) ? qv[u].y : (k == 2) ? qv[u].z : qv[u].w;
+                  acc[u][0] = fmaf(-q, cv.x, acc[u][0]);
+                  acc[u][1] = fmaf(-q, cv.y, acc[u][1]);
+                  acc[u][2] = fmaf(-q, cv.z, acc[u][2]);
+                  acc[u][3] = fmaf(-q, cv.w, acc[u][3]);
+                }
+              }
+            }
+          }
+          __syncthreads();
+          bt.refill(i);
+          if (active)
+#pragma unroll
+            for (int u = 0; u < 2; u++)
+              if (rl0 + u < nr)
+                *reinterpret_cast<float4*>(&Xio[(long long)(row0 + rl0 + u) * W + b0]) =
+                    make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
+        }
+        return;
+      }
+    }
     bt.start();
     for (int i = 0; i < bt.ntiles; i++) {
       if (!bt.ready(i, (DevState*)st)) return;
