@@ -107,11 +107,13 @@ struct ecg_ctx {
   // block Jacobi preconditioner (prec_nb == 0: none)
   struct Sweep {  // one substitution in level order (see PrecSweep)
     int *blk = nullptr, *lev = nullptr, *rows = nullptr, *cnt = nullptr, *col = nullptr, *map = nullptr;
+    int* dep = nullptr;  // level-local mode: index of each entry's row in the previous level
     double *val = nullptr, *diag = nullptr;
     float *valf = nullptr, *diagf = nullptr;
     int K = 1;
   };
   int prec_nb = 0;
+  int prec_local = 0, prec_maxw = 0;           // level-local mode (see PrecP)
   Sweep pf, pb;                                // forward and backward sweeps
   int *d_lp = nullptr, *d_lc = nullptr;        // L by rows (factorisation)
   double *d_lv = nullptr, *d_ld = nullptr;
@@ -278,6 +280,7 @@ PrecSweep make_sweep(const ecg_ctx::Sweep& w, bool fp32) {
   S.col = w.col;
   S.val = fp32 ? (const void*)w.valf : (const void*)w.val;
   S.diag = fp32 ? (const void*)w.diagf : (const void*)w.diag;
+  S.dep = w.dep;
   S.K = w.K;
   return S;
 }
@@ -285,6 +288,8 @@ PrecSweep make_sweep(const ecg_ctx::Sweep& w, bool fp32) {
 PrecP make_precp(const ecg_ctx* c, bool fp32) {
   PrecP Q;
   Q.nb = c->prec_nb;
+  Q.local = c->prec_local;
+  Q.maxw = c->prec_maxw;
   Q.f = make_sweep(c->pf, fp32);
   Q.b = make_sweep(c->pb, fp32);
   Q.part = c->d_ppart;
@@ -300,10 +305,12 @@ int prec_km(const ecg_ctx* c) {
 template <typename T, int W>
 void launch_prec(ecg_ctx* c, const KP& P, const PrecP& Q, int gw, const T* in, T* out, int w) {
   const dim3 grid(c->prec_nb, (std::max(W, w) + kPrecCols - 1) / kPrecCols);
+  // level-local mode: two levels of kPrecCols columns in shared memory
+  const size_t smem = Q.local ? 2 * (size_t)Q.maxw * kPrecCols * sizeof(T) : 0;
   switch (prec_km(c)) {
-    case 2: k_prec_solve<T, W, 2><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
-    case 4: k_prec_solve<T, W, 4><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
-    case 8: k_prec_solve<T, W, 8><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
+    case 2: k_prec_solve<T, W, 2><<<grid, kThreads, smem, c->stream>>>(P, Q, gw, in, out, w); break;
+    case 4: k_prec_solve<T, W, 4><<<grid, kThreads, smem, c->stream>>>(P, Q, gw, in, out, w); break;
+    case 8: k_prec_solve<T, W, 8><<<grid, kThreads, smem, c->stream>>>(P, Q, gw, in, out, w); break;
     default: k_prec_solve<T, W, 0><<<grid, kThreads, 0, c->stream>>>(P, Q, gw, in, out, w); break;
   }
 }
@@ -704,12 +711,15 @@ void free_sweep(ecg_ctx::Sweep& w) {
   dfree(w.diag);
   dfree(w.valf);
   dfree(w.diagf);
+  dfree(w.dep);
   w.K = 1;
 }
 
 void prec_free(ecg_ctx* c) {
   invalidate_graphs(c);
   c->prec_nb = 0;
+  c->prec_local = 0;
+  c->prec_maxw = 0;
   free_sweep(c->pf);
   free_sweep(c->pb);
   dfree(c->d_lp);
@@ -831,6 +841,41 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
   int Kf = 1, Kb = 1;
   ell(frows, lp, lc, nullptr, Kf, fcnt, fcol, fmap);
   ell(brows, up, uc, &umap, Kb, bcnt, bcol, bmap);
+  // Level-local mode: every entry references a row exactly one level
+  // before (true for the lexicographic order of 5- and 7-point blocks);
+  // dep holds that row's index inside its level.
+  auto local_deps = [&](const std::vector<int>& level, const std::vector<int>& blk, const std::vector<int>& lev,
+                        const std::vector<int>& rows, const std::vector<int>& cnt, const std::vector<int>& col, int K,
+                        std::vector<int>& dep, int& maxw) {
+    std::vector<int> loc(n);
+    maxw = 0;
+    for (int b = 0; b < nb; b++)
+      for (int l = blk[b]; l < blk[b + 1]; l++) {
+        maxw = std::max(maxw, lev[l + 1] - lev[l]);
+        for (int q = lev[l]; q < lev[l + 1]; q++) loc[rows[q]] = q - lev[l];
+      }
+    dep.assign((size_t)n * K, 0);
+    bool ok = true;
+    for (int q = 0; q < n && ok; q++) {
+      const int i = rows[q];
+      for (int k = 0; k < cnt[q]; k++) {
+        const int j = col[(size_t)q * K + k];
+        if (level[j] != level[i] - 1) {
+          ok = false;
+          break;
+        }
+        dep[(size_t)q * K + k] = loc[j];
+      }
+    }
+    return ok;
+  };
+  std::vector<int> fdep, bdep;
+  int mwf = 0, mwb = 0;
+  const bool lf = local_deps(levf, fblk, flev, frows, fcnt, fcol, Kf, fdep, mwf);
+  const bool lb = local_deps(levb, bblk, blev, brows, bcnt, bcol, Kb, bdep, mwb);
+  const int maxw = std::max(mwf, mwb);
+  // two levels of kPrecCols FP64 columns within the default 48 KB
+  const bool local = lf && lb && Kf <= 8 && Kb <= 8 && 2 * (size_t)maxw * kPrecCols * sizeof(double) <= 48 * 1024;
   const bool mixed = (c->opts.precision == ECG_MIXED);
   auto put_sweep = [&](ecg_ctx::Sweep& w, const std::vector<int>& blk, const std::vector<int>& lev,
                        const std::vector<int>& rows, const std::vector<int>& cnt, const std::vector<int>& col,
@@ -852,6 +897,9 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
       (rc = dalloc(&c->d_pflag, (size_t)1)))
     return rc;
   if (mixed && (rc = dalloc(&c->d_zf, (size_t)n))) return rc;
+  if (local && ((rc = upload(&c->pf.dep, fdep)) || (rc = upload(&c->pb.dep, bdep)))) return rc;
+  c->prec_local = local ? 1 : 0;
+  c->prec_maxw = local ? maxw : 0;
   c->prec_nb = nb;
   const PrecP Q = make_precp(c, false);
   CK(cudaMemsetAsync(c->d_pflag, 0, sizeof(int), c->stream));

@@ -149,10 +149,15 @@ struct PrecSweep {
   const int* col;   // q * K + k: column (global row) of entry k
   const void* val;  // q * K + k: value (T)
   const void* diag; // q: l_ii (T)
+  const int* dep;   // q * K + k: index of entry k's row inside the previous
+                    // level (level-local mode), else nullptr
   int K;
 };
 struct PrecP {
   int nb;
+  int local;         // 1: every entry references the previous level (both
+                     // sweeps), whose values the solve keeps in shared memory
+  int maxw;          // rows of the widest level (level-local mode)
   PrecSweep f;       // forward: y = L^{-1} x, entries l_ij, j < i
   PrecSweep b;       // backward: z = L^{-T} y, entries l_ji, j > i
   double* part;      // nb x W partial -V_{k-1}^T z (MSDO-CG)
@@ -1567,10 +1572,104 @@ __device__ void prec_sweep(const PrecSweep& S, int b, const T* in, T* out, int w
   }
 }
 
+// Columns of an n x w block one preconditioner CTA solves for.
+constexpr int kPrecCols = 4;
+
+// Level-local sweep: when every entry of a row references a row of the
+// level just before (the lexicographic order of a 5- or 7-point stencil
+// block does this), the previous level's results stay in shared memory, so
+// the chain from one level to the next runs through shared memory and a
+// barrier only.  Each thread prefetches the data of its (up to two) items
+// of the next level (structure, right-hand side) before the barrier that
+// ends the current one.
+template <typename T, int KM>
+struct PrecItem {
+  int i, cnt;
+  T rhs, diag;
+  T v[KM];
+  int d[KM];
+};
+
+template <typename T, int KM, bool FWD>
+__device__ void prec_sweep_local(const PrecSweep& S, int b, const T* in, T* out, int w, int c0, int nc, T* sprev,
+                                 T* scur) {
+  constexpr int U = 2;
+  const T* val = (const T*)S.val;
+  const T* diag = (const T*)S.diag;
+  const int K = S.K;
+  const int l0 = S.blk[b], l1 = S.blk[b + 1];
+  auto load = [&](int l, int u, PrecItem<T, KM>& it) -> bool {
+    const int q0 = S.lev[l];
+    const int idx = threadIdx.x + u * blockDim.x;
+    if (idx >= (S.lev[l + 1] - q0) * nc) return false;
+    const int qi = idx / nc, c = idx - qi * nc;
+    const int q = q0 + qi;
+    it.i = S.rows[q];
+    it.cnt = S.cnt[q];
+    it.rhs = FWD ? in[(long long)it.i * w + c0 + c] : out[(long long)it.i * w + c0 + c];
+    it.diag = diag[q];
+#pragma unroll
+    for (int k = 0; k < KM; k++) {
+      it.v[k] = (k < it.cnt) ? val[(long long)q * K + k] : T(0);
+      it.d[k] = (k < it.cnt) ? S.dep[(long long)q * K + k] : 0;
+    }
+    return true;
+  };
+  PrecItem<T, KM> cur[U];
+  bool have[U];
+  if (l0 < l1)
+#pragma unroll
+    for (int u = 0; u < U; u++) have[u] = load(l0, u, cur[u]);
+  for (int l = l0; l < l1; l++) {
+    const int items = (S.lev[l + 1] - S.lev[l]) * nc;
+    if (items <= U * (int)blockDim.x) {
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        if (!have[u]) continue;
+        const int idx = threadIdx.x + u * blockDim.x;
+        const int qi = idx / nc, c = idx - qi * nc;
+        T acc = cur[u].rhs;
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+          if (k < cur[u].cnt) acc -= cur[u].v[k] * sprev[cur[u].d[k] * nc + c];
+        acc = acc / cur[u].diag;
+        scur[qi * nc + c] = acc;
+        out[(long long)cur[u].i * w + c0 + c] = acc;
+      }
+    } else {  // a level wider than the prefetch: plain loop
+      for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int qi = idx / nc, c = idx - qi * nc;
+        const int q = S.lev[l] + qi;
+        const int i = S.rows[q], cnt = S.cnt[q];
+        T acc = FWD ? in[(long long)i * w + c0 + c] : out[(long long)i * w + c0 + c];
+        for (int k = 0; k < cnt; k++) acc -= val[(long long)q * K + k] * sprev[S.dep[(long long)q * K + k] * nc + c];
+        acc = acc / diag[q];
+        scur[qi * nc + c] = acc;
+        out[(long long)i * w + c0 + c] = acc;
+      }
+    }
+    if (l + 1 < l1)
+#pragma unroll
+      for (int u = 0; u < U; u++) have[u] = load(l + 1, u, cur[u]);
+    __syncthreads();
+    T* t = sprev;
+    sprev = scur;
+    scur = t;
+  }
+}
+
 // out = M^{-1} in = L^{-T} (L^{-1} in) for columns [c0, c0 + nc) of an n x w
 // block; out holds y = L^{-1} in after the first sweep.
 template <typename T, int KM>
 __device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int w, int c0, int nc) {
+  if (KM > 0 && Q.local) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s0 = (T*)smem_raw;           // Q.maxw x kPrecCols
+    T* s1 = s0 + Q.maxw * kPrecCols;  // Q.maxw x kPrecCols
+    prec_sweep_local<T, (KM > 0 ? KM : 1), true>(Q.f, b, in, out, w, c0, nc, s0, s1);
+    prec_sweep_local<T, (KM > 0 ? KM : 1), false>(Q.b, b, in, out, w, c0, nc, s0, s1);
+    return;
+  }
   prec_sweep<T, KM, true>(Q.f, b, in, out, w, c0, nc);
   prec_sweep<T, KM, false>(Q.b, b, in, out, w, c0, nc);
 }
@@ -1585,7 +1684,6 @@ __device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int
 // Grid: blockIdx.x = diagonal block, blockIdx.y = group of kPrecCols
 // columns (the 1-column solves use blockIdx.y == 0 only).  KM bounds the
 // entries per row of both sweeps (0: any).
-constexpr int kPrecCols = 4;
 template <typename T, int W, int KM>
 __global__ void __launch_bounds__(kThreads) k_prec_solve(KP P, PrecP Q, int gw, const T* in, T* out, int w) {
   const DevState* st = P.st;
