@@ -98,6 +98,16 @@ struct ecg_ctx {
   int hist_cap = 0;
   double *d_rho_part = nullptr, *d_beta_part = nullptr, *d_bb_part = nullptr;
   int gx = 1;
+  // FP32 spmm_gram / final grids by block width index (log2 W): one wave at
+  // the kernels' occupancy, at most gx
+  int gx_spmm32[7] = {}, gx_fin32[7] = {}, gx_gram32[7] = {};
+  // occupancy-sized grids of the CGS kernels by (kernel, shared memory)
+  struct OccEntry {
+    const void* kernel;
+    size_t smem;
+    int grid;
+  };
+  std::vector<OccEntry> occ;
   std::vector<double> h_hist;
   DevState* h_flags = nullptr;  // pinned, 2 entries
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -191,6 +201,11 @@ template <typename T, int W>
 constexpr size_t smem_spmm() {
   return sizeof(T) * (4 * Tile<W>::R * W + W * W + Tile<W>::R);
 }
+// k_spmm_gram_rows: its own layout, or the scalar one when it falls back
+template <int W>
+constexpr size_t smem_spmm_rows() {
+  return smem_spmm_f32<W>() > smem_spmm<float, W>() ? smem_spmm_f32<W>() : smem_spmm<float, W>();
+}
 template <int W>
 constexpr size_t smem_small() {
   return sizeof(double) * (3 * W * W + 2 * W);
@@ -210,6 +225,12 @@ int set_smem_attrs_t() {
   CK(cudaFuncSetAttribute(k_final<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<T, W>()));
   CK(cudaFuncSetAttribute(k_gram_self<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem_gram_self<T, W>()));
+  if constexpr (F32Rows<T, W>::on) {
+    CK(cudaFuncSetAttribute(k_spmm_gram_rows<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_spmm_rows<W>()));
+    CK(cudaFuncSetAttribute(k_spmm_gram_rows<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)smem_spmm_rows<W>()));
+  }
   return ECG_OK;
 }
 
@@ -268,6 +289,8 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   P.z = fp32 ? (void*)c->d_zf : (void*)c->d_z;
   P.block = (c->opts.block_residual && st == c->d_st) ? 1 : 0;
   P.Rb = c->d_Rb;
+  P.wcap = kChunk;
+  P.sre_src = 0;
   return P;
 }
 
@@ -385,23 +408,90 @@ void prof_collect(ecg_ctx* c) {
 
 // Reduce the gx per-CTA partials of nent small-matrix entries into
 // P.small[kSmallG ..] (one warp per entry).
-void reduce_small(ecg_ctx* c, const KP& P, int gw, int nent) {
+void reduce_small(ecg_ctx* c, const KP& P, int gw, int nent, int count = 0) {
   const int blocks = (nent * 32 + kThreads - 1) / kThreads;
-  k_reduce_partials<<<blocks, kThreads, 0, c->stream>>>(P.st, gw, P.part_buf, c->gx, nent, P.small + kSmallG);
+  k_reduce_partials<<<blocks, kThreads, 0, c->stream>>>(P.st, gw, P.part_buf, count > 0 ? count : c->gx, nent,
+                                                        P.small + kSmallG);
+}
+
+// Blocks per SM of a kernel at kThreads threads and smem bytes, times the
+// SM count, at most gx (gx when the query fails).
+int occupancy_grid(const ecg_ctx* c, const void* kernel, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return c->gx;
+  }
+  return std::max(1, std::min(c->gx, per_sm * c->num_sms));
+}
+
+// occupancy_grid through the context's cache: the CGS kernels' shared
+// memory depends on the window size, so their grids are looked up per
+// launch; enqueue_group fills the cache before it captures a graph.
+int occ_grid_cached(ecg_ctx* c, const void* kernel, size_t smem) {
+  for (const auto& e : c->occ)
+    if (e.kernel == kernel && e.smem == smem) return e.grid;
+  const int g = occupancy_grid(c, kernel, smem);
+  c->occ.push_back({kernel, smem, g});
+  return g;
+}
+
+// Grids of k_tdot_window and k_update: one wave at their occupancy.
+template <typename T, int W>
+void cgs_grids(ecg_ctx* c, int wcap, int& gt, int& gu) {
+  gt = occ_grid_cached(c, (const void*)k_tdot_window<T, W>, smem_tdot<T, W>(wcap));
+  gu = occ_grid_cached(c, (const void*)k_update<T, W>, smem_update<T, W>(wcap));
+}
+
+template <typename T>
+void warm_cgs_grids(ecg_ctx* c, int W, int wcap) {
+  int gt, gu;
+  switch (W) {
+    case 1: cgs_grids<T, 1>(c, wcap, gt, gu); break;
+    case 2: cgs_grids<T, 2>(c, wcap, gt, gu); break;
+    case 4: cgs_grids<T, 4>(c, wcap, gt, gu); break;
+    case 8: cgs_grids<T, 8>(c, wcap, gt, gu); break;
+    case 16: cgs_grids<T, 16>(c, wcap, gt, gu); break;
+    case 32: cgs_grids<T, 32>(c, wcap, gt, gu); break;
+    case 64: cgs_grids<T, 64>(c, wcap, gt, gu); break;
+  }
+}
+
+template <int W>
+void set_f32_grid(ecg_ctx* c, int wi) {
+  const int a = occupancy_grid(c, (const void*)k_spmm_gram_rows<W, true>, smem_spmm_rows<W>());
+  const int b = occupancy_grid(c, (const void*)k_spmm_gram_rows<W, false>, smem_spmm_rows<W>());
+  c->gx_spmm32[wi] = std::min(a, b);
+  c->gx_fin32[wi] = occupancy_grid(c, (const void*)k_final<float, W>, smem_final<float, W>());
+  c->gx_gram32[wi] = occupancy_grid(c, (const void*)k_gram_self<float, W>, smem_gram_self<float, W>());
+}
+
+void set_f32_grids(ecg_ctx* c) {
+  for (int i = 0; i < 7; i++) c->gx_spmm32[i] = c->gx_fin32[i] = c->gx_gram32[i] = c->gx;
+  set_f32_grid<4>(c, width_index(4));
+  set_f32_grid<8>(c, width_index(8));
+  set_f32_grid<16>(c, width_index(16));
 }
 
 // One iteration of the kernel chain for scalar type T and block width W.
 template <typename T, int W>
-int enqueue_iteration(ecg_ctx* c, int gy) {
+int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   cudaStream_t s = c->stream;
   const bool fp32 = sizeof(T) == 4;
   KP P = make_kp(c, c->d_st, c->d_desc, fp32);
+  P.wcap = wcap;
   T* X = (T*)c->d_X;
   T* Y = (T*)c->d_Y;
   T* x = (T*)P.x;
   T* r = (T*)P.r;
   const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
-  const int gxw = window_gx(c, gy);
+  int gtd, gup;
+  cgs_grids<T, W>(c, wcap, gtd, gup);
+  const int gxw = std::min(window_gx(c, gy), gtd);
+  // the FP32 row-blocked kernels run one wave at their own occupancy
+  const int gsp = F32Rows<T, W>::on ? c->gx_spmm32[width_index(W)] : c->gx;
+  const int gfin = F32Rows<T, W>::on ? c->gx_fin32[width_index(W)] : c->gx;
+  const int ggs = F32Rows<T, W>::on ? c->gx_gram32[width_index(W)] : c->gx;
   const long long tot = (long long)c->n * W;
   const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
   prof_mark(c, -1);
@@ -413,33 +503,41 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
                                                                                P.small + kSmallBe);
     prof_mark(c, 10);
   }
+  P.sre_src = 1;  // an SRE block goes from V_{k-1} straight into the first CGS pass
   k_generate<T, W><<<ggen, kThreads, 0, s>>>(P, W);
   prof_mark(c, 0);
   for (int pass = 0; pass < 2; pass++) {
-    k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(), s>>>(P, W, X);
+    P.sre_src = (pass == 0) ? 1 : 0;
+    k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(wcap), s>>>(P, W, X);
     k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
     prof_mark(c, 1);
-    k_update<T, W><<<c->gx, kThreads, smem_update<T, W>(), s>>>(P, W, X, c->d_C);
+    k_update<T, W><<<gup, kThreads, smem_update<T, W>(wcap), s>>>(P, W, X, c->d_C);
     prof_mark(c, 2);
   }
   if (pre) {
-    k_gram_self<T, W><<<c->gx, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
+    k_gram_self<T, W><<<ggs, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
     prof_mark(c, 3);
-    reduce_small(c, P, W, W * (W + 1) / 2);
+    reduce_small(c, P, W, W * (W + 1) / 2, ggs);
     k_small_e<W><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
     prof_mark(c, 4);
-    k_spmm_gram<T, W, true, true><<<c->gx, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
+    if constexpr (F32Rows<T, W>::on)
+      k_spmm_gram_rows<W, true><<<gsp, kThreads, smem_spmm_rows<W>(), s>>>(P, W, X, Y);
+    else
+      k_spmm_gram<T, W, true, true><<<gsp, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
     prof_mark(c, 5);
-    reduce_small(c, P, W, W * (W + 1) / 2 + W);
-    k_small_a<W, true><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W, gsp);
+    k_small_a<W, true><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
   } else {
-    k_spmm_gram<T, W, true, false><<<c->gx, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
+    if constexpr (F32Rows<T, W>::on)
+      k_spmm_gram_rows<W, false><<<gsp, kThreads, smem_spmm_rows<W>(), s>>>(P, W, X, Y);
+    else
+      k_spmm_gram<T, W, true, false><<<gsp, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
     prof_mark(c, 5);
-    reduce_small(c, P, W, W * (W + 1) / 2 + W);
-    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W, gsp);
+    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
   }
   prof_mark(c, 6);
-  k_final<T, W><<<c->gx, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
+  k_final<T, W><<<gfin, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
   if constexpr (sizeof(T) == 8) {
     if (P.block) {  // block-residual mode: alpha = W_k^T R, R -= V_k alpha, x, r = R 1
       k_block_alpha<W><<<c->gx, kThreads, 0, s>>>(P, W);
@@ -449,39 +547,49 @@ int enqueue_iteration(ecg_ctx* c, int gy) {
     }
   }
   prof_mark(c, 7);
-  k_finish<<<1, kThreads, 0, s>>>(P, W, c->gx, (int)sizeof(T));
+  k_finish<<<1, kThreads, 0, s>>>(P, W, gfin, (int)sizeof(T));
   prof_mark(c, 8);
   CK(cudaGetLastError());
   return ECG_OK;
 }
 
 template <typename T>
-int enqueue_iteration_w(ecg_ctx* c, int W, int gy) {
+int enqueue_iteration_w(ecg_ctx* c, int W, int gy, int wcap) {
   switch (W) {
-    case 1: return enqueue_iteration<T, 1>(c, gy);
-    case 2: return enqueue_iteration<T, 2>(c, gy);
-    case 4: return enqueue_iteration<T, 4>(c, gy);
-    case 8: return enqueue_iteration<T, 8>(c, gy);
-    case 16: return enqueue_iteration<T, 16>(c, gy);
-    case 32: return enqueue_iteration<T, 32>(c, gy);
-    case 64: return enqueue_iteration<T, 64>(c, gy);
+    case 1: return enqueue_iteration<T, 1>(c, gy, wcap);
+    case 2: return enqueue_iteration<T, 2>(c, gy, wcap);
+    case 4: return enqueue_iteration<T, 4>(c, gy, wcap);
+    case 8: return enqueue_iteration<T, 8>(c, gy, wcap);
+    case 16: return enqueue_iteration<T, 16>(c, gy, wcap);
+    case 32: return enqueue_iteration<T, 32>(c, gy, wcap);
+    case 64: return enqueue_iteration<T, 64>(c, gy, wcap);
   }
   return ECG_EINVAL;
 }
 
-// Column chunks of the window for an iteration index bounded by khost.
-int window_chunks(const ecg_ctx* c, int cap, int khost) {
+// Most window columns for an iteration index bounded by khost (every
+// stored block is at most t wide).
+long long window_cols(const ecg_ctx* c, int cap, int khost) {
   long long blocks = std::min<long long>(cap, std::max(0, khost - 1));
-  long long cols = blocks * c->t;
-  return (int)std::max<long long>(1, (cols + kChunk - 1) / kChunk);
+  return blocks * c->t;
+}
+// Column chunks of that window.
+int window_chunks(const ecg_ctx* c, int cap, int khost) {
+  return (int)std::max<long long>(1, (window_cols(c, cap, khost) + kChunk - 1) / kChunk);
 }
 
 // Issue `iters` iterations of width W, through a captured graph when the
 // window size is fixed and the group is a full one.
 int enqueue_group(ecg_ctx* c, bool fp32, int W, int iters, int cap, int khost) {
   const bool fixed = (c->opts.trunc > 0);
-  const int gy = window_chunks(c, cap, fixed ? cap + 1 : khost + iters);
-  auto one = [&]() { return fp32 ? enqueue_iteration_w<float>(c, W, gy) : enqueue_iteration_w<double>(c, W, gy); };
+  const int kb = fixed ? cap + 1 : khost + iters;
+  const int gy = window_chunks(c, cap, kb);
+  const int wcap = (int)std::min<long long>(kChunk, std::max<long long>(1, window_cols(c, cap, kb)));
+  auto one = [&]() {
+    return fp32 ? enqueue_iteration_w<float>(c, W, gy, wcap) : enqueue_iteration_w<double>(c, W, gy, wcap);
+  };
+  if (fp32) warm_cgs_grids<float>(c, W, wcap);  // no occupancy queries inside a capture
+  else warm_cgs_grids<double>(c, W, wcap);
   if (c->opts.use_graph && fixed && !c->profiling && iters == c->opts.check_every) {
     const int wi = width_index(W) + (fp32 ? 7 : 0);
     if (!c->gexec[wi] || c->graph_iters[wi] != iters) {
@@ -1139,6 +1247,7 @@ int ecg_create(const ecg_csr* A, const int32_t* partition, int t, const ecg_opts
   }
   if ((rc = set_all_smem_attrs())) return fail(rc);
   c->gx = std::max(1, std::min(4 * c->num_sms, (n + 31) / 32));
+  set_f32_grids(c);
   const size_t nt = (size_t)n * t;
   const bool mixed = (o.precision == ECG_MIXED);
   if ((rc = dalloc(&c->d_rowptr, (size_t)n + 1)) || (rc = dalloc(&c->d_col, (size_t)nnz)) ||

@@ -127,6 +127,11 @@ struct KP {
   void* z;           // M^{-1} r_{k-1} (n), written by k_prec_solve
   int block;         // 1: block-residual mode (k_final leaves x, r alone)
   double* Rb;        // block residual R_k (n x t), block-residual mode
+  int wcap;          // most window columns a CGS chunk can hold (<= kChunk);
+                     // the CGS kernels' shared memory is sized by it
+  int sre_src;       // 1: an SRE block is read from V_{k-1} where it is
+                     // used (k_generate skips the copy into X, the first
+                     // CGS pass reads V_{k-1} and writes X)
 };
 
 // Block Jacobi preconditioner M = L L^T, L = diag(L_1 .. L_nb), L_i the
@@ -365,6 +370,12 @@ constexpr long long kWaitPolls = 1LL << 26;
 constexpr int kMaxStreams = 16;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// dynamic shared memory of this launch (bytes)
+__device__ __forceinline__ uint32_t dyn_smem_bytes() {
+  uint32_t v;
+  asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+  return v;
+}
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -490,25 +501,55 @@ struct BulkTiles {
 
 // Dynamic shared memory of the tile kernels (bytes), for both the bulk-copy
 // pipeline and the fallback through registers.
+// The CGS kernels are sized by wcap, the most window columns a chunk can
+// hold (min(kChunk, stored blocks x t)): k_tdot_window needs the bulk
+// stages of wcap + W columns, FP32's row-slice sums (kThreads x 16
+// doubles) and the register path's R x (kChunk + W) tile; k_update needs
+// wcap x W coefficients and then the bulk stages or the register path's
+// R x wcap tile.
 template <typename T, int W>
-constexpr size_t smem_tdot() {
-  // FP32 also sums its row slices there: kThreads x 16 doubles
-  return 64 + ((sizeof(T) * Stages<T>::S * TdotTile<T, W>::R * (kChunk + W)) > (sizeof(T) == 4 ? kThreads * 16 * 8 : 0)
-                   ? sizeof(T) * Stages<T>::S * TdotTile<T, W>::R * (kChunk + W)
-                   : (size_t)kThreads * 16 * 8);
+constexpr size_t smem_tdot(int wcap = kChunk) {
+  constexpr size_t R = TdotTile<T, W>::R;
+  const size_t bulk = sizeof(T) * Stages<T>::S * R * (size_t)(wcap + W);
+  const size_t red = sizeof(T) == 4 ? (size_t)kThreads * 16 * 8 : 0;
+  const size_t reg = sizeof(T) * R * (kChunk + W);
+  const size_t m = bulk > red ? bulk : red;
+  return 64 + (m > reg ? m : reg);
 }
 template <typename T, int W>
-constexpr size_t smem_update() {
-  return sizeof(T) * kChunk * W + 64 + sizeof(T) * Stages<T>::S * UpdTile<T, W>::R * (kChunk + W);
+constexpr size_t smem_update(int wcap = kChunk) {
+  constexpr size_t R = UpdTile<T, W>::R;
+  const size_t cc = (size_t)(wcap < kChunk ? wcap : kChunk);
+  const size_t coef = (sizeof(T) * cc * W + 15) & ~(size_t)15;
+  const size_t bulk = 64 + sizeof(T) * Stages<T>::S * R * (cc + W);
+  const size_t reg = sizeof(T) * R * cc;
+  return coef + (bulk > reg ? bulk : reg);
 }
 template <typename T, int W>
 constexpr size_t smem_gram_self() {
+  // FP32 (W 4, 8, 16): kThreads-row stages, then 16 x kThreads doubles
+  if constexpr (sizeof(T) == 4 && (W == 4 || W == 8 || W == 16)) {
+    constexpr size_t st = sizeof(float) * Stages<float>::S * kThreads * W, red = sizeof(double) * 16 * kThreads;
+    return 64 + (st > red ? st : red);
+  }
   return 64 + sizeof(T) * Stages<T>::S * Tile<W>::R * W;
 }
 template <typename T, int W>
-constexpr size_t smem_final() {
+constexpr size_t smem_final_scalar() {
   return sizeof(double) * kThreads + 64 +
          sizeof(T) * ((2 * Stages<T>::S + 3) * Tile<W>::R * W + W * W + W + Tile<W>::R);
+}
+constexpr int kFinStages = 2;  // stages of the FP32 row-per-thread k_final
+template <int W>
+constexpr size_t smem_final_f32() {
+  return sizeof(double) * kThreads + 64 + sizeof(float) * ((size_t)kFinStages * 2 * kThreads * W + W * W + W) +
+         sizeof(float) * kThreads + sizeof(double) * kThreads;
+}
+template <typename T, int W>
+constexpr size_t smem_final() {
+  return (sizeof(T) == 4 && (W == 4 || W == 8 || W == 16) && smem_final_f32<W>() > smem_final_scalar<T, W>())
+             ? smem_final_f32<W>()
+             : smem_final_scalar<T, W>();
 }
 
 // Row ranges aligned to the tile height, so that all but the last tile of
@@ -612,8 +653,9 @@ __global__ void __launch_bounds__(kThreads) k_generate(KP P, int gw) {
   const T* vprev = last ? (const T*)last->V : nullptr;
   const T* pprev = last ? (const T*)last->W : nullptr;
   const double* beta = P.small + kSmallBe;
-  // preconditioned: k_prec_solve wrote X = M^{-1} V_{k-1}, or z = M^{-1} r
-  if (P.prec && gen == GEN_SRE) return;
+  // preconditioned: k_prec_solve wrote X = M^{-1} V_{k-1}, or z = M^{-1} r;
+  // with sre_src the first CGS pass reads V_{k-1} itself
+  if ((P.prec || P.sre_src) && gen == GEN_SRE) return;
   const T* r = (const T*)(P.prec ? P.z : P.r);
   T* X = (T*)P.X;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
@@ -649,6 +691,8 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
   const int wtot = D[nq - 1].off + D[nq - 1].w;
   const int c0 = blockIdx.y * kChunk;
   if (c0 >= wtot) return;
+  // the SRE block A W_{k-1} = V_{k-1}, not copied into X
+  if (P.sre_src && !P.prec && st->gen == GEN_SRE) B = (const T*)D[nq - 1].V;
   const int ncol = min(kChunk, wtot - c0);
   __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
@@ -680,6 +724,7 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
     bulk = bt.add(D[j].V, D[j].w * (int)sizeof(T));
   }
   bulk = bulk && span <= kChunk && bt.add(B, WB * (int)sizeof(T));
+  bulk = bulk && 64u + (uint32_t)S * (uint32_t)bt.stage_bytes <= dyn_smem_bytes();
   if (bulk) {
     cta_rows_aligned(P.n, R, bt.r0, bt.r1);
     bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
@@ -702,7 +747,7 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
       // columns lie in one block and start on a 16-byte boundary
       for (int j = jlo; j <= jhi; j++) w4 = w4 && (D[j].w % 4 == 0);
       const int EB = (ncol / 4) * BB;
-      if (w4 && EB <= kThreads) {
+      if (w4 && EB <= kThreads && 64u + kThreads * 16u * 8u <= dyn_smem_bytes()) {
         const int RS = kThreads / EB;
         const int eb = threadIdx.x % EB, rs = threadIdx.x / EB;
         const bool active = rs < RS;
@@ -850,14 +895,20 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
   if (nq <= 0) return;
   const BlockDesc* D = P.desc;
   const int wtot = D[nq - 1].off + D[nq - 1].w;
-  const int nch = (wtot + kChunk - 1) / kChunk;
+  // the block is read from Xsrc and written to Xio: V_{k-1} on the first
+  // pass of an SRE iteration whose generator skipped the copy, else X
+  const T* Xsrc = (P.sre_src && !P.prec && st->gen == GEN_SRE) ? (const T*)D[nq - 1].V : Xio;
+  // window columns per pass: the launch's shared memory holds ccap x W
+  // coefficients and ccap window columns of a tile
+  const int ccap = min(kChunk, P.wcap);
+  const int nch = (wtot + ccap - 1) / ccap;
   __shared__ const T* cptr[kChunk];
   __shared__ int cstr[kChunk];
   __shared__ int cofs[kChunk];  // pipelined: element offset of (row 0, column) in a stage
   __shared__ BulkStream sst[kMaxStreams];
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* sC = (T*)smem_raw;  // kChunk x W
-  unsigned char* rest = smem_raw + sizeof(T) * kChunk * W;
+  T* sC = (T*)smem_raw;  // ccap x W
+  unsigned char* rest = smem_raw + ((sizeof(T) * ccap * W + 15) & ~(size_t)15);
   BulkTiles<S> bt;
   bt.st = sst;
   bt.bar = (uint64_t*)rest;
@@ -865,7 +916,8 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
   bt.R = R;
   bool bulk = (nch == 1 && nq + 1 <= kMaxStreams);
   for (int j = 0; j < nq && bulk; j++) bulk = bt.add(D[j].W, D[j].w * (int)sizeof(T));
-  bulk = bulk && bt.add(Xio, W * (int)sizeof(T));
+  bulk = bulk && bt.add(Xsrc, W * (int)sizeof(T));
+  bulk = bulk && (uint32_t)(rest - smem_raw) + 64u + (uint32_t)S * (uint32_t)bt.stage_bytes <= dyn_smem_bytes();
   if (bulk) {
     if (threadIdx.x < wtot) {
       const int cg = threadIdx.x;
@@ -966,7 +1018,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
     }
     return;
   }
-  T* sQ = (T*)rest;  // R x kChunk
+  T* sQ = (T*)rest;  // R x ccap
   int r0, r1;
   cta_rows(P.n, r0, r1);
   for (int row0 = r0; row0 < r1; row0 += R) {
@@ -976,11 +1028,11 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
     for (int q = 0; q < EPT; q++) {
       int e = threadIdx.x + q * kThreads;
       int r = e / W;
-      acc[q] = (e < R * W && r < nr) ? Xio[(long long)row0 * W + e] : T(0);
+      acc[q] = (e < R * W && r < nr) ? Xsrc[(long long)row0 * W + e] : T(0);
     }
     for (int ch = 0; ch < nch; ch++) {
-      const int c0 = ch * kChunk;
-      const int ncol = min(kChunk, wtot - c0);
+      const int c0 = ch * ccap;
+      const int ncol = min(ccap, wtot - c0);
       __syncthreads();
       if (threadIdx.x < ncol) {
         int cg = c0 + threadIdx.x;
@@ -997,7 +1049,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
       __syncthreads();
       for (int idx = threadIdx.x; idx < R * ncol; idx += blockDim.x) {
         int r = idx / ncol, cc = idx - r * ncol;
-        sQ[r * kChunk + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
+        sQ[r * ccap + cc] = (r < nr) ? cptr[cc][(long long)(row0 + r) * cstr[cc]] : T(0);
       }
       __syncthreads();
 #pragma unroll
@@ -1006,7 +1058,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
         if (e < R * W) {
           int r = e / W, bb = e - r * W;
           T s = acc[q];
-          for (int a = 0; a < ncol; a++) s = fma(-sQ[r * kChunk + a], sC[a * W + bb], s);
+          for (int a = 0; a < ncol; a++) s = fma(-sQ[r * ccap + a], sC[a * W + bb], s);
           acc[q] = s;
         }
       }
@@ -1023,6 +1075,131 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
 
 // ------------------------------------------------------- orthonormalisation
 
+// ------------------------------------------- FP32 register-blocked forms
+// FP32 spends two shared-memory reads per FMA in the scalar forms above, so
+// its tile kernels are bound by those reads rather than by HBM.  For block
+// widths 4, 8 and 16 the kernels below give each thread whole rows or 4 x 4
+// blocks, with 16-byte shared-memory reads.
+
+// FP32 block widths with a register-blocked spmm_gram / final.
+template <typename T, int W>
+struct F32Rows {
+  static constexpr bool on = sizeof(T) == 4 && (W == 4 || W == 8 || W == 16);
+};
+
+// Row stride (floats) of the FP32 spmm_gram tiles: W columns plus one
+// 16-byte chunk, which holds (r_i, 0, 0, 0) in the Y rows so that
+// g = q^T r comes out of the same 4 x 4 blocks as G.  For W = 8 and 16 the
+// stride is an odd number of 16-byte chunks, so that eight consecutive rows
+// read at the same column land in eight different bank groups.
+template <int W>
+struct PadStride {
+  static constexpr int SP = W + 4;
+};
+
+// u-th component of a float4 (u a compile-time constant after unrolling).
+__device__ __forceinline__ float f4c(const float4& v, int u) {
+  return u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4fma(float4& acc, float a, const float4& b) {
+  acc.x = fmaf(a, b.x, acc.x);
+  acc.y = fmaf(a, b.y, acc.y);
+  acc.z = fmaf(a, b.z, acc.z);
+  acc.w = fmaf(a, b.w, acc.w);
+}
+
+// acc[c] = (x U)[4c .. 4c+3] for one row x (W floats, 16-byte aligned) and
+// the upper-triangular W x W matrix U (row-major, zeros below the
+// diagonal): chunk m of x meets only column chunks c >= m.
+template <int W>
+__device__ __forceinline__ void tri_row4(const float* x, const float* U, float4 (&acc)[W / 4]) {
+  constexpr int C4 = W / 4;
+#pragma unroll
+  for (int c = 0; c < C4; c++) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < C4; m++) {
+    const float4 xa = *reinterpret_cast<const float4*>(x + 4 * m);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const float xl = f4c(xa, u);
+      const float4* Ul = reinterpret_cast<const float4*>(U + (4 * m + u) * W);
+#pragma unroll
+      for (int c = m; c < C4; c++) f4fma(acc[c], xl, Ul[c]);
+    }
+  }
+}
+
+// k_gram_self for FP32 and W in {4, 8, 16}: tiles of kThreads rows through
+// the bulk-copy pipeline; each thread owns a 4 x 4 block (ab <= bb) of
+// X^T X and a slice of every tile's rows (16-byte shared-memory reads, 16
+// FMAs per pair), FP32 per tile and compensated across tiles.  The slices
+// are summed in the freed stages at the end.  Returns false, before
+// touching shared memory, when X is not 16-byte aligned.
+template <int W>
+__device__ __forceinline__ bool gram_self_f32(const KP& P, const DevState* st, const float* Xin) {
+  constexpr int R = kThreads, C4 = W / 4, EU = C4 * (C4 + 1) / 2, RS = kThreads / EU, E = W * (W + 1) / 2;
+  constexpr int S = Stages<float>::S;
+  if (((uintptr_t)Xin & 15) != 0) return false;
+  __shared__ BulkStream sst[kMaxStreams];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = (uint64_t*)smem_raw;
+  bt.stage = smem_raw + 64;
+  bt.R = R;
+  bt.add(Xin, W * (int)sizeof(float));
+  cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+  bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
+  const int eb = threadIdx.x % EU, rs = threadIdx.x / EU;
+  const bool active = rs < RS;
+  int ab, bb;
+  upper_ab(eb, C4, ab, bb);
+  RowAcc<float> ra[16];
+  bt.start();
+  for (int i = 0; i < bt.ntiles; i++) {
+    if (!bt.ready(i, (DevState*)st)) return true;
+    const float4* t4 = reinterpret_cast<const float4*>(bt.tile(i));
+    const int nr = bt.rows(i);
+    if (active) {
+      float sv[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) sv[k] = 0.f;
+      for (int r = rs; r < nr; r += RS) {
+        const float4 qa = t4[r * C4 + ab];
+        const float4 qb = t4[r * C4 + bb];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const float qu = f4c(qa, u);
+          sv[u * 4 + 0] = fmaf(qu, qb.x, sv[u * 4 + 0]);
+          sv[u * 4 + 1] = fmaf(qu, qb.y, sv[u * 4 + 1]);
+          sv[u * 4 + 2] = fmaf(qu, qb.z, sv[u * 4 + 2]);
+          sv[u * 4 + 3] = fmaf(qu, qb.w, sv[u * 4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; k++) ra[k].end(sv[k]);
+    }
+    bt.next(i);
+  }
+  double* red = reinterpret_cast<double*>(smem_raw + 64);  // [16][kThreads]
+  __syncthreads();
+  if (active)
+#pragma unroll
+    for (int k = 0; k < 16; k++) red[k * kThreads + threadIdx.x] = ra[k].value();
+  __syncthreads();
+  double* out = P.part_buf + (long long)blockIdx.x * E;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    int a, b;
+    upper_ab(e, W, a, b);
+    const int ba = a / 4, bq = b / 4;
+    const int ebe = ba * C4 - ba * (ba - 1) / 2 + (bq - ba), k = (a % 4) * 4 + (b % 4);
+    double sum = 0.0;
+    for (int q = 0; q < RS; q++) sum += red[k * kThreads + q * EU + ebe];
+    out[e] = sum;
+  }
+  return true;
+}
+
 // Partial upper-triangle Gram X^T X (Euclidean step of Pre-CholQR).
 template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* Xin) {
@@ -1032,6 +1209,9 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
   constexpr int S = Stages<T>::S;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
+  if constexpr (F32Rows<T, W>::on) {
+    if (gram_self_f32<W>(P, st, (const float*)Xin)) return;
+  }
   __shared__ BulkStream sst[kMaxStreams];
   extern __shared__ __align__(16) unsigned char smem_raw[];
   int ea[EPT], eb[EPT];
@@ -1087,9 +1267,28 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
   }
 }
 
+// 1/sqrt(d) for a positive normal d: an FP32 estimate refined by two steps
+// of Newton's method for f(y) = y^{-2} - d, y <- y + y (1 - d y^2) / 2.
+// Each step squares the relative error (about 1e-7 for the estimate), so
+// two end at FP64 rounding.  On this GPU an FP64 square root and division
+// are long chains of FP64 instructions, and the factorisations below are
+// latency-bound on them.  Outside the FP32 exponent range the plain
+// quotient is taken.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+  double y = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const double e = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, e, y);
+  }
+  return y;
+}
+
 // Cholesky G = R^T R of the W x W matrix in sG (full symmetric storage) into
 // sR (upper), with the pivot test pivot <= ratio * G_jj.  Returns false on
-// breakdown.  sG is destroyed.  All threads of the CTA must call it.
+// breakdown.  sG is destroyed; sD (W doubles) ends holding 1 / R_jj.  All
+// threads of the CTA must call it.
 template <int W>
 __device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag, double ratio) {
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) sR[i] = 0.0;
@@ -1099,13 +1298,18 @@ __device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag, dou
   for (int j = 0; j < W; j++) {
     if (threadIdx.x == 0) {
       double d = sG[j * W + j];
-      if (!(d > ratio * sD[j]) || !isfinite(d)) *sflag = 1;
-      else sR[j * W + j] = sqrt(d);
+      if (!(d > ratio * sD[j]) || !isfinite(d)) {
+        *sflag = 1;
+      } else {
+        const double inv = rsqrt_newton(d);
+        sR[j * W + j] = d * inv;
+        sD[j] = inv;  // the pivot test of column j is done
+      }
     }
     __syncthreads();
     if (*sflag) return false;
-    const double rjj = sR[j * W + j];
-    for (int i = j + 1 + threadIdx.x; i < W; i += blockDim.x) sR[j * W + i] = sG[j * W + i] / rjj;
+    const double inv = sD[j];
+    for (int i = j + 1 + threadIdx.x; i < W; i += blockDim.x) sR[j * W + i] = sG[j * W + i] * inv;
     __syncthreads();
     const int m = W - j - 1;
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
@@ -1117,9 +1321,10 @@ __device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag, dou
   return true;
 }
 
-// Inverse of the upper-triangular sR into sRi (upper), one column per thread.
+// Inverse of the upper-triangular sR into sRi (upper), one column per
+// thread; sInv holds 1 / R_ii (from cta_cholesky).
 template <int W>
-__device__ void cta_triu_inverse(const double* sR, double* sRi) {
+__device__ void cta_triu_inverse(const double* sR, const double* sInv, double* sRi) {
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = 0.0;
   __syncthreads();
   if (threadIdx.x < W) {
@@ -1127,7 +1332,7 @@ __device__ void cta_triu_inverse(const double* sR, double* sRi) {
     for (int i = c; i >= 0; i--) {
       double s = (i == c) ? 1.0 : 0.0;
       for (int l = i + 1; l <= c; l++) s = fma(-sR[i * W + l], sRi[l * W + c], s);
-      sRi[i * W + c] = s / sR[i * W + i];
+      sRi[i * W + c] = s * sInv[i];
     }
   }
   __syncthreads();
@@ -1162,20 +1367,183 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
     }
     return;
   }
-  cta_triu_inverse<W>(sR, sRi);
+  cta_triu_inverse<W>(sR, sD, sRi);
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) P.small[kSmallRe + i] = sRi[i];
 }
 
+// 4 x 4 blocks of the FP32 spmm_gram: the upper blocks (ab <= bb) of G and
+// the column chunk C4 (r) for g.
+template <int W>
+struct GramBlocks {
+  static constexpr int C4 = W / 4, EU = C4 * (C4 + 1) / 2, EB = EU + C4, RS = kThreads / EB;
+};
+
+// Shared memory (bytes) of the FP32 spmm_gram: the X and Y tiles (padded
+// rows), R_e^{-1}, and each thread's 16 FP64 running sums.
+template <int W>
+__host__ __device__ constexpr size_t smem_spmm_f32_tiles() {
+  return sizeof(float) * (2 * kThreads * PadStride<W>::SP + W * W);
+}
+template <int W>
+constexpr size_t smem_spmm_f32() {
+  return smem_spmm_f32_tiles<W>() + sizeof(double) * 16 * kThreads;
+}
+
+// k_spmm_gram for FP32 and W in {4, 8, 16}.  Tiles of kThreads rows:
+//  1. Y = A X four columns per item (float4 gathers of X), Y to global
+//     memory and to shared memory with the tile's X rows and r;
+//  2. PRE: q = X R_e^{-1}, v = Y R_e^{-1} in place, one thread per row;
+//  3. each thread owns a 4 x 4 block of [q^T v | q^T r] (upper blocks of
+//     G, and the r chunk) and a slice of the rows.  Per-tile sums are FP32,
+//     added across tiles into FP64 running sums in shared memory ([16] x
+//     [thread], so that a warp's accesses are consecutive).
+// The row slices are summed at the end; the partials have
+// the layout of the scalar form ([G upper | g] per CTA).  Returns false,
+// before touching shared memory, when X or Y is not 16-byte aligned.
+template <int W, bool PRE>
+__device__ __forceinline__ bool spmm_gram_f32(const KP& P, const float* Xin, float* Yout) {
+  constexpr int R = kThreads, C4 = W / 4, SP = PadStride<W>::SP;
+  constexpr int EU = GramBlocks<W>::EU, EB = GramBlocks<W>::EB, RS = GramBlocks<W>::RS, E = W * (W + 1) / 2;
+  constexpr int IT = R * C4 / kThreads;
+  if ((((uintptr_t)Xin | (uintptr_t)Yout) & 15) != 0) return false;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sX = (float*)smem_raw;  // R x SP: X, then q
+  float* sY = sX + R * SP;       // R x SP: [Y | r 0 0 0], then [v | r 0 0 0]
+  float* sRe = sY + R * SP;      // W x W
+  double* acc = (double*)(smem_raw + smem_spmm_f32_tiles<W>());  // 16 x kThreads
+  const float* val = values<float>(P);
+  const float* rvec = (const float*)P.r;
+  const float4* X4 = reinterpret_cast<const float4*>(Xin);
+  float4* Y4 = reinterpret_cast<float4*>(Yout);
+  if (PRE)
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRe[i] = (float)P.small[kSmallRe + i];
+  const int eb = threadIdx.x % EB, rs = threadIdx.x / EB;
+  const bool active = rs < RS;
+  int ab, bb;
+  if (eb < EU) {
+    upper_ab(eb, C4, ab, bb);
+  } else {
+    ab = eb - EU;
+    bb = C4;
+  }
+#pragma unroll
+  for (int k = 0; k < 16; k++) acc[k * kThreads + threadIdx.x] = 0.0;
+  int r0, r1;
+  cta_rows(P.n, r0, r1);
+  for (int row0 = r0; row0 < r1; row0 += R) {
+    const int nr = min(R, r1 - row0);
+    int pb[IT], pe[IT];
+    float4 y[IT];
+    int kmax = 0;
+#pragma unroll
+    for (int q = 0; q < IT; q++) {
+      const int r = (threadIdx.x + q * kThreads) / C4;
+      pb[q] = pe[q] = 0;
+      if (r < nr) {
+        pb[q] = P.rowptr[row0 + r];
+        pe[q] = P.rowptr[row0 + r + 1];
+      }
+      kmax = max(kmax, pe[q] - pb[q]);
+      y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int k = 0; k < kmax; k++) {
+#pragma unroll
+      for (int q = 0; q < IT; q++) {
+        const int p = pb[q] + k;
+        if (p < pe[q]) {
+          const int c = (threadIdx.x + q * kThreads) % C4;
+          f4fma(y[q], val[p], X4[(long long)P.col[p] * C4 + c]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < IT; q++) {
+      const int idx = threadIdx.x + q * kThreads, r = idx / C4, c = idx % C4;
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < nr) {
+        const long long o = (long long)(row0 + r) * C4 + c;
+        Y4[o] = y[q];
+        xv = X4[o];
+      }
+      *reinterpret_cast<float4*>(sY + r * SP + 4 * c) = y[q];
+      *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = xv;
+    }
+    {
+      const int r = threadIdx.x;
+      *reinterpret_cast<float4*>(sY + r * SP + W) = make_float4((r < nr) ? rvec[row0 + r] : 0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+    if (PRE) {
+      const int r = threadIdx.x;
+      if (r < nr) {
+        float4 t4[C4];
+        tri_row4<W>(sX + r * SP, sRe, t4);
+#pragma unroll
+        for (int c = 0; c < C4; c++) *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = t4[c];
+        tri_row4<W>(sY + r * SP, sRe, t4);
+#pragma unroll
+        for (int c = 0; c < C4; c++) *reinterpret_cast<float4*>(sY + r * SP + 4 * c) = t4[c];
+      }
+      __syncthreads();
+    }
+    if (active) {
+      float sv[16];
+#pragma unroll
+      for (int k = 0; k < 16; k++) sv[k] = 0.f;
+      for (int r = rs; r < nr; r += RS) {
+        const float4 qa = *reinterpret_cast<const float4*>(sX + r * SP + 4 * ab);
+        const float4 vb = *reinterpret_cast<const float4*>(sY + r * SP + 4 * bb);
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+          const float qu = f4c(qa, u);
+          sv[u * 4 + 0] = fmaf(qu, vb.x, sv[u * 4 + 0]);
+          sv[u * 4 + 1] = fmaf(qu, vb.y, sv[u * 4 + 1]);
+          sv[u * 4 + 2] = fmaf(qu, vb.z, sv[u * 4 + 2]);
+          sv[u * 4 + 3] = fmaf(qu, vb.w, sv[u * 4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; k++) acc[k * kThreads + threadIdx.x] += (double)sv[k];
+    }
+    __syncthreads();
+  }
+  // sum the row slices: thread rs * EB + eb holds block eb of slice rs
+  __syncthreads();
+  double* out = P.part_buf + (long long)blockIdx.x * (E + W);
+  for (int e = threadIdx.x; e < E + W; e += blockDim.x) {
+    int ebe, k;
+    if (e < E) {
+      int a, b;
+      upper_ab(e, W, a, b);
+      const int ba = a / 4, bq = b / 4;
+      ebe = ba * C4 - ba * (ba - 1) / 2 + (bq - ba);
+      k = (a % 4) * 4 + (b % 4);
+    } else {
+      const int a = e - E;
+      ebe = EU + a / 4;
+      k = (a % 4) * 4;
+    }
+    double s = 0.0;
+    for (int q = 0; q < RS; q++) s += acc[k * kThreads + q * EB + ebe];
+    out[e] = s;
+  }
+  return true;
+}
+
 // Y = A X; with GRAM, per-CTA partials of G = q^T (A q) (upper) and
-// g = q^T r, q = X R_e^{-1} when PRE (else q = X).
-template <typename T, int W, bool GRAM, bool PRE>
-__global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const T* Xin, T* Yout) {
+// g = q^T r, q = X R_e^{-1} when PRE (else q = X).  ROWS: the FP32
+// register-blocked form (k_spmm_gram_rows), else the scalar one.
+template <typename T, int W, bool GRAM, bool PRE, bool ROWS>
+__device__ __forceinline__ void spmm_gram_body(const KP& P, int gw, const T* Xin, T* Yout) {
   constexpr int R = Tile<W>::R;
   constexpr int E = W * (W + 1) / 2;
   constexpr int EPT = (E + kThreads - 1) / kThreads;
   constexpr int EPT2 = (R * W + kThreads - 1) / kThreads;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
+  if constexpr (ROWS) {
+    if (spmm_gram_f32<W, PRE>(P, (const float*)Xin, (float*)Yout)) return;
+  }
   const T* val = values<T>(P);
   const T* rvec = (const T*)P.r;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1274,6 +1642,17 @@ __global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const T* X
   }
 }
 
+template <typename T, int W, bool GRAM, bool PRE>
+__global__ void __launch_bounds__(kThreads) k_spmm_gram(KP P, int gw, const T* Xin, T* Yout) {
+  spmm_gram_body<T, W, GRAM, PRE, false>(P, gw, Xin, Yout);
+}
+
+// The FP32 register-blocked form (W in {4, 8, 16}) at three CTAs per SM.
+template <int W, bool PRE>
+__global__ void __launch_bounds__(kThreads, 3) k_spmm_gram_rows(KP P, int gw, const float* Xin, float* Yout) {
+  spmm_gram_body<float, W, true, PRE, true>(P, gw, Xin, Yout);
+}
+
 // A-CholQR step: reduce G and g, G = S^T S, R^{-1} = [R_e^{-1}] S^{-1},
 // alpha = S^{-T} g (= W_k^T r_{k-1}).
 template <int W, bool PRE>
@@ -1309,7 +1688,7 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
     }
     return;
   }
-  cta_triu_inverse<W>(sR, sSi);
+  cta_triu_inverse<W>(sR, sD, sSi);
   for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
     int a = e / W, b = e % W;
     double s = 0.0;
@@ -1330,6 +1709,98 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   }
 }
 
+// k_final for FP32 and W in {4, 8, 16}, one thread per row: the thread
+// reads its rows of X and Y from the stage, forms W_k = X R^{-1} and
+// V_k = Y R^{-1} in registers (R^{-1} read as broadcast 16-byte rows),
+// stores both rows, and updates x and r with W_k alpha and V_k alpha.  For
+// MSDO-CG, V_k replaces Y in the stage and the CTA sums V_k^T r_k over row
+// slices.  Returns false, before touching shared memory, when the blocks do
+// not suit the bulk copies; the caller then takes the scalar form.
+template <int W>
+__device__ __forceinline__ bool final_f32(const KP& P, const DevState* st, const float* Xin, const float* Yin,
+                                          float* Wout, float* Vout, float* xio, float* rio) {
+  constexpr int R = kThreads, C4 = W / 4, S = kFinStages, RSB = kThreads / W;
+  if ((((uintptr_t)Xin | (uintptr_t)Yin | (uintptr_t)Wout | (uintptr_t)Vout) & 15) != 0) return false;
+  __shared__ BulkStream sst[kMaxStreams];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sbuf = (double*)smem_raw;                        // kThreads
+  uint64_t* sbar = (uint64_t*)(sbuf + kThreads);           // 64 bytes
+  float* stg = (float*)((unsigned char*)sbar + 64);        // S stages of [R x W | R x W]
+  float* sRi = stg + S * 2 * R * W;                        // W x W
+  float* sal = sRi + W * W;                                // W
+  float* srn = sal + W;                                    // R
+  double* sbr = (double*)(srn + R);                        // RSB x W
+  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = (float)P.small[kSmallRi + i];
+  for (int i = threadIdx.x; i < W; i += blockDim.x) sal[i] = P.block ? 0.f : (float)P.small[kSmallAl + i];
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = sbar;
+  bt.stage = (unsigned char*)stg;
+  bt.R = R;
+  bt.add(Xin, W * (int)sizeof(float));
+  bt.add(Yin, W * (int)sizeof(float));
+  cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+  bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
+  bt.start();  // its barrier also publishes sRi and sal
+  double rho_acc = 0.0;
+  RowAcc<float> beta_acc;
+  const bool beta = P.want_beta != 0;
+  const int bcol = threadIdx.x % W, bsl = threadIdx.x / W;
+  for (int i = 0; i < bt.ntiles; i++) {
+    if (!bt.ready(i, (DevState*)st)) return true;
+    float* tX = (float*)bt.tile(i);
+    float* tY = tX + R * W;
+    const int nr = bt.rows(i), row0 = bt.r0 + i * R;
+    const int r = threadIdx.x;
+    float rn = 0.f;
+    if (r < nr) {
+      float4 w[C4], v[C4];
+      tri_row4<W>(tX + r * W, sRi, w);
+      tri_row4<W>(tY + r * W, sRi, v);
+      const long long o = (long long)(row0 + r) * C4;
+      float dx = 0.f, dr = 0.f;
+#pragma unroll
+      for (int c = 0; c < C4; c++) {
+        reinterpret_cast<float4*>(Wout)[o + c] = w[c];
+        reinterpret_cast<float4*>(Vout)[o + c] = v[c];
+        const float4 al = *reinterpret_cast<const float4*>(sal + 4 * c);
+        dx = fmaf(w[c].x, al.x, fmaf(w[c].y, al.y, fmaf(w[c].z, al.z, fmaf(w[c].w, al.w, dx))));
+        dr = fmaf(v[c].x, al.x, fmaf(v[c].y, al.y, fmaf(v[c].z, al.z, fmaf(v[c].w, al.w, dr))));
+      }
+      const int gi = row0 + r;
+      xio[gi] += dx;
+      rn = rio[gi] - dr;
+      rio[gi] = rn;
+      rho_acc += (double)rn * (double)rn;
+      if (beta) {
+#pragma unroll
+        for (int c = 0; c < C4; c++) *reinterpret_cast<float4*>(tY + r * W + 4 * c) = v[c];
+      }
+    }
+    if (beta) {
+      srn[r] = rn;
+      fence_proxy_async();  // the stage is refilled by the async proxy next
+      __syncthreads();
+      float s = 0.f;
+      for (int q = bsl; q < nr; q += RSB) s = fmaf(tY[q * W + bcol], srn[q], s);
+      beta_acc.end(s);
+    }
+    bt.next(i);
+  }
+  const double tot = block_sum(rho_acc, sbuf);
+  if (threadIdx.x == 0) P.rho_part[blockIdx.x] = tot;
+  if (beta) {
+    sbr[bsl * W + bcol] = beta_acc.value();
+    __syncthreads();
+    if (threadIdx.x < W) {
+      double s = 0.0;
+      for (int q = 0; q < RSB; q++) s += sbr[q * W + threadIdx.x];
+      P.beta_part[(long long)blockIdx.x * 64 + threadIdx.x] = s;
+    }
+  }
+  return true;
+}
+
 // W_k = X R^{-1}, V_k = Y R^{-1} (written to Wout / Vout), x += W_k alpha,
 // r -= V_k alpha; per-CTA ||r_k||^2 and, for MSDO-CG, V_k^T r_k partials.
 template <typename T, int W>
@@ -1342,6 +1813,11 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
     const long long s = st->next_slot;
     Wout = (T*)P.slotW + s * P.slot_stride;
     Vout = (T*)P.slotV + s * P.slot_stride;
+  }
+  if constexpr (F32Rows<T, W>::on) {
+    if (final_f32<W>(P, st, (const float*)Xin, (const float*)Yin, (float*)Wout, (float*)Vout, (float*)xio,
+                     (float*)rio))
+      return;
   }
   constexpr int S = Stages<T>::S;
   __shared__ BulkStream sst[kMaxStreams];
@@ -1771,26 +2247,34 @@ __global__ void __launch_bounds__(kThreads) k_block_update(KP P, int gw) {
   int r0, r1;
   cta_rows(P.n, r0, r1);
   double acc = 0.0;
+  // columns of alpha in chunks of CU, each against the whole row of W_k and
+  // V_k (re-read from L1), so that no row is held in registers
+  constexpr int CU = W < 4 ? W : 4;
   for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-    double w[W], v[W];
-#pragma unroll
-    for (int a = 0; a < W; a++) {
-      w[a] = Wk[(long long)i * W + a];
-      v[a] = Vk[(long long)i * W + a];
-    }
+    const double* wi = Wk + (long long)i * W;
+    const double* vi = Vk + (long long)i * W;
+    double* Ri = P.Rb + (long long)i * W;
     double dx = 0.0, rs = 0.0;
+    for (int c0 = 0; c0 < W; c0 += CU) {
+      double sx[CU], sr[CU];
 #pragma unroll
-    for (int c = 0; c < W; c++) {
-      double sx = 0.0, sr = 0.0;
-#pragma unroll
+      for (int u = 0; u < CU; u++) sx[u] = sr[u] = 0.0;
+#pragma unroll 4
       for (int a = 0; a < W; a++) {
-        sx = fma(w[a], sal[a * W + c], sx);
-        sr = fma(v[a], sal[a * W + c], sr);
+        const double wa = wi[a], va = vi[a];
+#pragma unroll
+        for (int u = 0; u < CU; u++) {
+          sx[u] = fma(wa, sal[a * W + c0 + u], sx[u]);
+          sr[u] = fma(va, sal[a * W + c0 + u], sr[u]);
+        }
       }
-      const double rn = P.Rb[(long long)i * W + c] - sr;
-      P.Rb[(long long)i * W + c] = rn;
-      dx += sx;
-      rs += rn;
+#pragma unroll
+      for (int u = 0; u < CU; u++) {
+        const double rn = Ri[c0 + u] - sr[u];
+        Ri[c0 + u] = rn;
+        dx += sx[u];
+        rs += rn;
+      }
     }
     x[i] += dx;
     r[i] = rs;

@@ -86,3 +86,41 @@ def test_mixed_at_full_size_reports_its_true_residual():
     assert abs(g.relres - true) <= 1e-6 * true
     assert abs(g.history[-1] / g.history[0] - true) <= 1e-6 * true
     assert true < 0.5
+
+
+# Multi-tile cases for the FP32 tile kernels: with 122k-250k rows each CTA
+# of spmm_gram and final works through two or more 256-row tiles, the last
+# one ragged.  Widths 16, 8 and 4, both orthonormalisations, and MSDO-CG
+# (whose final kernel also sums V_k^T r_k).
+FP32_CASES = [
+    ("spd350_t16_trunc2", lambda: W.random_spd_grid(350, 16, seed=61), dict(trunc=2)),
+    ("spd350_t16_trunc2_acholqr", lambda: W.random_spd_grid(350, 16, seed=61), dict(trunc=2, ortho=ecg.A_CHOLQR)),
+    ("spd350_t16_msdo_trunc2", lambda: W.random_spd_grid(350, 16, seed=64), dict(variant="msdo", trunc=2)),
+    ("spd500_t8_msdo_trunc3", lambda: W.random_spd_grid(500, 8, seed=62), dict(variant="msdo", trunc=3)),
+    ("spd500_t4_trunc2_acholqr", lambda: W.random_spd_grid(500, 4, seed=63), dict(trunc=2, ortho=ecg.A_CHOLQR)),
+]
+
+
+@pytest.mark.parametrize("name,make,kw", FP32_CASES, ids=[c[0] for c in FP32_CASES])
+def test_fp32_iterations_track_the_fp64_oracle(name, make, kw):
+    """The first FP32 inner iterations of the mixed method follow the FP64
+    oracle's residual history to FP32 accuracy: the inner solve starts from
+    b / rho_0 and its history is scaled back by rho_0, so until the first
+    refinement step it is the FP64 method's history rounded in FP32.  A
+    dropped term or a wrong block in any FP32 kernel moves it by O(1)."""
+    if not torch.cuda.is_available():
+        pytest.fail("this test needs a CUDA GPU")
+    p = make()
+    A = p.scipy()
+    K = 5
+    okw = dict(variant=kw.get("variant", "sre"), trunc=kw.get("trunc", 0), ortho=kw.get("ortho", 0))
+    o = O.ecg_solve(A, p.part, p.t, p.b, tol=1e-30, maxit=K + 1, **okw)
+    assert len(o.history) >= K + 1
+    with ecg.Solver.from_problem(p, precision=ecg.MIXED, **kw) as s:
+        g = s.solve(dev(p.b), tol=1e-12, maxit=K + 2, raise_on_error=False)
+    assert g.iters == K + 1
+    d = np.abs(g.history[1 : K + 1] - o.history[1 : K + 1]) / o.history[1 : K + 1]
+    print(f"{name}: relative deviation from the FP64 history by iteration {np.array2string(d, precision=2)}")
+    # FP32 rounding (u = 6e-8) of every block and Gram entry; measured
+    # deviations are 1e-10 to 5e-8 over these five iterations
+    assert np.all(d <= 1e-6), d
