@@ -48,7 +48,13 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # classes, from one ncu capture of the kernels as they stand
 # (profiles/k_tdot_window_16_diffusion2d_1024_t16.md), n = 1,048,576, t = 16,
 # window of 2 blocks.  Any other shape reports null.
-MEASURED_TRAFFIC = {("cgs_tdot", 16, 2): 402.71e6 + 5.04e6, ("cgs_update", 16, 2): 402.86e6 + 107.35e6}
+# DRAM bytes (read + write) per launch, averaged over the two CGS passes of
+# one iteration, from one ncu capture of the current kernels (the first pass
+# of an SRE iteration reads V_{k-1} as both a window block and the block)
+MEASURED_TRAFFIC = {
+    ("cgs_tdot", 16, 2): ((268.72e6 + 3.75e6) + (402.95e6 + 4.84e6)) / 2,
+    ("cgs_update", 16, 2): ((403.09e6 + 115.24e6) + (403.00e6 + 108.42e6)) / 2,
+}
 
 
 def peaks():
@@ -378,9 +384,11 @@ def main():
         "unit": "TFLOP/s",
         "frac": achieved / FP64_PEAK_TFLOPS,
         "traffic": MEASURED_TRAFFIC.get((dom, 16, args.trunc)),
-        "traffic_note": "DRAM bytes per full-window launch from one ncu capture of the current kernel; "
-        "algorithmic bytes per launch: cgs_tdot 3 x 8 x n x 16 = 402.7 MB read + 2.5 MB of partial sums, "
-        "cgs_update 3 x 8 x n x 16 read + 8 x n x 16 written = 536.9 MB (part of the write leaves L2 after the kernel)",
+        "traffic_note": "DRAM bytes per full-window launch, mean of the two CGS passes, from one ncu capture of "
+        "the current kernel; algorithmic bytes per launch: cgs_tdot reads the two window blocks and the block, "
+        "3 x 8 x n x 16 = 402.7 MB (the first pass of an SRE iteration reads V_{k-1}, already a window block: "
+        "268.4 MB) + 2.5 MB of partial sums; cgs_update 3 x 8 x n x 16 read + 8 x n x 16 written = 536.9 MB "
+        "(part of the write leaves L2 after the kernel)",
         "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
         "launches": dom_launch,
         "share": dom_ms / tot_ms,

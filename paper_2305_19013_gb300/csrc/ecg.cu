@@ -118,12 +118,14 @@ struct ecg_ctx {
   struct Sweep {  // one substitution in level order (see PrecSweep)
     int *blk = nullptr, *lev = nullptr, *rows = nullptr, *cnt = nullptr, *col = nullptr, *map = nullptr;
     int* dep = nullptr;  // level-local mode: index of each entry's row in the previous level
+    int *cpos = nullptr, *cq = nullptr, *cblk = nullptr;  // chunks of levels (see PrecSweep)
     double *val = nullptr, *diag = nullptr;
     float *valf = nullptr, *diagf = nullptr;
     int K = 1;
   };
   int prec_nb = 0;
   int prec_local = 0, prec_maxw = 0;           // level-local mode (see PrecP)
+  int prec_qc = 0;                             // chunked level-local mode (see PrecP)
   Sweep pf, pb;                                // forward and backward sweeps
   int *d_lp = nullptr, *d_lc = nullptr;        // L by rows (factorisation)
   double *d_lv = nullptr, *d_ld = nullptr;
@@ -234,11 +236,24 @@ int set_smem_attrs_t() {
   return ECG_OK;
 }
 
+// The chunked preconditioner sweeps use up to about 104 KB of dynamic
+// shared memory; allow that for every instantiation.
+template <typename T, int W>
+int set_prec_smem_attrs() {
+  constexpr int kBytes = 160 * 1024;
+  CK(cudaFuncSetAttribute(k_prec_solve<T, W, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes));
+  CK(cudaFuncSetAttribute(k_prec_solve<T, W, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes));
+  CK(cudaFuncSetAttribute(k_prec_solve<T, W, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kBytes));
+  return ECG_OK;
+}
+
 template <int W>
 int set_smem_attrs() {
   int rc;
   if ((rc = set_smem_attrs_t<double, W>())) return rc;
   if ((rc = set_smem_attrs_t<float, W>())) return rc;
+  if ((rc = set_prec_smem_attrs<double, W>())) return rc;
+  if ((rc = set_prec_smem_attrs<float, W>())) return rc;
   CK(cudaFuncSetAttribute(k_small_e<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_small<W>()));
   CK(cudaFuncSetAttribute(k_small_a<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem_small<W>()));
@@ -305,6 +320,9 @@ PrecSweep make_sweep(const ecg_ctx::Sweep& w, bool fp32) {
   S.diag = fp32 ? (const void*)w.diagf : (const void*)w.diag;
   S.dep = w.dep;
   S.K = w.K;
+  S.cpos = w.cpos;
+  S.cq = w.cq;
+  S.cblk = w.cblk;
   return S;
 }
 
@@ -313,6 +331,7 @@ PrecP make_precp(const ecg_ctx* c, bool fp32) {
   Q.nb = c->prec_nb;
   Q.local = c->prec_local;
   Q.maxw = c->prec_maxw;
+  Q.qc = c->prec_qc;
   Q.f = make_sweep(c->pf, fp32);
   Q.b = make_sweep(c->pb, fp32);
   Q.part = c->d_ppart;
@@ -328,8 +347,11 @@ int prec_km(const ecg_ctx* c) {
 template <typename T, int W>
 void launch_prec(ecg_ctx* c, const KP& P, const PrecP& Q, int gw, const T* in, T* out, int w) {
   const dim3 grid(c->prec_nb, (std::max(W, w) + kPrecCols - 1) / kPrecCols);
-  // level-local mode: two levels of kPrecCols columns in shared memory
-  const size_t smem = Q.local ? 2 * (size_t)Q.maxw * kPrecCols * sizeof(T) : 0;
+  // level-local mode: two levels of kPrecCols columns in shared memory,
+  // and in chunked mode the chunk buffers
+  const size_t smem = Q.local ? 2 * (size_t)Q.maxw * kPrecCols * sizeof(T) +
+                                    (Q.qc > 0 ? prec_chunk_bytes(Q.qc, std::max(Q.f.K, Q.b.K), (int)sizeof(T)) : 0)
+                              : 0;
   switch (prec_km(c)) {
     case 2: k_prec_solve<T, W, 2><<<grid, kThreads, smem, c->stream>>>(P, Q, gw, in, out, w); break;
     case 4: k_prec_solve<T, W, 4><<<grid, kThreads, smem, c->stream>>>(P, Q, gw, in, out, w); break;
@@ -820,6 +842,9 @@ void free_sweep(ecg_ctx::Sweep& w) {
   dfree(w.valf);
   dfree(w.diagf);
   dfree(w.dep);
+  dfree(w.cpos);
+  dfree(w.cq);
+  dfree(w.cblk);
   w.K = 1;
 }
 
@@ -828,6 +853,7 @@ void prec_free(ecg_ctx* c) {
   c->prec_nb = 0;
   c->prec_local = 0;
   c->prec_maxw = 0;
+  c->prec_qc = 0;
   free_sweep(c->pf);
   free_sweep(c->pb);
   dfree(c->d_lp);
@@ -1006,6 +1032,43 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
     return rc;
   if (mixed && (rc = dalloc(&c->d_zf, (size_t)n))) return rc;
   if (local && ((rc = upload(&c->pf.dep, fdep)) || (rc = upload(&c->pb.dep, bdep)))) return rc;
+  // Chunked level-local mode: chunks of consecutive levels of at most qc
+  // positions, qc chosen so that the FP64 chunk buffers and the two level
+  // buffers stay near 104 KB (two CTAs per SM with the static buffers).
+  int qc = 0;
+  if (local) {
+    const int K = std::max(Kf, Kb);
+    const size_t fixed = 2 * (size_t)maxw * kPrecCols * sizeof(double);
+    const size_t budget = 104 * 1024, per = prec_chunk_bytes(1, K, (int)sizeof(double)) - sizeof(int) * (kChunkLevels + 1);
+    const size_t lev_bytes = sizeof(int) * (kChunkLevels + 1);
+    if (budget > fixed + lev_bytes) qc = (int)std::min<size_t>(4096, (budget - fixed - lev_bytes) / per);
+    if (qc < maxw) qc = 0;
+  }
+  auto chunks = [&](const std::vector<int>& blk, const std::vector<int>& lev, ecg_ctx::Sweep& w) {
+    std::vector<int> cpos, cq, cblk(nb + 1, 0);
+    for (int b = 0; b < nb; b++) {
+      cblk[b] = (int)cpos.size();
+      int l = blk[b];
+      while (l < blk[b + 1]) {
+        const int start = l;
+        int rows = 0;
+        while (l < blk[b + 1] && l - start < kChunkLevels && rows + (lev[l + 1] - lev[l]) <= qc) {
+          rows += lev[l + 1] - lev[l];
+          l++;
+        }
+        cpos.push_back(start);
+        cq.push_back(lev[start]);
+      }
+    }
+    cblk[nb] = (int)cpos.size();
+    cpos.push_back(blk[nb]);
+    cq.push_back(lev[blk[nb]]);
+    int r;
+    if ((r = upload(&w.cpos, cpos)) || (r = upload(&w.cq, cq)) || (r = upload(&w.cblk, cblk))) return r;
+    return (int)ECG_OK;
+  };
+  if (qc > 0 && ((rc = chunks(fblk, flev, c->pf)) || (rc = chunks(bblk, blev, c->pb)))) return rc;
+  c->prec_qc = qc;
   c->prec_local = local ? 1 : 0;
   c->prec_maxw = local ? maxw : 0;
   c->prec_nb = nb;

@@ -144,8 +144,8 @@ struct KP {
 //
 // Each substitution is stored in level order ("positions" q): position q
 // holds row rows[q], its cnt[q] <= K off-diagonal entries at col/val[q*K ..]
-// (ELL, padded) and the pivot diag[q] = l_ii, so a row's data needs no
-// indirection through the row index.
+// (ELL, padded) and the reciprocal pivot diag[q] = 1 / l_ii, so a row's data
+// needs no indirection through the row index and no division.
 struct PrecSweep {
   const int* blk;   // nb + 1: block b's levels are [blk[b], blk[b+1])
   const int* lev;   // level l's positions are [lev[l], lev[l+1])
@@ -157,12 +157,20 @@ struct PrecSweep {
   const int* dep;   // q * K + k: index of entry k's row inside the previous
                     // level (level-local mode), else nullptr
   int K;
+  // chunks of consecutive levels inside a block (chunked level-local
+  // mode): chunk j starts at level cpos[j] and position cq[j] and ends where
+  // chunk j + 1 starts; block b's chunks are [cblk[b], cblk[b+1])
+  const int* cpos;
+  const int* cq;
+  const int* cblk;
 };
 struct PrecP {
   int nb;
   int local;         // 1: every entry references the previous level (both
                      // sweeps), whose values the solve keeps in shared memory
   int maxw;          // rows of the widest level (level-local mode)
+  int qc;            // > 0: chunked level-local mode, at most qc positions
+                     // (and kChunkLevels levels) per chunk
   PrecSweep f;       // forward: y = L^{-1} x, entries l_ij, j < i
   PrecSweep b;       // backward: z = L^{-T} y, entries l_ji, j > i
   double* part;      // nb x W partial -V_{k-1}^T z (MSDO-CG)
@@ -229,6 +237,13 @@ struct TdotTile {
 template <typename T, int W>
 struct UpdTile {
   static constexpr int R = (sizeof(T) == 4) ? ((2048 / W) < 128 ? (2048 / W) : 128) : Tile<W>::R;
+};
+// Stages of the CGS update: two in both precisions.  FP64 is bound by its
+// FMA rate; FP32 by shared-memory reads, and with two stages four CTAs fit
+// an SM.
+template <typename T>
+struct UpdStages {
+  static constexpr int S = 2;
 };
 
 __device__ __forceinline__ void cta_rows(int n, int& r0, int& r1) {
@@ -521,7 +536,7 @@ constexpr size_t smem_update(int wcap = kChunk) {
   constexpr size_t R = UpdTile<T, W>::R;
   const size_t cc = (size_t)(wcap < kChunk ? wcap : kChunk);
   const size_t coef = (sizeof(T) * cc * W + 15) & ~(size_t)15;
-  const size_t bulk = 64 + sizeof(T) * Stages<T>::S * R * (cc + W);
+  const size_t bulk = 64 + sizeof(T) * UpdStages<T>::S * R * (cc + W);
   const size_t reg = sizeof(T) * R * cc;
   return coef + (bulk > reg ? bulk : reg);
 }
@@ -888,7 +903,7 @@ template <typename T, int W>
 __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const double* Cin) {
   constexpr int R = UpdTile<T, W>::R;
   constexpr int EPT = (R * W + kThreads - 1) / kThreads;
-  constexpr int S = Stages<T>::S;
+  constexpr int S = UpdStages<T>::S;
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   const int nq = st->nq;
@@ -936,15 +951,18 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
     const int xofs = R * wtot;
     if constexpr (sizeof(T) == 4 && W % 4 == 0) {
       // FP32: each thread owns 2 rows x 4 columns of the tile and reads, per
-      // 4 window columns, 2 + 4 16-byte vectors for 32 FMAs.  Needs every
-      // block width a multiple of 4.
+      // 4 window columns, 2 + 4 16-byte vectors for 32 FMAs.  Its rows are
+      // rp and rp + R/2, so that the eight threads of a quarter-warp read
+      // two consecutive rows (different bank groups).  Needs every block
+      // width a multiple of 4.
       bool w4 = true;
       for (int j = 0; j < nq; j++) w4 = w4 && (D[j].w % 4 == 0);
       if (w4) {
         constexpr int CG = W / 4;
         const int cg = threadIdx.x % CG, rp = threadIdx.x / CG;
-        const int b0 = cg * 4, rl0 = 2 * rp;
-        const bool active = rl0 < R;
+        constexpr int HALF = R / 2;
+        const int b0 = cg * 4, rl0 = rp;
+        const bool active = rp < HALF;
         bt.start();
         for (int i = 0; i < bt.ntiles; i++) {
           if (!bt.ready(i, (DevState*)st)) return;
@@ -954,7 +972,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
           if (active) {
 #pragma unroll
             for (int u = 0; u < 2; u++) {
-              const float4 xv = *reinterpret_cast<const float4*>(stg + xofs + (rl0 + u) * W + b0);
+              const float4 xv = *reinterpret_cast<const float4*>(stg + xofs + (rl0 + u * HALF) * W + b0);
               acc[u][0] = xv.x;
               acc[u][1] = xv.y;
               acc[u][2] = xv.z;
@@ -965,7 +983,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
               const int sd = cstr[a];
               float4 qv[2];
 #pragma unroll
-              for (int u = 0; u < 2; u++) qv[u] = *reinterpret_cast<const float4*>(qa + (rl0 + u) * sd);
+              for (int u = 0; u < 2; u++) qv[u] = *reinterpret_cast<const float4*>(qa + (rl0 + u * HALF) * sd);
 #pragma unroll
               for (int k = 0; k < 4; k++) {
                 const float4 cv = *reinterpret_cast<const float4*>(&sC[(a + k) * W + b0]);
@@ -985,8 +1003,8 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
           if (active)
 #pragma unroll
             for (int u = 0; u < 2; u++)
-              if (rl0 + u < nr)
-                *reinterpret_cast<float4*>(&Xio[(long long)(row0 + rl0 + u) * W + b0]) =
+              if (rl0 + u * HALF < nr)
+                *reinterpret_cast<float4*>(&Xio[(long long)(row0 + rl0 + u * HALF) * W + b0]) =
                     make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
         }
         return;
@@ -1984,7 +2002,7 @@ __global__ void __launch_bounds__(kThreads) k_ic0_factor(PrecSweep F, const int*
 }
 
 // Level-ordered values of one sweep from the factor: val[e] = lv[map[e]],
-// diag[q] = ld[rows[q]], in FP64 and (when vf != nullptr) FP32.
+// diag[q] = 1 / ld[rows[q]], in FP64 and (when vf != nullptr) FP32.
 __global__ void k_prec_gather(int npos, int nent, const int* map, const int* rows, const double* lv,
                               const double* ld, double* v, double* d, float* vf, float* df) {
   const int stride = gridDim.x * blockDim.x;
@@ -1994,14 +2012,14 @@ __global__ void k_prec_gather(int npos, int nent, const int* map, const int* row
     if (vf) vf[e] = (float)x;
   }
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < npos; q += stride) {
-    const double x = ld[rows[q]];
+    const double x = 1.0 / ld[rows[q]];
     d[q] = x;
     if (df) df[q] = (float)x;
   }
 }
 
 // One substitution sweep over the levels of block b for the columns
-// [c0, c0 + nc) of an n x w block: out_i = (src_i - sum_k val_k out_{col_k}) / diag
+// [c0, c0 + nc) of an n x w block: out_i = (src_i - sum_k val_k out_{col_k}) * diag
 // with src = in (forward) or out itself (backward, in place).  Rows of one
 // level are independent: each thread computes kU of them (all loads first,
 // then the stores), and a barrier closes the level.
@@ -2036,7 +2054,7 @@ __device__ void prec_sweep(const PrecSweep& S, int b, const T* in, T* out, int w
             for (int k = 0; k < cnt; k++)
               acc -= val[(long long)q * K + k] * out[(long long)S.col[(long long)q * K + k] * w + c];
           }
-          sv[u] = acc / diag[q];
+          sv[u] = acc * diag[q];
           dst[u] = (long long)i * w + c;
         }
       }
@@ -2108,7 +2126,7 @@ __device__ void prec_sweep_local(const PrecSweep& S, int b, const T* in, T* out,
 #pragma unroll
         for (int k = 0; k < KM; k++)
           if (k < cur[u].cnt) acc -= cur[u].v[k] * sprev[cur[u].d[k] * nc + c];
-        acc = acc / cur[u].diag;
+        acc = acc * cur[u].diag;
         scur[qi * nc + c] = acc;
         out[(long long)cur[u].i * w + c0 + c] = acc;
       }
@@ -2119,7 +2137,7 @@ __device__ void prec_sweep_local(const PrecSweep& S, int b, const T* in, T* out,
         const int i = S.rows[q], cnt = S.cnt[q];
         T acc = FWD ? in[(long long)i * w + c0 + c] : out[(long long)i * w + c0 + c];
         for (int k = 0; k < cnt; k++) acc -= val[(long long)q * K + k] * sprev[S.dep[(long long)q * K + k] * nc + c];
-        acc = acc / diag[q];
+        acc = acc * diag[q];
         scur[qi * nc + c] = acc;
         out[(long long)i * w + c0 + c] = acc;
       }
@@ -2134,10 +2152,128 @@ __device__ void prec_sweep_local(const PrecSweep& S, int b, const T* in, T* out,
   }
 }
 
+// Chunked level-local sweep.  Per chunk of consecutive levels (at most qc
+// positions), the CTA first copies the chunk's structure (level bounds,
+// rows, counts, reciprocal pivots, values, dependencies) into shared
+// memory, then gathers the right-hand sides of its rows; the levels of the
+// chunk then run from shared memory with one barrier each.  A chunk costs
+// two memory latencies; a level no global load.
+constexpr int kChunkLevels = 256;
+
+// Bytes of the chunk buffers for qc positions, K entries per row and T.
+__host__ __device__ constexpr size_t prec_chunk_bytes(int qc, int K, int tsize) {
+  return (size_t)qc * tsize * (1 + K + kPrecCols) + (size_t)qc * sizeof(int) * (2 + K) +
+         sizeof(int) * (kChunkLevels + 1);
+}
+
+// Asynchronous 4- or 8-byte copies global -> shared (cp.async): a thread
+// issues all of its copies before it waits, so a chunk's loads cost one
+// memory latency rather than one per loop iteration.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
+  static_assert(BYTES == 4 || BYTES == 8, "4- or 8-byte elements");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+template <typename T, int KM, bool FWD>
+__device__ void prec_sweep_chunks(const PrecSweep& S, int b, const T* in, T* out, int w, int c0, int nc, int qc,
+                                  T* sprev, T* scur, unsigned char* cbuf) {
+  const int K = S.K;
+  T* s_diag = (T*)cbuf;                          // qc
+  T* s_val = s_diag + qc;                        // qc x K
+  T* s_rhs = s_val + (size_t)qc * K;             // qc x kPrecCols
+  int* s_rows = (int*)(s_rhs + (size_t)qc * kPrecCols);  // qc
+  int* s_cnt = s_rows + qc;                      // qc
+  int* s_dep = s_cnt + qc;                       // qc x K
+  int* s_lev = s_dep + (size_t)qc * K;           // kChunkLevels + 1
+  const T* val = (const T*)S.val;
+  const T* diag = (const T*)S.diag;
+  const T* src = FWD ? in : out;  // backward: y = L^{-1} in, already in out
+  for (int j = S.cblk[b]; j < S.cblk[b + 1]; j++) {
+    const int la = S.cpos[j], lb = S.cpos[j + 1];
+    const int qa = S.cq[j], nq = S.cq[j + 1] - qa, nl = lb - la;
+    __syncthreads();  // the previous chunk's buffers are no longer read
+    // level bounds stay global positions (the level loop subtracts qa)
+    for (int i = threadIdx.x; i <= nl; i += blockDim.x) cp_async_elem<4>(&s_lev[i], &S.lev[la + i]);
+    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
+      cp_async_elem<4>(&s_rows[i], &S.rows[qa + i]);
+      cp_async_elem<4>(&s_cnt[i], &S.cnt[qa + i]);
+      cp_async_elem<sizeof(T)>(&s_diag[i], &diag[qa + i]);
+    }
+    for (int i = threadIdx.x; i < nq * K; i += blockDim.x) {
+      cp_async_elem<sizeof(T)>(&s_val[i], &val[(long long)qa * K + i]);
+      cp_async_elem<4>(&s_dep[i], &S.dep[(long long)qa * K + i]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = threadIdx.x; i < nq * nc; i += blockDim.x) {
+      const int qi = i / nc, c = i - qi * nc;
+      cp_async_elem<sizeof(T)>(&s_rhs[qi * kPrecCols + c], &src[(long long)s_rows[qi] * w + c0 + c]);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (nc == kPrecCols && K == KM) {
+      // kPrecCols columns and K entries known at compile time: each result
+      // replaces its right-hand side in s_rhs, and the chunk's results go to
+      // global memory after its last level
+      for (int l = 0; l < nl; l++) {
+        const int p0 = s_lev[l] - qa, items = (s_lev[l + 1] - s_lev[l]) * kPrecCols;
+        for (int idx = threadIdx.x; idx < items; idx += kThreads) {
+          const int qi = idx / kPrecCols, c = idx % kPrecCols, q = p0 + qi;
+          T acc = s_rhs[q * kPrecCols + c];
+          const int cn = s_cnt[q];
+#pragma unroll
+          for (int k = 0; k < KM; k++)
+            if (k < cn) acc -= s_val[q * KM + k] * sprev[s_dep[q * KM + k] * kPrecCols + c];
+          acc = acc * s_diag[q];
+          scur[qi * kPrecCols + c] = acc;
+          s_rhs[q * kPrecCols + c] = acc;
+        }
+        __syncthreads();
+        T* t = sprev;
+        sprev = scur;
+        scur = t;
+      }
+      for (int i = threadIdx.x; i < nq * kPrecCols; i += kThreads)
+        out[(long long)s_rows[i / kPrecCols] * w + c0 + i % kPrecCols] = s_rhs[i];
+      continue;
+    }
+    for (int l = 0; l < nl; l++) {
+      const int p0 = s_lev[l] - qa, items = (s_lev[l + 1] - qa - p0) * nc;
+      for (int idx = threadIdx.x; idx < items; idx += blockDim.x) {
+        const int qi = idx / nc;
+        const int c = idx - qi * nc, q = p0 + qi;
+        T acc = s_rhs[q * kPrecCols + c];
+        const int cn = s_cnt[q];
+#pragma unroll
+        for (int k = 0; k < KM; k++)
+          if (k < cn) acc -= s_val[q * K + k] * sprev[s_dep[q * K + k] * nc + c];
+        acc = acc * s_diag[q];
+        scur[qi * nc + c] = acc;
+        out[(long long)s_rows[q] * w + c0 + c] = acc;
+      }
+      __syncthreads();
+      T* t = sprev;
+      sprev = scur;
+      scur = t;
+    }
+  }
+}
+
 // out = M^{-1} in = L^{-T} (L^{-1} in) for columns [c0, c0 + nc) of an n x w
 // block; out holds y = L^{-1} in after the first sweep.
 template <typename T, int KM>
 __device__ void prec_solve_block(const PrecP& Q, int b, const T* in, T* out, int w, int c0, int nc) {
+  if (KM > 0 && Q.local && Q.qc > 0) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* s0 = (T*)smem_raw;           // Q.maxw x kPrecCols
+    T* s1 = s0 + Q.maxw * kPrecCols;  // Q.maxw x kPrecCols
+    unsigned char* cbuf = (unsigned char*)(s1 + Q.maxw * kPrecCols);
+    prec_sweep_chunks<T, (KM > 0 ? KM : 1), true>(Q.f, b, in, out, w, c0, nc, Q.qc, s0, s1, cbuf);
+    prec_sweep_chunks<T, (KM > 0 ? KM : 1), false>(Q.b, b, in, out, w, c0, nc, Q.qc, s0, s1, cbuf);
+    return;
+  }
   if (KM > 0 && Q.local) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* s0 = (T*)smem_raw;           // Q.maxw x kPrecCols
