@@ -1396,6 +1396,32 @@ struct GramBlocks {
   static constexpr int C4 = W / 4, EU = C4 * (C4 + 1) / 2, EB = EU + C4, RS = kThreads / EB;
 };
 
+// tri_row4 for two rows x and z against the same U (acc = x U, acz = z U):
+// each 16-byte row of U is read once for both.
+template <int W>
+__device__ __forceinline__ void tri_row4_pair(const float* x, const float* z, const float* U, float4 (&acc)[W / 4],
+                                              float4 (&acz)[W / 4]) {
+  constexpr int C4 = W / 4;
+#pragma unroll
+  for (int c = 0; c < C4; c++) acc[c] = acz[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < C4; m++) {
+    const float4 xa = *reinterpret_cast<const float4*>(x + 4 * m);
+    const float4 za = *reinterpret_cast<const float4*>(z + 4 * m);
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const float xl = f4c(xa, u), zl = f4c(za, u);
+      const float4* Ul = reinterpret_cast<const float4*>(U + (4 * m + u) * W);
+#pragma unroll
+      for (int c = m; c < C4; c++) {
+        const float4 uv = Ul[c];
+        f4fma(acc[c], xl, uv);
+        f4fma(acz[c], zl, uv);
+      }
+    }
+  }
+}
+
 // Shared memory (bytes) of the FP32 spmm_gram: the X and Y tiles (padded
 // rows), R_e^{-1}, and each thread's 16 FP64 running sums.
 template <int W>
@@ -1494,13 +1520,13 @@ __device__ __forceinline__ bool spmm_gram_f32(const KP& P, const float* Xin, flo
     if (PRE) {
       const int r = threadIdx.x;
       if (r < nr) {
-        float4 t4[C4];
-        tri_row4<W>(sX + r * SP, sRe, t4);
+        float4 tq[C4], tv[C4];
+        tri_row4_pair<W>(sX + r * SP, sY + r * SP, sRe, tq, tv);
 #pragma unroll
-        for (int c = 0; c < C4; c++) *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = t4[c];
-        tri_row4<W>(sY + r * SP, sRe, t4);
-#pragma unroll
-        for (int c = 0; c < C4; c++) *reinterpret_cast<float4*>(sY + r * SP + 4 * c) = t4[c];
+        for (int c = 0; c < C4; c++) {
+          *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = tq[c];
+          *reinterpret_cast<float4*>(sY + r * SP + 4 * c) = tv[c];
+        }
       }
       __syncthreads();
     }
@@ -1773,8 +1799,7 @@ __device__ __forceinline__ bool final_f32(const KP& P, const DevState* st, const
     float rn = 0.f;
     if (r < nr) {
       float4 w[C4], v[C4];
-      tri_row4<W>(tX + r * W, sRi, w);
-      tri_row4<W>(tY + r * W, sRi, v);
+      tri_row4_pair<W>(tX + r * W, tY + r * W, sRi, w, v);
       const long long o = (long long)(row0 + r) * C4;
       float dx = 0.f, dr = 0.f;
 #pragma unroll
