@@ -5,7 +5,7 @@
  *
  * The paper has no counterpart: its solves start from x_0 = 0 (Section 5).
  * The network is an addition beside the method; ecg_solve with
- * ECG_STOP_B (stop when ||r_k|| <= tol ||b||) judges its proposals, and the
+ * ECG_STOP_B (stop when ||r_k|| <= tol ||b||) measures its proposals, and the
  * plain x_0 = 0 solve is always available as the fallback.
  *
  * Conventions.  Activations are NHWC (image, row, column, channel), bf16

@@ -838,7 +838,7 @@ __global__ void k_batch_round_begin(int nsys, SysState* st, Outer* o, const doub
 }
 
 // Mixed precision, per CTA rows: rf = r / scale and xf = 0 for the systems
-// whose inner solve runs this round.
+// whose inner solve runs in this refinement step.
 __global__ void k_batch_scale(BatchP B, const Outer* o, const double* rr, float* rf, float* xf) {
   const CtaInfo ci = B.cta[blockIdx.x];
   if (!o[ci.sys].ran) return;

@@ -4,8 +4,8 @@ an enlarged CG solve from (log coefficient, right-hand side) on a 2D grid.
 The paper has no such component (its solves start from x_0 = 0); it sits
 beside the method.  A solve started from the proposal uses the stopping
 rule ||r_k|| <= tol ||b|| (ECG_STOP_B), so a good x_0 shortens it, and the
-x_0 = 0 solve under the same rule is the fallback and the judge of the
-proposal.
+x_0 = 0 solve under the same rule is both the fallback and the measure of
+the proposal.
 
 This module only orchestrates: device memory comes from PyTorch tensors,
 and every arithmetic step (convolutions, their gradients, pooling,

@@ -1,7 +1,7 @@
 """Mixed precision (FP32 inner solves, FP64 iterative refinement) against the
 FP64 oracle.
 
-The mixed method is not in the paper; its result is judged by what the paper
+The mixed method is not in the paper; its result is measured by what the paper
 asks of a solve: the FP64 true residual ||b - A x|| / ||r_0|| must meet the
 tolerance.  Two solutions x_m, x_o that both meet it differ by at most
 ||A^{-1}|| (||r_m|| + ||r_o||), so relative to x the bound is
