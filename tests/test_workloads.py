@@ -122,3 +122,34 @@ def test_manufactured_rhs():
     p = W.poisson2d(16, 4, seed=3)
     assert np.allclose(p.scipy() @ p.x_star, p.b, rtol=0, atol=1e-13)
     assert p.x_star.min() >= -1.0 and p.x_star.max() <= 1.0
+
+
+@pytest.mark.parametrize("side,t,nb", [(64, 4, 16), (1024, 16, 64)])
+def test_jacobi_blocks_are_rectangles_refining_the_subdomains(side, t, nb):
+    """Section 5's layout: nb equal rectangular blocks of the grid, each inside
+    one subdomain, each subdomain the union of nb / t blocks."""
+    p = W.poisson2d(side, t, seed=1001) if side < 1024 else W.make("diffusion2d_1024_t16")
+    pb = W.jacobi_blocks(p, nb)
+    assert pb.shape == (p.n,) and pb.dtype == np.int32
+    sizes = np.bincount(pb, minlength=nb)
+    assert len(sizes) == nb and np.all(sizes == p.n // nb)
+    cell = np.asarray(p.meta.get("perm", np.arange(p.n)))  # grid cell of each row
+    y, x = np.divmod(cell, side)
+    owners = np.empty(nb, dtype=np.int64)
+    for b in range(nb):
+        rows = pb == b
+        assert len(np.unique(p.part[rows])) == 1
+        owners[b] = p.part[rows][0]
+        h = y[rows].max() - y[rows].min() + 1
+        w = x[rows].max() - x[rows].min() + 1
+        assert h * w == sizes[b]  # a full rectangle of cells
+    assert np.all(np.bincount(owners, minlength=t) == nb // t)
+
+
+@pytest.mark.parametrize("nb", [2, 4])
+def test_jacobi_blocks_reject_a_partition_that_does_not_refine_the_subdomains(nb):
+    # the 64^2 Poisson problem has 4 row-strip subdomains; with 2 or 4 blocks
+    # some block holds rows of more than one strip
+    p = W.poisson2d(64, 4, seed=1001)
+    with pytest.raises(ValueError):
+        W.jacobi_blocks(p, nb)
