@@ -11,17 +11,24 @@ SRE-CG (SRE-CG2 truncated to a window of 2 blocks) in FP64.
 Prints one JSON line.  Under torchrun (N > 1) every rank solves its own
 replica of the system (weak scaling); the time is the maximum over ranks.
 
-value    iterations per second of the whole job, inputs resident in HBM,
-         CUDA events on the solver's stream around one ecg_solve call that
-         runs exactly K iterations (tol = 0, maxit = K + 1).
+value    iterations per second of the whole job with a full window, inputs
+         resident in HBM: CUDA events on the solver's stream around one
+         ecg_solve call of trunc + K iterations and one of trunc iterations;
+         the K steps take the difference (the first trunc iterations, whose
+         window is still filling, are not counted).
 e2e      the same metric through the C ABI with host buffers (b copied in,
-         x and the residual history copied out inside the timed call).
+         x and the residual history copied out inside the timed call of K
+         iterations, window start-up included).
 roofline the kernel class with the largest share of the iteration, from a
-         second, profiled run of K iterations (CUDA events on the solver's
-         stream around every kernel class); FP64 FMA-bound, so its peak is
-         the FP64 issue rate.
+         second, profiled run (CUDA events on the solver's stream around
+         every kernel class).
+time_to_tol  wall time to the paper's tolerance rho_k <= 1e-8 rho_0
+         (Algorithm 1) for plain FP64 SRE-CG, for FP64 with the block Jacobi
+         IC(0) preconditioner (64 blocks; Section 3, Algorithm 5) and for the
+         mixed-precision method with the same preconditioner.
 --impl reference times the FP64 CPU oracle (the reference implementation of
-this build) on a 1/16 row sample of the same workload; see cpu_baseline.
+this build) at the full size on every host core; so does cpu_baseline, on a
+bounded number of iterations.
 """
 from __future__ import annotations
 
@@ -57,16 +64,29 @@ MEASURED_TRAFFIC = {
 }
 
 
+# Roofline denominators when the driver's measured peaks are absent: the
+# profiling recipe's fallback figures for a GB300 (HBM copy, dense bf16).
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+
+
 def peaks():
+    """The measured peaks (MEASURED_PEAKS.json), else the fallback; the
+    returned dict says which in "source"."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
+            d = dict(json.load(f))
+        d["source"] = "measured (MEASURED_PEAKS.json)"
+        return d
     except Exception:
-        return {}
+        d = dict(FALLBACK_PEAKS)
+        d["source"] = "fallback (no MEASURED_PEAKS.json on this box)"
+        return d
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples (every 100 ms) of SM clock and throttle reasons,
+    stamped with host time, so that the samples of a region can be picked
+    out afterwards (summary(t0, t1))."""
 
     FIELDS = (
         "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -74,49 +94,66 @@ class ClockSampler:
         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
     )
 
-    def __init__(self, index=0):
+    def __init__(self, index=0, period_ms=100):
         self.index = index
-        self.rows = []
-        self._stop = threading.Event()
+        self.period_ms = period_ms
+        self.rows = []  # (host time, fields)
+        self._proc = None
         self._thr = None
 
-    def _run(self):
-        while not self._stop.is_set():
-            try:
-                out = subprocess.run(
-                    ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
-                    capture_output=True,
-                    text=True,
-                    timeout=5,
-                ).stdout.strip()
-                if out:
-                    self.rows.append([c.strip() for c in out.split(",")])
-            except Exception:
-                return
-            self._stop.wait(0.2)
+    def _read(self):
+        for line in self._proc.stdout:
+            line = line.strip()
+            if line:
+                self.rows.append((time.perf_counter(), [c.strip() for c in line.split(",")]))
 
     def __enter__(self):
-        self._thr = threading.Thread(target=self._run, daemon=True)
-        self._thr.start()
+        try:
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 f"-lms={self.period_ms}"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
+            self._thr = threading.Thread(target=self._read, daemon=True)
+            self._thr.start()
+            time.sleep(0.5)  # first samples before the region starts
+        except Exception:
+            self._proc = None
         return self
 
     def __exit__(self, *a):
-        self._stop.set()
+        if self._proc is not None:
+            time.sleep(0.3)
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
         if self._thr:
-            self._thr.join(timeout=10)
+            self._thr.join(timeout=5)
 
-    def summary(self):
-        if not self.rows:
+    def summary(self, t0=None, t1=None, pad=0.25):
+        """Samples taken in [t0 - pad, t1 + pad] (all samples when t0 is
+        None); at least the two nearest samples."""
+        rows = self.rows
+        if t0 is not None and rows:
+            sel = [r for r in rows if t0 - pad <= r[0] <= t1 + pad]
+            if len(sel) < 2:
+                mid = 0.5 * (t0 + t1)
+                sel = sorted(rows, key=lambda r: abs(r[0] - mid))[:2]
+            rows = sel
+        rows = [r for _, r in rows]
+        if not rows:
             return None
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 4 + i and r[4 + i] == "Active"})
         return {
             "sm_mhz": float(np.median(sm)) if sm else None,
             "sm_max_mhz": max(mx) if mx else None,
             "reasons": reasons,
-            "samples": len(self.rows),
+            "samples": len(rows),
+            "window": f"samples within {pad} s of the timed region, every {self.period_ms} ms",
         }
 
 
@@ -225,29 +262,41 @@ def warmstart_run(torch, side=64, ntrain=256, nheld=8, epochs=30):
 
 
 
-def run_oracle_sample(K, W, trunc):
-    """The FP64 CPU oracle (single thread) on a 1/16 row sample of the
-    workload: the 256 x 256 version of the same coefficient layout (16 x 16
-    tiles of log-uniform kappa, t = 16, same seed).  Its work per iteration is
-    linear in n, so iterations/s scale by 256^2 / 1024^2 to the full size."""
-    import oracle as O
+def headline_problem(seed=2001):
     from paper_2305_19013_gb300 import workloads as Wk
 
-    p = Wk.blocky_diffusion2d(256, 16, blocks=16, seed=2001)
+    return Wk.blocky_diffusion2d(1024, 16, blocks=16, seed=seed)
+
+
+def oracle_rate(p, K, W, trunc):
+    """The FP64 CPU oracle at the full size on every host core (its OpenMP
+    build; the same bits as the single-threaded one): after W untimed
+    iterations, a solve of trunc iterations and one of trunc + K iterations
+    are timed; the K steps take the difference, like the GPU's value."""
+    import oracle as O
+
     A = p.scipy()
-    if W > 0:
-        O.ecg_solve(A, p.part, 16, p.b, tol=0.0, maxit=W + 1, trunc=trunc)
-    t0 = time.perf_counter()
-    r = O.ecg_solve(A, p.part, 16, p.b, tol=0.0, maxit=K + 1, trunc=trunc)
-    dt = time.perf_counter() - t0
-    scale = p.n / 1048576.0
+    cores = O.threads(None)
+    try:
+        if W > 0:
+            O.ecg_solve(A, p.part, p.t, p.b, tol=0.0, maxit=W + 1, trunc=trunc)
+        t0 = time.perf_counter()
+        O.ecg_solve(A, p.part, p.t, p.b, tol=0.0, maxit=trunc + 1, trunc=trunc)
+        t1 = time.perf_counter()
+        r = O.ecg_solve(A, p.part, p.t, p.b, tol=0.0, maxit=trunc + K + 1, trunc=trunc)
+        t2 = time.perf_counter()
+    finally:
+        O.threads(1)
+    assert r.iters == trunc + K
+    dt = (t2 - t1) - (t1 - t0)
     return {
-        "value": (r.iters / dt) * scale,
+        "value": K / dt,
         "unit": UNIT,
-        "cores": 1,
+        "cores": cores,
         "kind": "oracle",
-        "sample": f"{r.iters} iterations of SRE-CG (trunc={trunc}) on the 256x256 version of the workload "
-        f"(n={p.n}, 1/16 of the rows), {dt:.1f} s single-threaded; iterations/s scaled by n_sample/n_full",
+        "sample": f"{K} full-window iterations of SRE-CG (trunc={trunc}, Pre-CholQR) on the full {p.n}-row system "
+        f"after {W} warm-up iterations: the oracle's OpenMP build on {cores} host threads, timed as a "
+        f"{trunc + K}-iteration solve minus a {trunc}-iteration solve ({dt:.1f} s)",
         "seconds": dt,
     }
 
@@ -255,7 +304,8 @@ def run_oracle_sample(K, W, trunc):
 def reference_arm(args, rank):
     if rank != 0:
         return
-    cb = run_oracle_sample(args.steps, args.warmup, args.trunc)
+    p = headline_problem()
+    cb = oracle_rate(p, args.steps, args.warmup, args.trunc)
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -270,11 +320,71 @@ def reference_arm(args, rank):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "method": f"SRE-CG2 trunc={args.trunc}", "sampled_rows": "1/16"},
+        "config": {"workload": WORKLOAD, "n": p.n, "nnz": p.nnz, "t": 16,
+                   "method": f"SRE-CG2 truncated to {args.trunc} blocks (SRE-CG)", "ortho": "Pre-CholQR",
+                   "parallelism": "single"},
         "cpu_baseline": {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")},
         "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def time_to_tol_runs(torch, p, stream, args, names):
+    """Solves to the paper's tolerance (rho_k <= 1e-8 rho_0, Algorithm 1),
+    device-resident b, wall time of the solve call (the preconditioner's
+    setup is timed separately)."""
+    from paper_2305_19013_gb300 import ecg
+    from paper_2305_19013_gb300 import workloads as Wk
+
+    out = {}
+    pb = None
+    specs = {"fp64": (ecg.FP64, False), "mixed": (ecg.MIXED, False),
+             f"fp64_ic0_{args.prec_blocks}": (ecg.FP64, True), f"mixed_ic0_{args.prec_blocks}": (ecg.MIXED, True)}
+    b_dev = torch.from_numpy(p.b).cuda()
+    x_dev = torch.empty_like(b_dev)
+    for name in names:
+        prec, pre = specs[name]
+        if pre and pb is None:
+            pb = Wk.jacobi_blocks(p, args.prec_blocks)
+        with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
+                                     stream=stream.cuda_stream) as sv:
+            ts = time.perf_counter()
+            if pre:  # block Jacobi IC(0) (Section 3, Algorithm 5)
+                sv.set_preconditioner(pb, args.prec_blocks)
+            torch.cuda.synchronize()
+            t_setup = time.perf_counter() - ts
+            t0 = time.perf_counter()
+            r = sv.solve(b_dev, tol=1e-8, maxit=args.time_to_tol_maxit, x_out=x_dev, raise_on_error=False)
+            torch.cuda.synchronize()
+            out[name] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status,
+                         "relres_true": r.relres_true, "device_ms": r.device_ms}
+            if pre:
+                out[name]["setup_seconds"] = t_setup
+    return out
+
+
+def full_window_ms(solver, b_dev, x_dev, K, trunc, stream, barrier, torch):
+    """CUDA-event time of K full-window iterations: a solve of trunc + K
+    iterations minus a solve of trunc iterations, each bracketed by a barrier
+    and a device synchronisation."""
+    def one(iters):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = solver.solve(b_dev, tol=0.0, maxit=iters + 1, x_out=x_dev)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        assert res.iters == iters, (res.iters, iters)
+        return e0.elapsed_time(e1)
+
+    short = one(trunc)
+    t0 = time.perf_counter()
+    long_ = one(trunc + K)
+    t1 = time.perf_counter()
+    return long_ - short, long_, short, (t0, t1)
 
 
 def main():
@@ -286,9 +396,10 @@ def main():
     ap.add_argument("--trunc", type=int, default=2)
     ap.add_argument("--ortho", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--time-to-tol", action="store_true", help="also solve to 1e-8 and report the time")
+    ap.add_argument("--no-time-to-tol", action="store_true", help="skip the solves to 1e-8")
     ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
-    ap.add_argument("--time-to-tol-only", default="", help="only the time-to-tol runs whose name contains this")
+    ap.add_argument("--time-to-tol-all", action="store_true",
+                    help="also run mixed precision without a preconditioner (it stalls on this problem)")
     ap.add_argument("--prec-blocks", type=int, default=64, help="block Jacobi blocks for the preconditioned runs")
     ap.add_argument("--warmstart", action="store_true",
                     help="also train the warm-start network on GRF diffusion problems and compare solves")
@@ -306,7 +417,6 @@ def main():
     import torch
 
     from paper_2305_19013_gb300 import ecg
-    from paper_2305_19013_gb300 import workloads as Wk
 
     torch.cuda.set_device(local)
     dist = None
@@ -316,7 +426,7 @@ def main():
         dist.init_process_group("nccl")
     K, Wm = args.steps, args.warmup
     assert Wm >= 3, "at least 3 warm-up steps"
-    p = Wk.blocky_diffusion2d(1024, 16, blocks=16, seed=2001 + rank)
+    p = headline_problem(seed=2001 + rank)
     stream = torch.cuda.current_stream()
     solver = ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, stream=stream.cuda_stream)
     b_dev = torch.from_numpy(p.b).cuda()
@@ -330,19 +440,11 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    # ---- timed region: exactly K iterations, inputs resident in HBM
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
+    # ---- timed region: K full-window iterations, inputs resident in HBM
     with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        e0.record(stream)
-        res = solver.solve(b_dev, tol=0.0, maxit=K + 1, x_out=x_dev)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms = e0.elapsed_time(e1)
-    assert res.iters == K, res.iters
+        ms, ms_long, ms_short, (tw0, tw1) = full_window_ms(solver, b_dev, x_dev, K, args.trunc, stream, barrier,
+                                                           torch)
+    assert ms > 0.0, (ms_long, ms_short)
     # kernels of one iteration: generate, 2 x (coefficients, reduce, update),
     # [Euclidean Gram, reduce, factor] for Pre-CholQR, A-Gram, reduce, factor,
     # final update, finish
@@ -353,29 +455,35 @@ def main():
     ms_max = float(t_all.item())
     value = world * K / (ms_max / 1000.0)
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- end to end through the C ABI with host buffers (K iterations)
     b_host = p.b.copy()
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    res_h = solver.solve(b_host, tol=0.0, maxit=K + 1)
+    solver.solve(b_host, tol=0.0, maxit=K + 1)
     t_e2e = time.perf_counter() - t0
     t_e = torch.tensor([t_e2e], device="cuda")
     if dist is not None:
         dist.all_reduce(t_e, op=dist.ReduceOp.MAX)
     e2e_value = world * K / float(t_e.item())
 
-    # ---- per-kernel-class profile (same K iterations, events on the stream)
+    # ---- per-kernel-class profile (same trunc + K iterations, events on the stream)
     solver.profile(True)
-    solver.solve(b_dev, tol=0.0, maxit=K + 1, x_out=x_dev)
+    solver.solve(b_dev, tol=0.0, maxit=args.trunc + K + 1, x_out=x_dev)
     prof = solver.profile_read()
     solver.profile(False)
-    fl, bytes_total = algorithmic_counts(p.n, p.nnz, 16, args.trunc, K)
+    fl, bytes_total = algorithmic_counts(p.n, p.nnz, 16, args.trunc, args.trunc + K)
     tot_ms = sum(v[0] for v in prof.values())
     dom = max((k for k in prof if k in fl), key=lambda k: prof[k][0])
     dom_ms, dom_launch = prof[dom]
     achieved = fl[dom] / (dom_ms / 1000.0) / 1e12
     pk = peaks()
+    probe = None
+    if world == 1:
+        try:
+            probe = ecg.probe_fp64()
+        except Exception:
+            probe = None
     roofline = {
         "bound": "alu",
         "kernel": dom,
@@ -390,13 +498,18 @@ def main():
         "268.4 MB) + 2.5 MB of partial sums; cgs_update 3 x 8 x n x 16 read + 8 x n x 16 written = 536.9 MB "
         "(part of the write leaves L2 after the kernel)",
         "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+        "peak_probe": probe,
+        "frac_of_probe": (achieved / probe) if probe else None,
+        "probe_note": "peak_probe: FP64 FMA rate measured in this run by ecg_probe_fp64 (8 independent chains "
+        "per thread, 8 CTAs x 256 threads per SM)",
         "launches": dom_launch,
         "share": dom_ms / tot_ms,
     }
+    prof_ms_total = tot_ms
     total_fl = sum(fl.values())
-    iter_tflops = total_fl / (ms / 1000.0) / 1e12
-    hbm = pk.get("hbm_gbs", 6686.1)
-    hbm_gbs = bytes_total / (ms / 1000.0) / 1e9
+    iter_tflops = total_fl / (prof_ms_total / 1000.0) / 1e12
+    hbm = pk["hbm_gbs"]
+    hbm_gbs = bytes_total / (prof_ms_total / 1000.0) / 1e9
 
     line = {
         "metric": METRIC,
@@ -419,9 +532,10 @@ def main():
             "method": f"SRE-CG2 truncated to {args.trunc} blocks (SRE-CG)",
             "ortho": "Pre-CholQR" if args.ortho == 0 else "A-CholQR",
             "parallelism": "replicas" if world > 1 else "single",
+            "timing": f"full window: CUDA events, ({args.trunc}+K)-iteration solve minus {args.trunc}-iteration solve",
             "l2": "no flush: the iteration streams ~3 GB of blocks, far above the 129 MB L2",
         },
-        "gpu_launches": K * launches_per_iter + 3,  # + residual, start, final residual
+        "gpu_launches": K * launches_per_iter,
         "e2e": {
             "value": e2e_value,
             "unit": UNIT,
@@ -433,42 +547,27 @@ def main():
             "fp64_tflops": iter_tflops,
             "fp64_frac": iter_tflops / FP64_PEAK_TFLOPS,
             "hbm_gbs": hbm_gbs,
-            "hbm_frac_of_measured": hbm_gbs / hbm,
+            "hbm_frac": hbm_gbs / hbm,
+            "hbm_peak": hbm,
+            "hbm_peak_source": pk["source"],
             "profile_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "note": "profiled run of trunc + K iterations (window start-up included); algorithmic bytes and flops "
+            "counted for the same iterations",
         },
-        "clocks": clk.summary(),
+        "clocks": clk.summary(tw0, tw1),
     }
     solver.close()
-    if args.time_to_tol:
-        # time to the paper's tolerance, FP64 and FP32 inner solves with FP64 refinement
-        ttt = {}
-        pb = Wk.jacobi_blocks(p, args.prec_blocks)
-        runs = [("fp64", ecg.FP64, False), ("mixed", ecg.MIXED, False),
-                (f"fp64_ic0_{args.prec_blocks}", ecg.FP64, True), (f"mixed_ic0_{args.prec_blocks}", ecg.MIXED, True)]
-        for name, prec, pre in runs:
-            if args.time_to_tol_only and args.time_to_tol_only not in name:
-                continue
-            with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
-                                         stream=stream.cuda_stream) as sv:
-                ts = time.perf_counter()
-                if pre:  # block Jacobi IC(0) (Section 3, Algorithm 5); setup timed separately
-                    sv.set_preconditioner(pb, args.prec_blocks)
-                torch.cuda.synchronize()
-                t_setup = time.perf_counter() - ts
-                t0 = time.perf_counter()
-                r = sv.solve(b_dev, tol=1e-8, maxit=args.time_to_tol_maxit, x_out=x_dev)
-                torch.cuda.synchronize()
-                ttt[name] = {"seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status,
-                             "relres_true": r.relres_true}
-                if pre:
-                    ttt[name]["setup_seconds"] = t_setup
-        line["time_to_tol"] = ttt
+    if world == 1 and not args.no_time_to_tol:
+        names = ["fp64", f"fp64_ic0_{args.prec_blocks}", f"mixed_ic0_{args.prec_blocks}"]
+        if args.time_to_tol_all:
+            names.insert(1, "mixed")
+        line["time_to_tol"] = time_to_tol_runs(torch, p, stream, args, names)
     if args.batch:
         line["batch"] = batch_run(torch)
     if args.warmstart:
         line["warmstart"] = warmstart_run(torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = run_oracle_sample(8, 1, args.trunc)
+        cb = oracle_rate(p, 8, 0, args.trunc)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -206,6 +206,15 @@ const char* ecg_strerror(int code);
 int ecg_profile_enable(ecg_ctx* ctx, int on);
 int ecg_profile_read(ecg_ctx* ctx, int cls, const char** name, double* ms, long long* launches);
 
+/* Measure this GPU's FP64 fused multiply-add rate: a kernel of 8 blocks
+ * per SM x 256 threads, each running 8 independent FMA chains of `iters`
+ * steps, timed with CUDA events after a warm-up launch, on the default
+ * stream of the current device.  *tflops receives 2 x FMAs / seconds / 1e12.
+ * The FP64 block kernels of the method are bound by this rate (not a step of
+ * the paper's methods; the paper states no hardware).  Allocates and frees
+ * a small device buffer.  Returns ECG_OK, ECG_EINVAL or ECG_ECUDA. */
+int ecg_probe_fp64(int iters, double* tflops);
+
 /* ----------------------------------------------------------------------
  * Step-level entry points.  Each runs one step of the iteration with the
  * same kernels ecg_solve uses, on the context's matrix, partition and
@@ -268,14 +277,16 @@ int ecg_op_msdo_generate(ecg_ctx* ctx, const double* r, const double* P_prev,
  * n rows (1 <= n < 2^31); 1 <= m <= 64 blocks X_j of n x wx[j] doubles,
  * 1 <= wx[j] <= 128 and sum wx <= 256; Y is n x wy with wy in
  * {1,2,4,8,16,32,64}; C is (sum wx) x wy.  X (a host array of device
- * pointers), Y and C: X_j, Y, C are device pointers.  stream is a
- * cudaStream_t (NULL: the default stream).  The call returns after C is
- * written.  Sizes beyond these limits return ECG_EINVAL.
+ * pointers), Y and C: X_j, Y, C are device pointers on the current
+ * device.  stream is a cudaStream_t (NULL: the default stream).  The call
+ * waits for the stream and returns after C is written.  Sizes beyond these
+ * limits return ECG_EINVAL.
  *
  * Memory: the partial sums (4 MiB), the launch state and the block list
  * live in static device arrays that every GPU loading this library holds
  * until the process exits.  The first call on each device looks up their
- * device addresses; make that first call before any stream capture.  All
+ * device addresses and raises the shared-memory limit of the kernels it
+ * launches; make that first call before any stream capture.  All
  * calls on a device share the arrays, so calls that overlap on the GPU
  * (from two host threads or two streams at once) race and corrupt each
  * other's results: issue them one after another. */

@@ -5,10 +5,17 @@
  *
  * TEST INFRASTRUCTURE.  This file exists to check the CUDA solver.  Only the
  * test suite, the smoke check and the CPU-baseline leg of the benchmark load
- * it.  It shares no code, header, table or helper with the CUDA path; it is
- * single-threaded, uses no BLAS, and runs every loop in its obvious order.
- * It is compiled with -ffp-contract=off so that x86 and Arm builds round
- * identically.
+ * it.  It shares no code, header, table or helper with the CUDA path; it
+ * uses no BLAS and runs every loop in its obvious order.  It is compiled
+ * with -ffp-contract=off so that x86 and Arm builds round identically.
+ *
+ * Threads.  The same source is built twice: plain (one thread) and with
+ * -fopenmp, where loops whose iterations are independent (rows of a block,
+ * diagonal blocks of the preconditioner, chunks of a sum) are shared out
+ * among threads.  Every sum over rows is taken in fixed chunks of OR_CHUNK
+ * consecutive rows: each chunk is summed over its rows in increasing order
+ * and the chunk sums are then added in chunk order.  The order does not
+ * depend on the number of threads, so both builds return the same bits.
  *
  * Conventions.  A block of w vectors of length n is a row-major n x w array
  * (entry (i, j) at [i*w + j]).  Small w x w matrices are row-major too.
@@ -51,11 +58,87 @@
 
 #define OR_BREAKDOWN_RATIO 1e-14
 
+#ifdef _OPENMP
+#include <omp.h>
+#define OR_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PAR_FOR
+#endif
+
+/* rows per chunk of every sum over rows (see "Threads" above) */
+#define OR_CHUNK 4096
+
+/* Threads of the OpenMP build (no effect in the plain build); n < 1 keeps
+ * the current setting.  Returns the number of threads in use. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------ row sums */
+
+/* out[q] = sum over rows i of chunk c that lie in [i0, n) of
+ * A[i*lda + ja] * B[i*ldb + c0 + q], q < nc, rows in increasing order. */
+static void or_chunk_dot(int64_t c, int64_t i0, int64_t n, const double* A, int64_t lda, int ja,
+                         const double* B, int64_t ldb, int c0, int nc, double* out) {
+  int64_t lo = c * OR_CHUNK, hi = lo + OR_CHUNK;
+  if (lo < i0) lo = i0;
+  if (hi > n) hi = n;
+  for (int q = 0; q < nc; q++) out[q] = 0.0;
+  for (int64_t i = lo; i < hi; i++) {
+    const double a = A[i * lda + ja];
+    for (int q = 0; q < nc; q++) out[q] += a * B[i * ldb + c0 + q];
+  }
+}
+
+/* d[q] = sum_{i0 <= i < n} A[i*lda + ja] * B[i*ldb + c0 + q] for q < nc
+ * (nc <= 64): a column of A against nc columns of B, summed chunk by chunk
+ * (OR_CHUNK rows) and the chunk sums added in chunk order. */
+static void or_col_dots(int64_t i0, int64_t n, const double* A, int64_t lda, int ja, const double* B,
+                        int64_t ldb, int c0, int nc, double* d) {
+  for (int q = 0; q < nc; q++) d[q] = 0.0;
+  if (i0 >= n) return;
+  const int64_t cf = i0 / OR_CHUNK, nch = (n + OR_CHUNK - 1) / OR_CHUNK - cf;
+  double* part = (double*)malloc(sizeof(double) * (size_t)(nch * nc));
+  if (part) {
+    OR_PAR_FOR
+    for (int64_t c = 0; c < nch; c++) or_chunk_dot(cf + c, i0, n, A, lda, ja, B, ldb, c0, nc, part + c * nc);
+    for (int64_t c = 0; c < nch; c++)
+      for (int q = 0; q < nc; q++) d[q] += part[c * nc + q];
+    free(part);
+  } else { /* same sums, one chunk at a time */
+    double tmp[nc];
+    for (int64_t c = 0; c < nch; c++) {
+      or_chunk_dot(cf + c, i0, n, A, lda, ja, B, ldb, c0, nc, tmp);
+      for (int q = 0; q < nc; q++) d[q] += tmp[q];
+    }
+  }
+}
+
+/* dst[0 .. count) = src[0 .. count) */
+static void or_copy(int64_t count, double* dst, const double* src) {
+  OR_PAR_FOR
+  for (int64_t i = 0; i < count; i++) dst[i] = src[i];
+}
+
+/* sum_i u[i] v[i] over [0, n), chunk by chunk */
+static double or_dot(int64_t n, const double* u, const double* v) {
+  double s;
+  or_col_dots(0, n, u, 1, 0, v, 1, 0, 1, &s);
+  return s;
+}
+
 /* ---------------------------------------------------------------- products */
 
 /* y = A x for A in CSR (Algorithm 1 line 1: r0 = b - A x0). */
 void or_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
              const double* x, double* y) {
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) {
     double s = 0.0;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; p++) s += val[p] * x[col[p]];
@@ -67,6 +150,7 @@ void or_spmv(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
  * and V_k = A P_k of Algorithm 2 line 9). */
 void or_spmm(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int w,
              const double* X, double* Y) {
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) {
     for (int c = 0; c < w; c++) {
       double s = 0.0;
@@ -79,6 +163,7 @@ void or_spmm(int64_t n, const int64_t* rowptr, const int32_t* col, const double*
 /* W = [T^t(r)]: column j holds r restricted to subdomain delta_j, zero
  * elsewhere (Section 1, eq. (Tt)). */
 void or_split(int64_t n, const int32_t* part, int t, const double* r, double* W) {
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) {
     for (int j = 0; j < t; j++) W[i * t + j] = 0.0;
     W[i * t + part[i]] = r[i];
@@ -89,6 +174,7 @@ void or_split(int64_t n, const int32_t* part, int t, const double* r, double* W)
  * eq. (Tt)); W is n x t/2. */
 void or_split_half(int64_t n, const int32_t* part, int t, const double* r, double* W) {
   int h = t / 2;
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) {
     for (int j = 0; j < h; j++) W[i * h + j] = 0.0;
     W[i * h + part[i] / 2] = r[i];
@@ -97,19 +183,46 @@ void or_split_half(int64_t n, const int32_t* part, int t, const double* r, doubl
 
 /* C = X^T Y (wx x wy) for n x wx X and n x wy Y: the block inner products
  * W^T r, P^T A P and (AQ)^T W of Sections 2-4. */
-void or_block_tdot(int64_t n, int wx, const double* X, int wy, const double* Y, double* C) {
-  /* Rows in the outer loop; every entry still sums its n products in row
-   * order, exactly as the plain triple loop with rows innermost would. */
-  for (int a = 0; a < wx * wy; a++) C[a] = 0.0;
-  for (int64_t i = 0; i < n; i++)
+static void or_tdot_chunk(int64_t c, int64_t n, int wx, const double* X, int wy, const double* Y, double* P) {
+  const int64_t lo = c * OR_CHUNK, hi = (lo + OR_CHUNK < n) ? lo + OR_CHUNK : n;
+  for (int a = 0; a < wx * wy; a++) P[a] = 0.0;
+  for (int64_t i = lo; i < hi; i++)
     for (int a = 0; a < wx; a++) {
       const double xa = X[i * wx + a];
-      for (int b = 0; b < wy; b++) C[a * wy + b] += xa * Y[i * wy + b];
+      for (int b = 0; b < wy; b++) P[a * wy + b] += xa * Y[i * wy + b];
     }
+}
+
+void or_block_tdot(int64_t n, int wx, const double* X, int wy, const double* Y, double* C) {
+  /* Entry (a, b) sums its products over the rows of each chunk of OR_CHUNK
+   * rows in increasing order; the chunk sums are added in chunk order. */
+  const int64_t nch = (n + OR_CHUNK - 1) / OR_CHUNK;
+  const int e = wx * wy;
+  for (int a = 0; a < e; a++) C[a] = 0.0;
+  double* part = (double*)malloc(sizeof(double) * (size_t)(nch * e));
+  if (part) {
+    OR_PAR_FOR
+    for (int64_t c = 0; c < nch; c++) or_tdot_chunk(c, n, wx, X, wy, Y, part + c * e);
+    for (int64_t c = 0; c < nch; c++)
+      for (int a = 0; a < e; a++) C[a] += part[c * e + a];
+    free(part);
+    return;
+  }
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)e); /* same sums, one chunk at a time */
+  if (!tmp) {
+    for (int a = 0; a < e; a++) C[a] = NAN;
+    return;
+  }
+  for (int64_t c = 0; c < nch; c++) {
+    or_tdot_chunk(c, n, wx, X, wy, Y, tmp);
+    for (int a = 0; a < e; a++) C[a] += tmp[a];
+  }
+  free(tmp);
 }
 
 /* W -= Q C for n x wq Q, wq x w C and n x w W (the CGS update). */
 void or_block_sub(int64_t n, int wq, const double* Q, int w, const double* C, double* W) {
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++)
     for (int b = 0; b < w; b++) {
       double s = 0.0;
@@ -120,6 +233,7 @@ void or_block_sub(int64_t n, int wq, const double* Q, int w, const double* C, do
 
 /* X <- X R^{-1} for upper-triangular R, one row at a time. */
 void or_right_trsm(int64_t n, int w, const double* R, double* X) {
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) {
     double* x = X + i * w;
     for (int j = 0; j < w; j++) {
@@ -158,57 +272,56 @@ int or_cholesky(int w, const double* G, double* R) {
  * (R_jj^2 <= 1e-14 ||w_j||^2), mirroring the Cholesky test. */
 int or_householder_qr(int64_t n, int w, const double* W, double* Q, double* R) {
   double* Wc = (double*)malloc(sizeof(double) * (size_t)(n * w));
-  double* Vh = (double*)malloc(sizeof(double) * (size_t)(n * w)); /* Householder vectors */
+  double* Vh = (double*)malloc(sizeof(double) * (size_t)(n * w)); /* Householder vectors, v_j at Vh + j n */
   double* beta = (double*)malloc(sizeof(double) * (size_t)w);
   double* cn2 = (double*)malloc(sizeof(double) * (size_t)w);
-  if (!Wc || !Vh || !beta || !cn2) {
-    free(Wc); free(Vh); free(beta); free(cn2);
+  double* d = (double*)malloc(sizeof(double) * (size_t)w);
+  if (!Wc || !Vh || !beta || !cn2 || !d) {
+    free(Wc); free(Vh); free(beta); free(cn2); free(d);
     return -1;
   }
-  memcpy(Wc, W, sizeof(double) * (size_t)(n * w));
-  for (int j = 0; j < w; j++) {
-    double s = 0.0;
-    for (int64_t i = 0; i < n; i++) s += W[i * w + j] * W[i * w + j];
-    cn2[j] = s;
-  }
+  or_copy(n * w, Wc, W);
+  for (int j = 0; j < w; j++) or_col_dots(0, n, W, w, j, W, w, j, 1, &cn2[j]);
   for (int j = 0; j < w; j++) {
     /* Householder vector for Wc[j:, j]. */
-    double nx2 = 0.0;
-    for (int64_t i = j; i < n; i++) nx2 += Wc[i * w + j] * Wc[i * w + j];
+    double nx2;
+    or_col_dots(j, n, Wc, w, j, Wc, w, j, 1, &nx2);
     double nx = sqrt(nx2);
     double x0 = Wc[(int64_t)j * w + j];
     double alpha = (x0 >= 0.0) ? -nx : nx;
-    for (int64_t i = 0; i < n; i++) Vh[i * w + j] = 0.0;
-    for (int64_t i = j; i < n; i++) Vh[i * w + j] = Wc[i * w + j];
-    Vh[(int64_t)j * w + j] -= alpha;
-    double vn2 = 0.0;
-    for (int64_t i = j; i < n; i++) vn2 += Vh[i * w + j] * Vh[i * w + j];
+    OR_PAR_FOR
+    for (int64_t i = 0; i < n; i++) Vh[j * n + i] = (i >= j) ? Wc[i * w + j] : 0.0;
+    Vh[j * n + j] -= alpha;
+    double vn2;
+    or_col_dots(j, n, Vh + j * n, 1, 0, Vh + j * n, 1, 0, 1, &vn2);
     beta[j] = (vn2 > 0.0) ? 2.0 / vn2 : 0.0;
-    /* Apply H_j = I - beta v v^T to Wc[j:, j:]. */
-    for (int c = j; c < w; c++) {
-      double d = 0.0;
-      for (int64_t i = j; i < n; i++) d += Vh[i * w + j] * Wc[i * w + c];
-      d *= beta[j];
-      for (int64_t i = j; i < n; i++) Wc[i * w + c] -= d * Vh[i * w + j];
-    }
+    /* Apply H_j = I - beta v v^T to Wc[j:, j:]: d_c = beta v^T Wc[j:, c]
+     * for every column c >= j, then Wc[j:, c] -= d_c v (each column's
+     * update reads only that column). */
+    or_col_dots(j, n, Vh + j * n, 1, 0, Wc, w, j, w - j, d);
+    for (int c = j; c < w; c++) d[c - j] *= beta[j];
+    OR_PAR_FOR
+    for (int64_t i = j; i < n; i++)
+      for (int c = j; c < w; c++) Wc[i * w + c] -= d[c - j] * Vh[j * n + i];
   }
   for (int a = 0; a < w; a++)
     for (int b = 0; b < w; b++) R[a * w + b] = (b >= a) ? Wc[(int64_t)a * w + b] : 0.0;
   /* Q = H_0 ... H_{w-1} [I; 0]. */
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++)
     for (int c = 0; c < w; c++) Q[i * w + c] = (i == c) ? 1.0 : 0.0;
   for (int j = w - 1; j >= 0; j--) {
-    for (int c = 0; c < w; c++) {
-      double d = 0.0;
-      for (int64_t i = j; i < n; i++) d += Vh[i * w + j] * Q[i * w + c];
-      d *= beta[j];
-      for (int64_t i = j; i < n; i++) Q[i * w + c] -= d * Vh[i * w + j];
-    }
+    or_col_dots(j, n, Vh + j * n, 1, 0, Q, w, 0, w, d);
+    for (int c = 0; c < w; c++) d[c] *= beta[j];
+    OR_PAR_FOR
+    for (int64_t i = j; i < n; i++)
+      for (int c = 0; c < w; c++) Q[i * w + c] -= d[c] * Vh[j * n + i];
   }
   /* Make diag(R) nonnegative. */
   for (int j = 0; j < w; j++) {
     if (R[j * w + j] < 0.0) {
       for (int b = 0; b < w; b++) R[j * w + b] = -R[j * w + b];
+      OR_PAR_FOR
       for (int64_t i = 0; i < n; i++) Q[i * w + j] = -Q[i * w + j];
     }
   }
@@ -220,7 +333,7 @@ int or_householder_qr(int64_t n, int w, const double* W, double* Q, double* R) {
       break;
     }
   }
-  free(Wc); free(Vh); free(beta); free(cn2);
+  free(Wc); free(Vh); free(beta); free(cn2); free(d);
   return status;
 }
 
@@ -276,7 +389,7 @@ int or_a_orthonormalize(int64_t n, const int64_t* rowptr, const int32_t* col, co
     int qs = or_householder_qr(n, w, W, Qe, R);
     if (qs < 0) { status = OR_ENOMEM; goto done; }
     if (qs > 0) { status = OR_EBREAKDOWN; goto done; }
-    memcpy(W, Qe, sizeof(double) * (size_t)(n * w));
+    or_copy(n * w, W, Qe);
   }
   or_spmm(n, rowptr, col, val, w, W, V);
   or_block_tdot(n, w, W, w, V, G);
@@ -429,7 +542,9 @@ int or_prec_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const do
     }
     free(fill);
   }
-  /* pattern: local columns j <= i of the lower triangle (full for kind 0) */
+  /* pattern: local columns j <= i of the lower triangle (full for kind 0);
+   * lptr[p + 1] first holds the count of row p */
+  OR_PAR_FOR
   for (int64_t p = 0; p < n; p++) {
     const int b = pc->blk[p];
     const int64_t li = p - pc->bptr[b];
@@ -448,12 +563,14 @@ int or_prec_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const do
       }
       cnt += 1; /* diagonal */
     }
-    pc->lptr[p + 1] = pc->lptr[p] + cnt;
+    pc->lptr[p + 1] = cnt;
   }
+  for (int64_t p = 0; p < n; p++) pc->lptr[p + 1] += pc->lptr[p];
   const int64_t nnz = pc->lptr[n];
   pc->lcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)nnz);
   pc->lval = (double*)malloc(sizeof(double) * (size_t)nnz);
   if (!pc->lcol || !pc->lval) { or_prec_free(pc); return OR_ENOMEM; }
+  OR_PAR_FOR
   for (int64_t p = 0; p < n; p++) {
     const int b = pc->blk[p];
     const int64_t li = p - pc->bptr[b];
@@ -481,9 +598,13 @@ int or_prec_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const do
   /* Row-by-row Cholesky on the pattern:
    *   l_ij = (a_ij - sum_{k < j} l_ik l_jk) / l_jj   for j < i in the pattern,
    *   l_ii = sqrt(a_ii - sum_{k < i} l_ik^2),
-   * the sums running over the columns k present in both rows. */
-  for (int64_t p = 0; p < n; p++) {
-    const int b = pc->blk[p];
+   * the sums running over the columns k present in both rows.  A row only
+   * reads rows of its own block, so the blocks are independent. */
+  int notspd = 0;
+  OR_PAR_FOR
+  for (int bb = 0; bb < nb; bb++)
+  for (int64_t p = pc->bptr[bb]; p < pc->bptr[bb + 1]; p++) {
+    const int b = bb;
     const int64_t i = pc->rows[p];
     const int64_t e0 = pc->lptr[p], e1 = pc->lptr[p + 1];
     for (int64_t e = e0; e < e1 - 1; e++) {
@@ -501,9 +622,17 @@ int or_prec_setup(int64_t n, const int64_t* rowptr, const int32_t* col, const do
     }
     double d = or_a_entry(rowptr, col, val, i, i);
     for (int64_t e = e0; e < e1 - 1; e++) d -= pc->lval[e] * pc->lval[e];
-    if (!(d > 0.0)) { or_prec_free(pc); return OR_ENOTSPD; }
+    if (!(d > 0.0)) {
+      /* a failed pivot ends this block; the factor is discarded below */
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+      notspd = 1;
+      break;
+    }
     pc->lval[e1 - 1] = sqrt(d);
   }
+  if (notspd) { or_prec_free(pc); return OR_ENOTSPD; }
   *out = pc;
   return OR_OK;
 }
@@ -522,10 +651,12 @@ void or_prec_export(const or_prec* pc, int64_t* I, int64_t* J, double* V) {
   }
 }
 
-/* X <- L^{-1} X for an n x w block (forward substitution in each block). */
+/* X <- L^{-1} X for an n x w block (forward substitution in each block;
+ * the blocks are independent). */
 void or_prec_lsolve(const or_prec* pc, int w, double* X) {
-  for (int64_t p = 0; p < pc->n; p++) {
-    const int b = pc->blk[p];
+  OR_PAR_FOR
+  for (int b = 0; b < pc->nb; b++)
+  for (int64_t p = pc->bptr[b]; p < pc->bptr[b + 1]; p++) {
     const int64_t i = pc->rows[p];
     const int64_t e1 = pc->lptr[p + 1];
     for (int c = 0; c < w; c++) {
@@ -540,8 +671,9 @@ void or_prec_lsolve(const or_prec* pc, int w, double* X) {
 /* X <- L^{-T} X for an n x w block (backward substitution in each block,
  * by columns of L: solve for the last unknown, then remove it). */
 void or_prec_ltsolve(const or_prec* pc, int w, double* X) {
-  for (int64_t p = pc->n - 1; p >= 0; p--) {
-    const int b = pc->blk[p];
+  OR_PAR_FOR
+  for (int b = 0; b < pc->nb; b++)
+  for (int64_t p = pc->bptr[b + 1] - 1; p >= pc->bptr[b]; p--) {
     const int64_t i = pc->rows[p];
     const int64_t e1 = pc->lptr[p + 1];
     for (int c = 0; c < w; c++) {
@@ -570,10 +702,21 @@ static void or_prec_split(const or_prec* pc, int64_t n, const int32_t* part, int
   or_prec_ltsolve(pc, half ? t / 2 : t, W);
 }
 
-static double or_norm2(int64_t n, const double* v) {
-  double s = 0.0;
-  for (int64_t i = 0; i < n; i++) s += v[i] * v[i];
-  return sqrt(s);
+static double or_norm2(int64_t n, const double* v) { return sqrt(or_dot(n, v, v)); }
+
+/* The MSDO-CG direction of Algorithm 2 (lines 6-7): on entry P holds the
+ * split [T(r_{k-1})] (n x w); on return beta = -V_{k-1}^T z (w entries) and
+ * P = [T(r_{k-1})] + P_{k-1} diag(beta).  z is r_{k-1}, or M^{-1} r_{k-1} in
+ * the preconditioned form of Algorithm 5.  Reading: eq. (pk) prints
+ * P_{k-1}^t A r where Algorithm 2 writes V_{k-1}^T r; with V_{k-1} = A P_{k-1}
+ * both are the same vector, computed here from the stored V_{k-1}. */
+void or_msdo_direction(int64_t n, int w, const double* Pprev, const double* Vprev, const double* z,
+                       double* beta, double* P) {
+  or_block_tdot(n, w, Vprev, 1, z, beta);
+  for (int j = 0; j < w; j++) beta[j] = -beta[j];
+  OR_PAR_FOR
+  for (int64_t i = 0; i < n; i++)
+    for (int j = 0; j < w; j++) P[i * w + j] += Pprev[i * w + j] * beta[j];
 }
 
 /* Enlarged CG.  variant 0: SRE-CG2 (Algorithm 1; W_k = A W_{k-1}); 1: MSDO-CG
@@ -659,6 +802,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
   if (x0) memcpy(x, x0, sizeof(double) * (size_t)n);
   else memset(x, 0, sizeof(double) * (size_t)n);
   or_spmv(n, rowptr, col, val, x, tmp);
+  OR_PAR_FOR
   for (int64_t i = 0; i < n; i++) r[i] = b[i] - tmp[i];
   rho0 = or_norm2(n, r);
   double rho_prev = rho0;
@@ -709,7 +853,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
     } else {
       width = wprev;
       if (variant == 0) {
-        memcpy(W, Vprev, sizeof(double) * (size_t)(n * width)); /* W_k = A W_{k-1} */
+        or_copy(n * width, W, Vprev); /* W_k = A W_{k-1} */
         if (pc) or_prec_apply(pc, width, W);                     /* M^{-1} A W_{k-1} */
       } else {
         if (pc) or_prec_split(pc, n, part, t, width != t, r, tmp, W);
@@ -720,10 +864,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
            * preconditioned); P_k = T(r_{k-1}) + P_{k-1} diag(beta_k). */
           memcpy(z, r, sizeof(double) * (size_t)n);
           if (pc) or_prec_apply(pc, 1, z);
-          or_block_tdot(n, width, Vprev, 1, z, beta);
-          for (int j = 0; j < width; j++) beta[j] = -beta[j];
-          for (int64_t i = 0; i < n; i++)
-            for (int j = 0; j < width; j++) W[i * width + j] += Pprev[i * width + j] * beta[j];
+          or_msdo_direction(n, width, Pprev, Vprev, z, beta, W);
         }
       }
     }
@@ -761,18 +902,19 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
         Vb[slot] = (double*)malloc(sizeof(double) * (size_t)(n * t));
         if (!Qb[slot] || !Vb[slot]) { status = OR_ENOMEM; goto out; }
       }
-      memcpy(Qb[slot], W, sizeof(double) * (size_t)(n * width));
-      memcpy(Vb[slot], Vn, sizeof(double) * (size_t)(n * width));
+      or_copy(n * width, Qb[slot], W);
+      or_copy(n * width, Vb[slot], Vn);
       wq[slot] = width;
     }
     if (basis && basis_used + n * width <= basis_cap) {
-      memcpy(basis + basis_used, W, sizeof(double) * (size_t)(n * width));
+      or_copy(n * width, basis + basis_used, W);
       basis_used += n * width;
     }
     if (widths) widths[k - 1] = width;
 
     /* ---- alpha_k = W_k^T r_{k-1}; x_k, r_k, rho_k (lines 12-15) ---- */
     or_block_tdot(n, width, W, 1, r, alpha);
+    OR_PAR_FOR
     for (int64_t i = 0; i < n; i++) {
       double sx = 0.0, sr = 0.0;
       for (int j = 0; j < width; j++) {
@@ -788,8 +930,8 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
     rho_prev = rho;
     if (history) history[k] = rho;
     if (xhist) memcpy(xhist + (int64_t)(k - 1) * n, x, sizeof(double) * (size_t)n);
-    memcpy(Pprev, W, sizeof(double) * (size_t)(n * width));
-    memcpy(Vprev, Vn, sizeof(double) * (size_t)(n * width));
+    or_copy(n * width, Pprev, W);
+    or_copy(n * width, Vprev, Vn);
     wprev = width;
     k++;
   }
@@ -803,6 +945,7 @@ out:
     double rr = or_norm2(n, r);
     res->relres = (rho0 > 0.0) ? rr / rho0 : rr;
     or_spmv(n, rowptr, col, val, x, tmp);
+    OR_PAR_FOR
     for (int64_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
     double nb = or_norm2(n, b);
     res->relres_true = (nb > 0.0) ? or_norm2(n, tmp) / nb : or_norm2(n, tmp);
@@ -869,8 +1012,8 @@ int or_becg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const do
   if (history) history[0] = rho0;
   or_split(n, part, t, tmp, R); /* R_0 = [T^t(r_0)] */
   while (rho_prev > eps * rho0 && k < kmax) {
-    if (k == 1) memcpy(W, R, sizeof(double) * (size_t)(n * t)); /* W_1 = R_0 */
-    else memcpy(W, Vprev, sizeof(double) * (size_t)(n * t));    /* W_k = A W_{k-1} */
+    if (k == 1) or_copy(n * t, W, R); /* W_1 = R_0 */
+    else or_copy(n * t, W, Vprev);    /* W_k = A W_{k-1} */
     if (k > 1 && nq > 0) {
       for (int j = 0; j < nq; j++) {
         const int slot = (head + j) % cap;
@@ -894,8 +1037,8 @@ int or_becg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const do
         Vb[slot] = (double*)malloc(sizeof(double) * (size_t)(n * t));
         if (!Qb[slot] || !Vb[slot]) { status = OR_ENOMEM; goto out; }
       }
-      memcpy(Qb[slot], W, sizeof(double) * (size_t)(n * t));
-      memcpy(Vb[slot], Vn, sizeof(double) * (size_t)(n * t));
+      or_copy(n * t, Qb[slot], W);
+      or_copy(n * t, Vb[slot], Vn);
     }
     /* alpha_k = W_k^T R_{k-1}; X += W alpha; R -= V alpha */
     or_block_tdot(n, t, W, t, R, alpha);
@@ -922,7 +1065,7 @@ int or_becg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const do
     rho_prev = rho;
     if (history) history[k] = rho;
     if (xhist) memcpy(xhist + (int64_t)(k - 1) * n, x, sizeof(double) * (size_t)n);
-    memcpy(Vprev, Vn, sizeof(double) * (size_t)(n * t));
+    or_copy(n * t, Vprev, Vn);
     k++;
   }
   if (status == OR_ENOCONV && rho_prev <= eps * rho0) status = OR_OK;
@@ -936,7 +1079,7 @@ out:
     for (int64_t i = 0; i < n; i++) tmp[i] = b[i] - tmp[i];
     const double nb = or_norm2(n, b);
     res->relres_true = (nb > 0.0) ? or_norm2(n, tmp) / nb : or_norm2(n, tmp);
-    if (Xout) memcpy(Xout, X, sizeof(double) * (size_t)(n * t));
+    if (Xout) or_copy(n * t, Xout, X);
   }
   if (Qb) for (int j = 0; j < cap; j++) free(Qb[j]);
   if (Vb) for (int j = 0; j < cap; j++) free(Vb[j]);
@@ -960,19 +1103,16 @@ int or_cg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const doub
   else memset(x, 0, sizeof(double) * (size_t)n);
   or_spmv(n, rowptr, col, val, x, q);
   for (int64_t i = 0; i < n; i++) { r[i] = b[i] - q[i]; p[i] = r[i]; }
-  double rr = 0.0;
-  for (int64_t i = 0; i < n; i++) rr += r[i] * r[i];
+  double rr = or_dot(n, r, r);
   double rho0 = sqrt(rr), rho = rho0;
   if (history) history[0] = rho0;
   int k = 1;
   while (rho > eps * rho0 && k < kmax) {
     or_spmv(n, rowptr, col, val, p, q);
-    double pq = 0.0;
-    for (int64_t i = 0; i < n; i++) pq += p[i] * q[i];
+    double pq = or_dot(n, p, q);
     double a = rr / pq;
     for (int64_t i = 0; i < n; i++) { x[i] += a * p[i]; r[i] -= a * q[i]; }
-    double rr_new = 0.0;
-    for (int64_t i = 0; i < n; i++) rr_new += r[i] * r[i];
+    double rr_new = or_dot(n, r, r);
     double bcoef = rr_new / rr;
     for (int64_t i = 0; i < n; i++) p[i] = r[i] + bcoef * p[i];
     rr = rr_new;

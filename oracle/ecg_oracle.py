@@ -10,6 +10,8 @@ Conjugate Gradient methods", arXiv 2305.19013):
 - ``split``/``split_half``: [T^t(r)] and [T^{t/2}(r)] (eq. (Tt), Section 4).
 - ``block_tdot``/``block_sub``: X^T Y and W - Q C (block inner products and
   the CGS update, Sections 2-3).
+- ``msdo_direction``: the MSDO-CG block [T(r)] + P_{k-1} diag(beta) with
+  beta = -V_{k-1}^T r (Algorithm 2).
 - ``cholesky``/``householder_qr``/``a_orthonormalize``/``cgs2``: the
   A-orthonormalisation (Section 2.1, Section 5).
 - ``ecg_solve``: SRE-CG2, MSDO-CG, modified MSDO-CG, truncated and flexible
@@ -40,21 +42,57 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ecg_oracle.c")
 _LIB = os.path.join(_HERE, "libecg_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libecg_oracle_omp.so")  # same source, -fopenmp
 
 OK, ENOCONV, EINVAL, ENOMEM, EBREAKDOWN, ENOTSPD = 0, 1, -1, -2, -4, -5
 
-_lib = None
+_libs = {}          # path -> loaded CDLL
+_use_omp = False    # route calls to the OpenMP build (see threads())
+
+
+def _compile(out, extra):
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call(
+        ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"]
+    )
+    os.replace(tmp, out)
+
+
+def _stale(lib):
+    return not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
-        )
-        os.replace(tmp, _LIB)
+    """Compile the oracle with gcc (plain C99, no FMA contraction): the
+    single-threaded library and, when the compiler offers OpenMP, the same
+    source with -fopenmp.  Both sum every reduction over rows in the same
+    fixed chunks, so they return the same bits."""
+    if force or _stale(_LIB):
+        _compile(_LIB, [])
+    if force or _stale(_LIB_OMP):
+        try:
+            _compile(_LIB_OMP, ["-fopenmp"])
+        except (subprocess.CalledProcessError, OSError):
+            pass  # no OpenMP: threads() stays at one thread
     return _LIB
+
+
+def have_threads() -> bool:
+    """True when the OpenMP build of the oracle exists."""
+    build()
+    return os.path.exists(_LIB_OMP)
+
+
+def threads(n: int | None = None) -> int:
+    """Route oracle calls to the OpenMP build with n threads (n > 1; None:
+    every core) or back to the single-threaded build (n == 1).  Returns the
+    number of threads now in use.  The results do not change."""
+    global _use_omp
+    if n == 1 or not have_threads():
+        _use_omp = False
+        return 1
+    _use_omp = True
+    return int(_load().or_set_threads(int(n) if n else os.cpu_count() or 1))
 
 
 class _Res(C.Structure):
@@ -80,11 +118,14 @@ _D = C.c_double
 
 
 def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = C.CDLL(build())
+    path = _LIB_OMP if _use_omp else _LIB
+    lib = _libs.get(path)
+    if lib is not None:
+        return lib
+    build()
+    lib = C.CDLL(path)
     sigs = {
+        "or_set_threads": (_INT, [_INT]),
         "or_spmv": (None, [_I64, _P, _P, _P, _P, _P]),
         "or_spmm": (None, [_I64, _P, _P, _P, _INT, _P, _P]),
         "or_split": (None, [_I64, _P, _INT, _P, _P]),
@@ -112,12 +153,13 @@ def _load():
         "or_cg_solve": (_INT, [_I64, _P, _P, _P, _P, _P, _D, _INT, _P, _P, _P, _P]),
         "or_becg_solve": (_INT, [_I64, _P, _P, _P, _P, _INT, _INT, _INT, _P, _P, _D, _INT, _P, _P, _P, _P, _P]),
         "or_mem_flexible": (_I64, [_INT, _INT, _INT]),
+        "or_msdo_direction": (None, [_I64, _INT, _P, _P, _P, _P, _P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
+    _libs[path] = lib
     return lib
 
 
@@ -188,6 +230,21 @@ def block_sub(Q, Cm, W):
     Q, Cm, W = _f64(Q), _f64(Cm), _f64(W).copy()
     _load().or_block_sub(W.shape[0], Q.shape[1], _p(Q), W.shape[1], _p(Cm), _p(W))
     return W
+
+
+def msdo_direction(part, t, r, P_prev, V_prev, z=None):
+    """MSDO-CG direction (Algorithm 2 lines 6-7): returns (P, beta) with
+    beta = -V_prev^T z (z = r unless given, e.g. M^{-1} r) and
+    P = [T(r)] + P_prev diag(beta); T = T^t when P_prev has t columns,
+    T^{t/2} when it has t/2.  The solver builds its MSDO blocks with the same
+    C function."""
+    P_prev, V_prev, r = _f64(P_prev), _f64(V_prev), _f64(r)
+    z = r if z is None else _f64(z)
+    n, w = P_prev.shape
+    P = split(part, t, r) if w == t else split_half(part, t, r)
+    beta = np.empty(w)
+    _load().or_msdo_direction(n, w, _p(P_prev), _p(V_prev), _p(z), _p(beta), _p(P))
+    return P, beta
 
 
 def right_trsm(R, X):

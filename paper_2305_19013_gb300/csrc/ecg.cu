@@ -1522,6 +1522,54 @@ int ecg_profile_read(ecg_ctx* c, int cls, const char** name, double* ms, long lo
   return kProfClasses;
 }
 
+// ------------------------------------------------------ FP64 rate probe
+
+namespace {
+// Each thread runs kProbeChains independent FP64 FMA chains; the result is
+// written out so that no chain can be removed.
+constexpr int kProbeChains = 8;
+__global__ void __launch_bounds__(256) k_probe_dfma(int iters, double a, double b, double* sink) {
+  double v[kProbeChains];
+#pragma unroll
+  for (int c = 0; c < kProbeChains; c++) v[c] = (double)(threadIdx.x + c) * 1e-3;
+  for (int i = 0; i < iters; i++) {
+#pragma unroll
+    for (int c = 0; c < kProbeChains; c++) v[c] = fma(v[c], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kProbeChains; c++) s += v[c];
+  if (s == 1234.5678) sink[blockIdx.x] = s;  // practically never taken
+}
+}  // namespace
+
+int ecg_probe_fp64(int iters, double* tflops) {
+  if (iters < 1 || !tflops) return ECG_EINVAL;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  CK(cudaMalloc(&sink, sizeof(double) * 8 * sms));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = ECG_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = ECG_ECUDA;
+  const int blocks = 8 * sms;
+  float ms = 0.f;
+  if (rc == ECG_OK) {
+    k_probe_dfma<<<blocks, 256>>>(iters / 8 + 1, 0.999999, 1e-7, sink);  // warm-up
+    cudaEventRecord(e0);
+    k_probe_dfma<<<blocks, 256>>>(iters, 0.999999, 1e-7, sink);
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || ms <= 0.f)
+      rc = ECG_ECUDA;
+  }
+  if (rc == ECG_OK) *tflops = 2.0 * kProbeChains * (double)iters * blocks * 256 / (ms * 1e-3) / 1e12;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(sink);
+  return rc;
+}
+
 // ------------------------------------------------------ step-level calls
 
 int ecg_op_split(ecg_ctx* c, const double* r, double* W, int half) {
@@ -1735,8 +1783,16 @@ constexpr int kNoAllocMaxDevices = 64;
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
 std::mutex g_noalloc_mutex;
 
+template <int WB>
+cudaError_t noalloc_smem_attr() {
+  return cudaFuncSetAttribute((const void*)k_tdot_window<double, WB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)smem_tdot<double, WB>());
+}
+
 // Device addresses of the arrays above for the current device, looked up on
-// the first call made on that device.
+// the first call made on that device, which also raises the dynamic shared
+// memory limit of the kernels it launches (some need more than the 48 KiB
+// default; a context does the same in ecg_create, but this call needs none).
 int noalloc_setup(NoAllocDevice** out) {
   int dev = -1;
   CK(cudaGetDevice(&dev));
@@ -1748,6 +1804,13 @@ int noalloc_setup(NoAllocDevice** out) {
     CK(cudaGetSymbolAddress((void**)&d.st, g_noalloc_state));
     CK(cudaGetSymbolAddress((void**)&d.desc, g_noalloc_desc));
     CK(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(noalloc_smem_attr<1>());
+    CK(noalloc_smem_attr<2>());
+    CK(noalloc_smem_attr<4>());
+    CK(noalloc_smem_attr<8>());
+    CK(noalloc_smem_attr<16>());
+    CK(noalloc_smem_attr<32>());
+    CK(noalloc_smem_attr<64>());
     d.ready = true;
   }
   *out = &d;

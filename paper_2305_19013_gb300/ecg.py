@@ -100,6 +100,7 @@ SIGNATURES = {
     "ecg_solve": (_I, [_P, _P, _P, _P, _D, _I, C.POINTER(_Result)]),
     "ecg_destroy": (None, [_P]),
     "ecg_strerror": (C.c_char_p, [_I]),
+    "ecg_probe_fp64": (_I, [_I, C.POINTER(C.c_double)]),
     "ecg_profile_enable": (_I, [_P, _I]),
     "ecg_profile_read": (_I, [_P, _I, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "ecg_op_split": (_I, [_P, _P, _P, _I]),
@@ -581,24 +582,48 @@ class BatchSolver:
 def tdot_noalloc(Xs, Y, out=None, stream=None):
     """[X_0 .. X_{m-1}]^T Y through ecg_tdot_noalloc, which allocates no
     device memory of its own (its scratch is a static array inside the
-    library).  Xs: float64 CUDA tensors n x w_j; Y: n x wy (or n); out:
-    a preallocated (sum w_j) x wy tensor, or None to let torch allocate the
-    result here in Python.  stream: a cudaStream_t handle or None.
+    library).  Xs: a non-empty list of float64 CUDA tensors n x w_j; Y:
+    n x wy (or n); all on one device, on which the call runs.  out: a
+    preallocated contiguous float64 (sum w_j) x wy tensor on that device, or
+    None to let torch allocate the result here in Python.  stream: a
+    cudaStream_t handle, or None for torch's current stream on that device.
     Returns (status, out)."""
     import torch
 
     lib = load()
+    if len(Xs) == 0:
+        raise ValueError("tdot_noalloc needs at least one block X_j")
     if Y.dim() == 1:
         Y = Y.reshape(-1, 1)
     n, wy = int(Y.shape[0]), int(Y.shape[1])
     _check_tensor(Y, (n, wy), "Y")
     for X in Xs:
         _check_tensor(X, (n, X.shape[1]), "X")
+        if X.device != Y.device:
+            raise ValueError("every X_j must be on Y's device")
     m = len(Xs)
-    ptrs = (C.c_void_p * max(m, 1))(*[X.data_ptr() for X in Xs])
-    ws = (C.c_int * max(m, 1))(*[int(X.shape[1]) for X in Xs])
+    ptrs = (C.c_void_p * m)(*[X.data_ptr() for X in Xs])
+    ws = (C.c_int * m)(*[int(X.shape[1]) for X in Xs])
     tot = sum(int(X.shape[1]) for X in Xs)
     if out is None:
-        out = torch.empty((max(tot, 1), wy), dtype=torch.float64, device=Y.device)
-    rc = lib.ecg_tdot_noalloc(n, m, C.cast(ptrs, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(Y), wy, _ptr(out), stream)
+        out = torch.empty((tot, wy), dtype=torch.float64, device=Y.device)
+    _check_tensor(out, (tot, wy), "out")
+    if out.device != Y.device:
+        raise ValueError("out must be on Y's device")
+    with torch.cuda.device(Y.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(Y.device).cuda_stream
+        rc = lib.ecg_tdot_noalloc(n, m, C.cast(ptrs, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(Y), wy, _ptr(out),
+                                  stream)
     return rc, out
+
+
+def probe_fp64(iters: int = 20000) -> float:
+    """This GPU's FP64 FMA rate in TFLOP/s (ecg_probe_fp64), the bound of the
+    FP64 block kernels that run on CUDA cores."""
+    lib = load()
+    out = C.c_double(0.0)
+    rc = lib.ecg_probe_fp64(int(iters), C.byref(out))
+    if rc != OK:
+        raise EcgError(rc, "ecg_probe_fp64")
+    return float(out.value)

@@ -258,6 +258,35 @@ def test_switch_block_lies_in_section41_space():
     assert rel(r.xhist[1], BF.to_np(x2)) < 1e-10
 
 
+@pytest.mark.parametrize("half", [False, True])
+def test_msdo_direction_beta_against_exact_sums(half):
+    """Algorithm 2 lines 6-7: beta = -V_{k-1}^T r and P = [T(r)] + P_{k-1}
+    diag(beta).  beta is pinned against correctly rounded sums (math.fsum
+    over the rows) and P entry by entry, for the t and the t/2 split; a
+    dropped sign or a transposed V would fail."""
+    import math
+
+    t = 8
+    rng = np.random.default_rng(31)
+    n = 9000  # three chunks of the oracle's row sums, the last one ragged
+    part = np.sort(rng.integers(0, t, n)).astype(np.int32)
+    w = t // 2 if half else t
+    Pp = rng.standard_normal((n, w))
+    Vp = rng.standard_normal((n, w))
+    r = rng.standard_normal(n)
+    P, beta = O.msdo_direction(part, t, r, Pp, Vp)
+    exact = np.array([-math.fsum(Vp[:, j] * r) for j in range(w)])
+    assert np.max(np.abs(beta - exact)) <= 1e-14 * np.sum(np.abs(Vp) * np.abs(r)[:, None], axis=0).max()
+    T = np.zeros((n, w))
+    T[np.arange(n), part // 2 if half else part] = r
+    assert np.array_equal(P, T + Pp * beta[None, :])
+    # the preconditioned form takes beta from z = M^{-1} r instead of r
+    z = rng.standard_normal(n)
+    P2, beta2 = O.msdo_direction(part, t, r, Pp, Vp, z=z)
+    assert np.allclose(beta2, -(Vp.T @ z), rtol=1e-13, atol=0)
+    assert np.array_equal(P2, T + Pp * beta2[None, :])
+
+
 @pytest.mark.parametrize("variant", ["modmsdo", "msdo"])
 def test_msdo_variants_match_brute_force_galerkin(variant):
     """Modified MSDO-CG searches span{T^t(r_0), ..., T^t(r_{k-1})} (Section
