@@ -113,6 +113,12 @@ typedef struct {
                            x_k = x_0 + X_k 1 and rho_k = ||R_k 1||.  SRE-CG2
                            directions, FP64, no switch, restart or
                            preconditioner (ECG_EINVAL otherwise) */
+  int tensor_cores;     /* 1 (default): the FP64 CGS update W -= Q C runs on
+                           the tensor cores (exact digit products, FP64
+                           result) when the block width is 16 and the window
+                           has at most 32 columns; 0: always on CUDA-core FP64
+                           FMAs.  Not a choice of the paper: both compute the
+                           same FP64 product up to rounding */
   void* stream;      /* cudaStream_t for all work; NULL: a stream the
                         context creates */
 } ecg_opts;
@@ -241,6 +247,13 @@ int ecg_op_prec_apply(ecg_ctx* ctx, const double* in, double* out, int w);
  * (sum wx) x wy.  1 <= m <= 1024. */
 int ecg_op_tdot(ecg_ctx* ctx, int m, const double* const* X, const int* wx, const double* Y,
                 int wy, double* C);
+
+/* W -= [Q_0 ... Q_{m-1}] C: the CGS update of Sections 2.1 and 3 (each of
+ * the two passes of CGS2 ends with it), for the n x w block W (updated in
+ * place), m blocks Q_j of n x wq[j] (1 <= wq[j] <= 128, 1 <= m <= 1024)
+ * and the (sum wq) x w row-major coefficients C (device memory).  With
+ * tensor_cores on, w = 16 and sum wq <= 32 it runs the tensor-core form. */
+int ecg_op_block_sub(ecg_ctx* ctx, int m, const double* const* Q, const int* wq, const double* C, double* W, int w);
 
 /* Two passes of block classical Gram-Schmidt in the A-inner product of the
  * n x w block W against m A-orthonormal blocks Q_j (n x wq[j]) with

@@ -34,6 +34,7 @@
 
 #include "ecg.h"
 #include "ecg_kernels.cuh"
+#include "ecg_tc.cuh"
 
 using namespace ecg;
 
@@ -264,6 +265,10 @@ int set_smem_attrs() {
 
 int set_all_smem_attrs() {
   int rc = ECG_OK;
+  CK(cudaFuncSetAttribute(tc::k_update_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc::smem_update_tc<16>()));
+  CK(cudaFuncSetAttribute(tc::k_tdot_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc::smem_tdot_tc<16>()));
   if ((rc = set_smem_attrs<1>())) return rc;
   if ((rc = set_smem_attrs<2>())) return rc;
   if ((rc = set_smem_attrs<4>())) return rc;
@@ -495,6 +500,45 @@ void set_f32_grids(ecg_ctx* c) {
   set_f32_grid<16>(c, width_index(16));
 }
 
+// Grid of the tensor-core kernels: two CTAs per SM, at most one per
+// 128-row tile.
+int tc_grid(const ecg_ctx* c) {
+  return (int)std::max<long long>(1, std::min<long long>(2LL * c->num_sms, ((long long)c->n + 127) / 128));
+}
+
+// The CGS update X -= Q C (C in d_C or Cin): the tensor-core form where it
+// applies (FP64, W = 16, at most 32 window columns, tensor_cores on), else
+// the CUDA-core kernel.  The tensor-core form runs two CTAs per SM (each
+// holds 256 of the SM's 512 TMEM columns).
+template <typename T, int W>
+void launch_update(ecg_ctx* c, const KP& P, T* X, const double* Cin, int wcap, int gup) {
+  if constexpr (tc::update_tc_ok<T, W>(32)) {
+    if (c->opts.tensor_cores && tc::update_tc_ok<T, W>(wcap)) {
+      tc::k_update_tc<W><<<tc_grid(c), 256, tc::smem_update_tc<W>(), c->stream>>>(P, W, (double*)X, Cin);
+      return;
+    }
+  }
+  k_update<T, W><<<gup, kThreads, smem_update<T, W>(wcap), c->stream>>>(P, W, X, Cin);
+}
+
+// C = V^T B over the window (CGS coefficients) into Cout: the tensor-core
+// form where it applies (FP64, W = 16, at most 32 window columns,
+// tensor_cores on), else the CUDA-core kernel; then the fixed-order
+// reduction of the per-CTA partials.
+template <typename T, int W>
+void launch_tdot(ecg_ctx* c, const KP& P, const T* B, double* Cout, int wcap, int gy, int gxw) {
+  if constexpr (tc::tdot_tc_ok<T, W>(32)) {
+    if (c->opts.tensor_cores && tc::tdot_tc_ok<T, W>(wcap) && gy == 1) {
+      const int g = tc_grid(c);
+      tc::k_tdot_tc<W><<<g, 256, tc::smem_tdot_tc<W>(), c->stream>>>(P, W, (const double*)B);
+      k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, 1), kThreads, 0, c->stream>>>(P, W, g, Cout);
+      return;
+    }
+  }
+  k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(wcap), c->stream>>>(P, W, B);
+  k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, W, gxw, Cout);
+}
+
 // One iteration of the kernel chain for scalar type T and block width W.
 template <typename T, int W>
 int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
@@ -530,10 +574,9 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   prof_mark(c, 0);
   for (int pass = 0; pass < 2; pass++) {
     P.sre_src = (pass == 0) ? 1 : 0;
-    k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(wcap), s>>>(P, W, X);
-    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, s>>>(P, W, gxw, c->d_C);
+    launch_tdot<T, W>(c, P, X, c->d_C, wcap, gy, gxw);
     prof_mark(c, 1);
-    k_update<T, W><<<gup, kThreads, smem_update<T, W>(wcap), s>>>(P, W, X, c->d_C);
+    launch_update<T, W>(c, P, X, c->d_C, wcap, gup);
     prof_mark(c, 2);
   }
   if (pre) {
@@ -759,6 +802,7 @@ int validate_opts(const ecg_opts* o, int t) {
   if (o->restart_at_switch && !(o->switch_tol > 0.0)) return ECG_EINVAL;
   if (o->block_residual != 0 && o->block_residual != 1) return ECG_EINVAL;
   if (o->stop_rule != ECG_STOP_R0 && o->stop_rule != ECG_STOP_B) return ECG_EINVAL;
+  if (o->tensor_cores != 0 && o->tensor_cores != 1) return ECG_EINVAL;
   if (o->block_residual && (o->variant != ECG_SRE || o->switch_tol > 0.0 || o->precision != ECG_FP64 ||
                             o->restart_every || o->restart_tol > 0.0))
     return ECG_EINVAL;
@@ -776,14 +820,12 @@ struct Ops {
   static void spmm(ecg_ctx* c, KP P, const double* X, double* Y) {
     k_spmm_gram<double, W, false, false><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, X, Y);
   }
-  static void tdot(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) {
+  static void tdot(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout, int wtot) {
     int gxw = window_gx(c, gy);
-    k_tdot_window<double, W><<<dim3(gxw, gy), kThreads, smem_tdot<double, W>(), c->stream>>>(P, gw, B);
-    k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, gw, gxw,
-                                                                                                   Cout);
+    launch_tdot<double, W>(c, P, B, Cout, wtot <= 32 ? wtot : kChunk, gy, gxw);
   }
-  static void update(ecg_ctx* c, KP P, double* X, const double* Cin) {
-    k_update<double, W><<<c->gx, kThreads, smem_update<double, W>(), c->stream>>>(P, W, X, Cin);
+  static void update(ecg_ctx* c, KP P, double* X, const double* Cin, int wtot) {
+    launch_update<double, W>(c, P, X, Cin, wtot <= 32 ? wtot : kChunk, c->gx);
   }
   static void orth(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) {
     const bool pre = (c->opts.ortho == ECG_PRE_CHOLQR);
@@ -821,9 +863,13 @@ int dispatch_w(int w, Args... args) {
 template <int W> struct RunGenerate { static void run(ecg_ctx* c, KP P) { Ops<W>::generate(c, P); } };
 template <int W> struct RunSpmm { static void run(ecg_ctx* c, KP P, const double* X, double* Y) { Ops<W>::spmm(c, P, X, Y); } };
 template <int W> struct RunTdot {
-  static void run(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout) { Ops<W>::tdot(c, P, gw, B, gy, Cout); }
+  static void run(ecg_ctx* c, KP P, int gw, const double* B, int gy, double* Cout, int wtot) {
+    Ops<W>::tdot(c, P, gw, B, gy, Cout, wtot);
+  }
 };
-template <int W> struct RunUpdate { static void run(ecg_ctx* c, KP P, double* X, const double* Cin) { Ops<W>::update(c, P, X, Cin); } };
+template <int W> struct RunUpdate {
+  static void run(ecg_ctx* c, KP P, double* X, const double* Cin, int wtot) { Ops<W>::update(c, P, X, Cin, wtot); }
+};
 template <int W> struct RunOrth {
   static void run(ecg_ctx* c, KP P, double* Wio, double* V, double* x, double* r) { Ops<W>::orth(c, P, Wio, V, x, r); }
 };
@@ -1168,6 +1214,7 @@ void ecg_default_opts(ecg_opts* o) {
   o->restart_at_switch = 0;
   o->block_residual = 0;
   o->stop_rule = ECG_STOP_R0;
+  o->tensor_cores = 1;
   o->stream = nullptr;
 }
 
@@ -1655,11 +1702,11 @@ int ecg_op_tdot(ecg_ctx* c, int m, const double* const* X, const int* wx, const 
   }
   const int gy = (off + kChunk - 1) / kChunk;
   int rc;
-  if ((rc = ensure_part(c, (size_t)gy * window_gx(c, gy) * kChunk * wy))) return rc;
+  if ((rc = ensure_part(c, (size_t)std::max(gy * window_gx(c, gy), tc_grid(c)) * kChunk * wy))) return rc;
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, wy, m, GEN_SPLIT)))) return rc;
   KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
-  if ((rc = dispatch_w<RunTdot>(wy, c, P, wy, Y, gy, C))) return rc;
+  if ((rc = dispatch_w<RunTdot>(wy, c, P, wy, Y, gy, C, off))) return rc;
   return finish_op(c, nullptr);
 }
 
@@ -1680,15 +1727,37 @@ int ecg_op_cgs2(ecg_ctx* c, int m, const double* const* Q, const double* const* 
   }
   const int gy = (off + kChunk - 1) / kChunk;
   int rc;
-  if ((rc = ensure_part(c, (size_t)gy * window_gx(c, gy) * kChunk * w))) return rc;
+  if ((rc = ensure_part(c, (size_t)std::max(gy * window_gx(c, gy), tc_grid(c)) * kChunk * w))) return rc;
   if ((rc = ensure_C(c, (size_t)gy * kChunk * w))) return rc;
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, w, m, GEN_SPLIT)))) return rc;
   KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
   for (int pass = 0; pass < 2; pass++) {
-    if ((rc = dispatch_w<RunTdot>(w, c, P, w, (const double*)W, gy, c->d_C))) return rc;
-    if ((rc = dispatch_w<RunUpdate>(w, c, P, W, (const double*)c->d_C))) return rc;
+    if ((rc = dispatch_w<RunTdot>(w, c, P, w, (const double*)W, gy, c->d_C, off))) return rc;
+    if ((rc = dispatch_w<RunUpdate>(w, c, P, W, (const double*)c->d_C, off))) return rc;
   }
+  return finish_op(c, nullptr);
+}
+
+int ecg_op_block_sub(ecg_ctx* c, int m, const double* const* Q, const int* wq, const double* Cm, double* W, int w) {
+  if (!c || m < 1 || m > 1024 || !Q || !wq || !Cm || !W || width_index(w) < 0) return ECG_EINVAL;
+  std::vector<BlockDesc> d(m);
+  int off = 0;
+  for (int j = 0; j < m; j++) {
+    if (!Q[j] || wq[j] < 1 || wq[j] > 128) return ECG_EINVAL;
+    d[j].W = const_cast<double*>(Q[j]);
+    d[j].V = const_cast<double*>(Q[j]);
+    d[j].w = wq[j];
+    d[j].off = off;
+    d[j].slot = 0;
+    d[j].pad = 0;
+    off += wq[j];
+  }
+  int rc;
+  if ((rc = put_op_desc(c, d))) return rc;
+  if ((rc = put_op_state(c, op_state(c, w, m, GEN_SPLIT)))) return rc;
+  KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
+  if ((rc = dispatch_w<RunUpdate>(w, c, P, W, Cm, off))) return rc;
   return finish_op(c, nullptr);
 }
 
@@ -1738,7 +1807,7 @@ int ecg_op_msdo_generate(ecg_ctx* c, const double* r, const double* P_prev, cons
   if ((rc = put_op_desc(c, d))) return rc;
   if ((rc = put_op_state(c, op_state(c, 1, 1, GEN_SPLIT)))) return rc;
   KP P = make_kp(c, c->d_opst, c->d_opdesc, false);
-  if ((rc = dispatch_w<RunTdot>(1, c, P, 1, r, 1, c->d_small + kSmallG))) return rc;
+  if ((rc = dispatch_w<RunTdot>(1, c, P, 1, r, 1, c->d_small + kSmallG, w))) return rc;
   k_neg_copy<<<1, 64, 0, c->stream>>>(c->d_small + kSmallG, c->d_small + kSmallBe, w);
   if ((rc = put_op_state(c, op_state(c, w, 1, GEN_MSDO)))) return rc;
   P.X = Pout;

@@ -1,0 +1,702 @@
+// ecg_tc.cuh -- FP64 block products of the CGS2 step on the tensor cores
+// (tcgen05, sm_103a).
+//
+// GB300 issues about 1.2 TFLOP/s of FP64 FMA against 6.7 TB/s of HBM, so
+// the FP64 CGS2 kernels of ecg_kernels.cuh are bound by FP64 issue (each
+// row of the window update W -= Q C costs 2 m t^2 FMAs).  The kernels here
+// compute the same FP64 products exactly enough for FP64 results, on the
+// FP16 tensor pipe, by the error-free splitting of Ozaki, Ogita, Oishi and
+// Rump ("Error-free transformations of matrix multiplication by using fast
+// routines of matrix multiplication and its applications", Numer.
+// Algorithms 59, 2012), in the fixed-point form used for tensor cores by
+// Mukunoki, Ozaki, Ogita and Imamura ("DGEMM using Tensor Cores, and Its
+// Accurate and Reproducible Versions", ISC 2020):
+//
+//   - every row of Q (and every column of C) gets a power-of-two scale from
+//     its largest binary exponent, so that each scaled entry lies in (-1, 1);
+//   - the scaled entry is truncated to a 64-bit fixed-point fraction U and
+//     cut into 8 digits of 8 bits, d_0 (most significant) .. d_7, each an
+//     integer in [-255, 255] that FP16 holds exactly;
+//   - the MMA multiplies digit matrices: FP16 x FP16 products of such
+//     integers are exact, and every FP32 sum in the accumulator stays an
+//     integer below 2^24, so the tensor-core accumulation is exact;
+//   - digit pairs (p, r) with the same p + r = g share a group accumulator
+//     (same binary weight 2^{-8(g+2)}); groups g <= 8 are kept;
+//   - the group sums are combined into one 128-bit integer and rounded once
+//     to FP64 with integer instructions only; the FP64 pipe does one
+//     subtraction per output (X - Q C).
+//
+// Error.  Each operand is truncated at 2^-64 of its scale and the dropped
+// groups (g >= 9) weigh below 2^-64; the computed Q C differs from the
+// exact product of the FP64 inputs by less than about 2^-60 x (row scale) x
+// (column scale) x window columns, below FP64's own rounding of a dot
+// product of that length (2^-53 per term).
+//
+// Exactness of the accumulator.  Group g sums at most 8 digit pairs over at
+// most 32 window columns: |sum| <= 8 * 32 * 255^2 = 16,646,400 < 2^24.  So
+// the kernels take windows of at most 32 columns (m t <= 32: the truncated
+// methods at t = 16 with two blocks, t = 8 with up to four).
+//
+// Rounding of non-finite input: a row or column whose scale is Inf/NaN
+// gives NaN outputs; subnormal inputs count as zero (below 2^-1022).
+#pragma once
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "ecg_kernels.cuh"
+
+namespace ecg {
+namespace tc {
+
+// ------------------------------------------------------------ tcgen05 PTX
+
+// Allocate ncols TMEM columns (power of two, 32..512) for this CTA; the
+// address is written to *dst (shared memory).  One whole warp executes it.
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading
+// (K-direction core-matrix) byte offset, stride (M/N-direction 8-row group)
+// byte offset; bit 46 is the fixed descriptor version.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::f16: FP16 A and B (both K-major), FP32 D.
+__host__ __device__ constexpr uint32_t idesc_f16(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// D[tmem] (+)= A * B, issued by one thread.
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on *bar once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+// 8 consecutive 32-bit TMEM columns of this warp's 32 lanes (lane quarter
+// of the warp) into v; tmem_wait_ld() before use.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Bounded wait on an mbarrier phase (kWaitNs of %globaltimer time).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (long long p = 0; p < kWaitPolls; p += 64) {
+    for (int q = 0; q < 64; q++)
+      if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+// Element (r, k) of a K-major, unswizzled operand tile of R rows and K
+// columns (FP16): 8 x 8 core matrices of 128 contiguous bytes, K-direction
+// core matrices adjacent (LBO = 128 B), row groups K/8 core matrices apart
+// (SBO = K * 16 B).
+__device__ __forceinline__ int kmaj(int r, int k, int K) { return ((r >> 3) * (K >> 3) + (k >> 3)) * 64 + (r & 7) * 8 + (k & 7); }
+
+// ------------------------------------------------------- fixed-point digits
+
+// Biased binary exponent of v (0 for zero and subnormals, 2047 for Inf/NaN).
+__device__ __forceinline__ int bexp(double v) { return (int)((__double_as_longlong(v) >> 52) & 0x7FF); }
+
+// |v| / 2^(S - 1022) as a 64-bit fraction, truncated: U = floor(|v| 2^(64 -
+// (S - 1022))) for the biased scale exponent S >= bexp(v).
+__device__ __forceinline__ unsigned long long fixed64(double v, int S) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = S - e;
+  return (e == 0 || sh >= 64) ? 0ull : ((m << 11) >> sh);
+}
+
+// Digit p (0: most significant) of two fractions u0, u1 as an FP16 pair
+// (low half from u0), with signs s0, s1 (0 or 1): the byte is placed under
+// the FP16 exponent of 1024 (0x6400 | d = 1024 + d exactly), and
+// (1024 + d) * sgn - 1024 * sgn gives +-d exactly.
+__device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned long long u1, int p, __half2 sgn,
+                                               __half2 off) {
+  const int sh = 56 - 8 * p;
+  const uint32_t d0 = (uint32_t)(u0 >> sh) & 0xFFu, d1 = (uint32_t)(u1 >> sh) & 0xFFu;
+  const uint32_t raw = 0x64006400u | d0 | (d1 << 16);
+  const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&raw), sgn, off);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+__device__ __forceinline__ void sign_pair(double v0, double v1, __half2& sgn, __half2& off) {
+  const __half a = __double_as_longlong(v0) < 0 ? __float2half(-1.f) : __float2half(1.f);
+  const __half b = __double_as_longlong(v1) < 0 ? __float2half(-1.f) : __float2half(1.f);
+  sgn = __halves2half2(a, b);
+  off = __halves2half2(__hmul(a, __float2half(-1024.f)), __hmul(b, __float2half(-1024.f)));
+}
+
+// (hi * 2^64 + lo) * 2^E rounded to the nearest double (ties to even), the
+// 128-bit integer in two's complement.  Results below 2^-1022 flush to
+// zero, results beyond the double range give Inf.
+__device__ __forceinline__ double i128_to_double(long long hi, unsigned long long lo, int E) {
+  unsigned long long sign = 0;
+  unsigned long long uh = (unsigned long long)hi, ul = lo;
+  if (hi < 0) {
+    sign = 1ull << 63;
+    ul = ~ul + 1ull;
+    uh = ~uh + (ul == 0ull ? 1ull : 0ull);
+  }
+  if (uh == 0ull && ul == 0ull) return 0.0;
+  int msb = uh ? 127 - __clzll((long long)uh) : 63 - __clzll((long long)ul);
+  unsigned long long m;
+  int sh = msb - 52;
+  if (sh <= 0) {
+    m = ul << (-sh);
+  } else {  // sh <= 75; the integers here stay below 2^117, so sh < 64
+    m = (sh == 0) ? ul : ((uh << (64 - sh)) | (ul >> sh));
+    const unsigned long long rem = ul & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      m++;
+      if (m == (1ull << 53)) {
+        m >>= 1;
+        sh++;
+      }
+    }
+  }
+  const int be = sh + E + 52 + 1023;
+  if (be >= 2047) return __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  if (be <= 0) return __longlong_as_double((long long)sign);
+  return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// (hi, lo) += v * 2^sh for an integer v (|v| < 2^31) and 0 <= sh <= 64,
+// in 128-bit two's complement.
+__device__ __forceinline__ void i128_add_shifted(long long& hi, unsigned long long& lo, long long v, int sh) {
+  long long ah;
+  unsigned long long al;
+  if (sh == 0) {
+    ah = v >> 63;
+    al = (unsigned long long)v;
+  } else if (sh >= 64) {
+    ah = v;
+    al = 0ull;
+  } else {
+    ah = v >> (64 - sh);
+    al = (unsigned long long)v << sh;
+  }
+  const unsigned long long s = lo + al;
+  hi += ah + (s < lo ? 1ll : 0ll);
+  lo = s;
+}
+
+// Group sums D_0 .. D_8 (weights 2^{8(8-g)}) as one 128-bit integer.
+__device__ __forceinline__ void groups_to_i128(const float (&D)[9], long long& hi, unsigned long long& lo) {
+  long long L = 0, H = 0;
+#pragma unroll
+  for (int g = 8; g >= 4; g--) L += (long long)__float2int_rn(D[g]) << (8 * (8 - g));
+#pragma unroll
+  for (int g = 3; g >= 0; g--) H += (long long)__float2int_rn(D[g]) << (8 * (3 - g));
+  // T = H 2^40 + L
+  const unsigned long long hl = (unsigned long long)H << 40;
+  lo = hl + (unsigned long long)L;
+  const unsigned long long carry = (lo < hl) ? 1ull : 0ull;
+  hi = (H >> 24) + (L < 0 ? -1ll : 0ll) + (long long)carry;
+}
+
+// ------------------------------------------------------------ CGS update
+
+// Xout = Xsrc - Q C for a window of at most 32 columns and block width W:
+// 128-row tiles, the MMA's M = 128 rows, A = the 8 digit slabs of the
+// tile's Q rows (K = 8 x 32), B = the digits of C stacked by digit
+// (N = 9 W: digit rows r = 0..8, r = 8 zero), slab p accumulating into
+// groups p .. 8 (TMEM columns p W ..).
+template <int W>
+struct UpdTc {
+  static constexpr int R = 128;       // rows per tile
+  static constexpr int KC = 32;       // window columns (K per digit slab)
+  static constexpr int ND = 8;        // digits per operand
+  static constexpr int NG = 9;        // groups kept (g = 0..8)
+  static constexpr int KA = ND * KC;  // A tile K
+  static constexpr int NB = NG * W;   // B rows (digit r = 0..8)
+  static constexpr uint32_t TCOLS = (NG * W <= 128) ? 128u : 256u;
+  // shared memory: A tile, B tile, scales, barrier
+  static constexpr size_t A_BYTES = (size_t)R * KA * 2;
+  static constexpr size_t B_BYTES = (size_t)NB * KC * 2;
+  static constexpr size_t SMEM = A_BYTES + B_BYTES + 4 * (W + R);  // + column and row scales
+};
+
+template <int W>
+constexpr size_t smem_update_tc() {
+  return UpdTc<W>::SMEM;
+}
+
+// True when the tensor-core update applies: FP64, W = 16, and a window of
+// at most 32 columns (wcap is the most the launch will see).
+template <typename T, int W>
+__host__ __device__ constexpr bool update_tc_ok(int wcap) {
+  return sizeof(T) == 8 && W == 16 && wcap <= 32;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio, const double* Cin) {
+  static_assert(W == 16, "the epilogue maps two 8-column halves of W = 16 onto the eight warps");
+  using U = UpdTc<W>;
+  constexpr int R = U::R, KC = U::KC, KA = U::KA, NB = U::NB;
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  const int nq = st->nq;
+  if (nq <= 0) return;
+  const BlockDesc* D = P.desc;
+  const int wtot = D[nq - 1].off + D[nq - 1].w;
+  if (wtot > KC) {  // not reached: the host launches this form only for windows of <= 32 columns
+    if (threadIdx.x == 0) {
+      ((DevState*)st)->status = ST_ECUDA;
+      ((DevState*)st)->stop = 1;
+    }
+    return;
+  }
+  const double* Xsrc = (P.sre_src && !P.prec && st->gen == GEN_SRE) ? (const double*)D[nq - 1].V : Xio;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __half* sA = (__half*)smem_raw;                         // R x KA, K-major
+  __half* sB = (__half*)(smem_raw + U::A_BYTES);          // NB x KC, K-major
+  int* sScaleC = (int*)(smem_raw + U::A_BYTES + U::B_BYTES);  // W column scales of C, then R row scales
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  __shared__ const double* colp[KC];  // column c of the window: pointer to row 0's entry
+  __shared__ int cols[KC];            // and its row stride (block width)
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // window columns
+  if (tid < KC) {
+    const double* p = nullptr;
+    int w = 0;
+    if (tid < wtot) {
+      int j = 0;
+      while (j + 1 < nq && D[j + 1].off <= tid) j++;
+      p = (const double*)D[j].W + (tid - D[j].off);
+      w = D[j].w;
+    }
+    colp[tid] = p;
+    cols[tid] = w;
+  }
+  // C's column scales and digits: B[r W + b][a] = digit r of C[a][b] (r < 8),
+  // zero for r = 8 and for a >= wtot
+  if (tid < W) {
+    int s = 0;
+    for (int a = 0; a < wtot; a++) s = max(s, bexp(Cin[a * W + tid]));
+    sScaleC[tid] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * (KC / 2); e += blockDim.x) {
+    const int n = e / (KC / 2), a = 2 * (e % (KC / 2));
+    const int r = n / W, b = n % W;
+    uint32_t v = 0;
+    if (r < 8 && a < wtot) {
+      const double c0 = Cin[a * W + b];
+      const double c1 = (a + 1 < wtot) ? Cin[(a + 1) * W + b] : 0.0;
+      __half2 sg, of;
+      sign_pair(c0, c1, sg, of);
+      v = digit_pair(fixed64(c0, sScaleC[b]), fixed64(c1, sScaleC[b]), r, sg, of);
+    }
+    *reinterpret_cast<uint32_t*>(&sB[kmaj(n, a, KC)]) = v;
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tbase, U::TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  bool cnan = false;
+  for (int b = 0; b < W; b++) cnan = cnan || (sScaleC[b] == 2047);
+
+  int r0, r1;
+  cta_rows_aligned(P.n, R, r0, r1);
+  const int ntiles = (r1 - r0 + R - 1) / R;
+  // slicing: thread (row = tid / 2, half = tid % 2) takes window columns
+  // [16 half, 16 half + 16) of its row
+  const int srow = tid >> 1, shalf = tid & 1;
+  bool ok = true;
+  int it = 0;
+  for (; it < ntiles && ok; it++) {
+    const int row0 = r0 + it * R;
+    const int nr = min(R, r1 - row0);
+    {
+      const int grow = row0 + srow;
+      double q[16];
+      int smax = 0;
+#pragma unroll
+      for (int c = 0; c < 16; c++) {
+        const int col = 16 * shalf + c;
+        const double* p = colp[col];
+        q[c] = (p && srow < nr) ? p[(long long)grow * cols[col]] : 0.0;
+        smax = max(smax, bexp(q[c]));
+      }
+      smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, 1));
+      if (smax == 2047) {  // a non-finite row: zero digits here, NaN output in the epilogue
+#pragma unroll
+        for (int c = 0; c < 16; c++) q[c] = 0.0;
+      }
+      const int S = (smax == 2047) ? 0 : smax;
+#pragma unroll
+      for (int c = 0; c < 16; c += 2) {
+        const unsigned long long u0 = fixed64(q[c], S), u1 = fixed64(q[c + 1], S);
+        __half2 sg, of;
+        sign_pair(q[c], q[c + 1], sg, of);
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * KC + 16 * shalf + c, KA)]) = digit_pair(u0, u1, p, sg, of);
+      }
+      if (shalf == 0) sScaleC[W + srow] = smax;  // the row scale, for the epilogue
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      // slab p: A columns [p KC, (p+1) KC), B digit rows r <= 8 - p (all 9
+      // for p = 0, so that the first MMA initialises every group column)
+      for (int p = 0; p < 8; p++) {
+        const int nrows = (p == 0 ? 9 : 9 - p) * W;
+        const uint32_t idesc = idesc_f16(R, nrows);
+        for (int ks = 0; ks < KC / 16; ks++) {
+          const uint64_t ad = sdesc(a0 + (uint32_t)((p * KC + ks * 16) / 8) * 128u, 128u, (uint32_t)(KA / 8) * 128u);
+          const uint64_t bd = sdesc(b0 + (uint32_t)(ks * 16 / 8) * 128u, 128u, (uint32_t)(KC / 8) * 128u);
+          mma_f16(tmem + (uint32_t)(p * W), ad, bd, idesc, (p > 0 || ks > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&bar);
+    }
+    const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+    ok = __syncthreads_and(done);
+    if (!ok) break;  // it stays the tile whose MMAs did not complete
+    tc_fence_after();
+    // epilogue: warp w reads rows 32 (w % 4) + lane, columns b in
+    // [8 (w / 4), 8 (w / 4) + 8) (W = 16) of the nine groups
+    {
+      const int row = 32 * (warp & 3) + lane;
+      const int bq = 8 * (warp >> 2);
+      float g[8][9];
+#pragma unroll
+      for (int gi = 0; gi < 9; gi++) {
+        uint32_t v[8];
+        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(gi * W + bq), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; j++) g[j][gi] = __uint_as_float(v[j]);
+      }
+      const int Si = sScaleC[W + row];
+      if (row < nr) {
+        const long long grow = row0 + row;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          const int b = bq + j;
+          long long hi;
+          unsigned long long lo;
+          groups_to_i128(g[j], hi, lo);
+          const int Sb = sScaleC[b];
+          double pq;
+          if (Si == 2047 || cnan) pq = __longlong_as_double(0x7FF8000000000000ll);
+          else pq = i128_to_double(hi, lo, (Si - 1022) + (Sb - 1022) - 80);
+          Xio[grow * W + b] = Xsrc[grow * W + b] - pq;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (!ok && tid == 0) {
+    ((DevState*)st)->fault = 1;
+    ((DevState*)st)->status = ST_ECUDA;
+    ((DevState*)st)->stop = 1;
+    // give the MMAs in flight a second bounded wait before the columns are freed
+    mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
+}
+
+// ------------------------------------------------------- CGS coefficients
+
+// Per-CTA partial sums of C = [V_0 .. V_{nq-1}]^T B for a window of at most
+// 32 columns and W = 16, over the CTA's rows, into the partial-sum layout of
+// k_tdot_window (reduced by k_reduce_C).  128-row tiles are the MMA's K:
+// A = the V digits of the tile, M = (digit p, window column a) = 256 rows
+// in two MMAs (p < 4 and p >= 4), B = the B digits, N = (digit r, column
+// b); the second MMA keeps r <= 4 (pairs with p + r > 8 are dropped).
+// Every accumulator entry sums 128 exact products of at most 255^2:
+// 128 * 65025 < 2^23.  The scales are per tile and column, so each tile's
+// digit-pair sums are combined into 128-bit integers per (p, a, b), summed
+// over p, rounded to FP64 and added to the CTA's FP64 sums.
+template <int W>
+struct TdotTc {
+  static constexpr int R = 128;             // rows per tile (MMA K)
+  static constexpr int KC = 32;             // window columns
+  static constexpr int MA = 8 * KC;         // A rows (digit, column)
+  static constexpr int NB = 8 * W;          // B rows (digit, column)
+  static constexpr int N2 = 5 * W;          // second MMA: r <= 4
+  static constexpr uint32_t TCOLS = 256;    // NB + N2 = 208 columns used
+  static constexpr size_t A_BYTES = (size_t)MA * R * 2;
+  static constexpr size_t B_BYTES = (size_t)NB * R * 2;
+  // the per-(p, a, b) 128-bit partials reuse the A tile once the MMAs are done
+  static constexpr size_t PART_BYTES = (size_t)8 * KC * W * 16;
+  static constexpr size_t SMEM = A_BYTES + B_BYTES + 4 * (KC + W);
+  static_assert(PART_BYTES <= A_BYTES, "partials alias the A tile");
+};
+
+template <int W>
+constexpr size_t smem_tdot_tc() {
+  return TdotTc<W>::SMEM;
+}
+
+template <typename T, int W>
+__host__ __device__ constexpr bool tdot_tc_ok(int wcap) {
+  return sizeof(T) == 8 && W == 16 && wcap <= 32;
+}
+
+// float holding an integer of magnitude below 2^24, to int (exact)
+__device__ __forceinline__ int f2i_exact(float f) { return __float2int_rn(f); }
+
+template <int W>
+__global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* B) {
+  static_assert(W == 16, "16 B columns per tile row");
+  using U = TdotTc<W>;
+  constexpr int R = U::R, KC = U::KC, MA = U::MA, NB = U::NB, N2 = U::N2;
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  const int nq = st->nq;
+  if (nq <= 0) return;
+  const BlockDesc* D = P.desc;
+  const int wtot = D[nq - 1].off + D[nq - 1].w;
+  if (wtot > KC || blockIdx.y != 0) {  // not reached: launched only for windows of <= 32 columns
+    if (threadIdx.x == 0 && wtot > KC) {
+      ((DevState*)st)->status = ST_ECUDA;
+      ((DevState*)st)->stop = 1;
+    }
+    return;
+  }
+  if (P.sre_src && !P.prec && st->gen == GEN_SRE) B = (const double*)D[nq - 1].V;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __half* sA = (__half*)smem_raw;                       // MA x R, K-major
+  __half* sB = (__half*)(smem_raw + U::A_BYTES);        // NB x R, K-major
+  int* sSv = (int*)(smem_raw + U::A_BYTES + U::B_BYTES);  // KC column scales of V
+  int* sSx = sSv + KC;                                     // W column scales of B
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  __shared__ const double* colp[KC];
+  __shared__ int cols[KC];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid < KC) {
+    const double* p = nullptr;
+    int w = 0;
+    if (tid < wtot) {
+      int j = 0;
+      while (j + 1 < nq && D[j + 1].off <= tid) j++;
+      p = (const double*)D[j].V + (tid - D[j].off);
+      w = D[j].w;
+    }
+    colp[tid] = p;
+    cols[tid] = w;
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tbase, U::TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+
+  int r0, r1;
+  cta_rows_aligned(P.n, R, r0, r1);
+  const int ntiles = (r1 - r0 + R - 1) / R;
+  // loading: V column va = lane, row pairs vg + 8 j (vg = warp); B column
+  // xb = tid % 16, row pairs xg + 16 j (xg = tid / 16)
+  const int va = lane, vg = warp, xb = tid & 15, xg = tid >> 4;
+  // outputs of this thread: (a, b) = (tid / 16, tid % 16) and (tid / 16 + 16, tid % 16)
+  double acc0 = 0.0, acc1 = 0.0;
+  bool ok = true;
+  int it = 0;
+  for (; it < ntiles && ok; it++) {
+    const int row0 = r0 + it * R;
+    const int nr = min(R, r1 - row0);
+    if (tid < KC + W) sSv[tid] = 0;  // sSx follows sSv
+    __syncthreads();
+    double v[8][2], x[4][2];
+    {
+      const double* p = colp[va];
+      const long long cs = cols[va];
+      int mx = 0;
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        const int rr = 2 * (vg + 8 * j);
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          v[j][u] = (p && rr + u < nr) ? p[(long long)(row0 + rr + u) * cs] : 0.0;
+          mx = max(mx, bexp(v[j][u]));
+        }
+      }
+      atomicMax(&sSv[va], mx);
+      int mb = 0;
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const int rr = 2 * (xg + 16 * j);
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          x[j][u] = (rr + u < nr) ? B[(long long)(row0 + rr + u) * W + xb] : 0.0;
+          mb = max(mb, bexp(x[j][u]));
+        }
+      }
+      mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 16));
+      if (lane < 16) atomicMax(&sSx[xb], mb);
+    }
+    __syncthreads();
+    {
+      const int Sv = sSv[va] == 2047 ? 0 : sSv[va];
+#pragma unroll
+      for (int j = 0; j < 8; j++) {
+        double a0 = v[j][0], a1 = v[j][1];
+        if (sSv[va] == 2047) a0 = a1 = 0.0;  // non-finite column: NaN output below
+        const unsigned long long u0 = fixed64(a0, Sv), u1 = fixed64(a1, Sv);
+        __half2 sg, of;
+        sign_pair(a0, a1, sg, of);
+        const int k = 2 * (vg + 8 * j);
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) = digit_pair(u0, u1, p, sg, of);
+      }
+      const int Sx = sSx[xb] == 2047 ? 0 : sSx[xb];
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        double b0 = x[j][0], b1 = x[j][1];
+        if (sSx[xb] == 2047) b0 = b1 = 0.0;
+        const unsigned long long u0 = fixed64(b0, Sx), u1 = fixed64(b1, Sx);
+        __half2 sg, of;
+        sign_pair(b0, b1, sg, of);
+        const int k = 2 * (xg + 16 * j);
+#pragma unroll
+        for (int r = 0; r < 8; r++)
+          *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) = digit_pair(u0, u1, r, sg, of);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+      const uint32_t sbo = (uint32_t)(R / 8) * 128u;
+      for (int ks = 0; ks < R / 16; ks++) {
+        const uint32_t ko = (uint32_t)(ks * 16 / 8) * 128u;
+        const uint64_t bd = sdesc(b0 + ko, 128u, sbo);
+        // digits p < 4: A rows [0, 128) x all B rows; p >= 4: A rows [128, 256) x B rows r <= 4
+        mma_f16(tmem, sdesc(a0 + ko, 128u, sbo), bd, idesc_f16(128, NB), ks > 0 ? 1u : 0u);
+        mma_f16(tmem + (uint32_t)NB, sdesc(a0 + (uint32_t)(128 / 8) * sbo + ko, 128u, sbo), bd, idesc_f16(128, N2),
+                ks > 0 ? 1u : 0u);
+      }
+      mma_commit(&bar);
+    }
+    const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+    ok = __syncthreads_and(done);
+    if (!ok) break;
+    tc_fence_after();
+    // drain: warp w holds digit p = 4 (w / 4) + w % 4 of window column a =
+    // lane; it combines its digit pairs (p, r) per b into 128-bit integers
+    {
+      const int region = warp >> 2, q = warp & 3;
+      const int p = 4 * region + q;
+      const int rmax = min(7, 8 - p);
+      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
+      // the MMAs have completed (barrier above), so the A tile is free: the
+      // 128-bit partials go there
+      long long* part = reinterpret_cast<long long*>(smem_raw);
+#pragma unroll
+      for (int bh = 0; bh < W / 8; bh++) {
+        float d[8][8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) {
+          if (r <= rmax) {  // uniform over the warp
+            uint32_t t0[8];
+            tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t0);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 8; j++) d[r][j] = __uint_as_float(t0[j]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) d[r][j] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          // T = sum_r D_{p r} 2^{8 (8 - p - r)} over the kept pairs p + r <= 8
+          long long hi = 0;
+          unsigned long long lo = 0;
+#pragma unroll
+          for (int r = 0; r < 8; r++)
+            if (r <= rmax) i128_add_shifted(hi, lo, (long long)f2i_exact(d[r][j]), 8 * (8 - p - r));
+          const int e = (p * KC + lane) * W + 8 * bh + j;
+          part[2 * e] = hi;
+          part[2 * e + 1] = (long long)lo;
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+    {
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const int a = (tid >> 4) + 16 * h, b = tid & 15;
+        long long hi = 0;
+        unsigned long long lo = 0;
+        const long long* part = reinterpret_cast<const long long*>(smem_raw);
+        for (int p = 0; p < 8; p++) {
+          const int e = (p * KC + a) * W + b;
+          const unsigned long long l2 = (unsigned long long)part[2 * e + 1];
+          const unsigned long long s = lo + l2;
+          hi += part[2 * e] + (s < lo ? 1ll : 0ll);
+          lo = s;
+        }
+        double val;
+        if (sSv[a] == 2047 || sSx[b] == 2047) val = __longlong_as_double(0x7FF8000000000000ll);
+        else val = i128_to_double(hi, lo, (sSv[a] - 1022) + (sSx[b] - 1022) - 80);
+        if (h == 0) acc0 += val;
+        else acc1 += val;
+      }
+    }
+    __syncthreads();
+  }
+  if (!ok && tid == 0) {
+    ((DevState*)st)->fault = 1;
+    ((DevState*)st)->status = ST_ECUDA;
+    ((DevState*)st)->stop = 1;
+    mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
+  if (!ok) return;
+  double* out = P.part_buf + (long long)blockIdx.x * (kChunk * W);
+  const int a0 = tid >> 4, b = tid & 15;
+  if (a0 < wtot) out[a0 * W + b] = acc0;
+  if (a0 + 16 < wtot) out[(a0 + 16) * W + b] = acc1;
+}
+
+}  // namespace tc
+}  // namespace ecg

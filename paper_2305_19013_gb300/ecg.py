@@ -55,6 +55,7 @@ class _Opts(C.Structure):
         ("restart_at_switch", C.c_int),
         ("stop_rule", C.c_int),
         ("block_residual", C.c_int),
+        ("tensor_cores", C.c_int),
         ("stream", C.c_void_p),
     ]
 
@@ -107,6 +108,7 @@ SIGNATURES = {
     "ecg_op_spmm": (_I, [_P, _P, _P, _I]),
     "ecg_op_tdot": (_I, [_P, _I, _P, _P, _P, _I, _P]),
     "ecg_op_cgs2": (_I, [_P, _I, _P, _P, _P, _P, _I]),
+    "ecg_op_block_sub": (_I, [_P, _I, _P, _P, _P, _P, _I]),
     "ecg_op_a_orthonormalize": (_I, [_P, _P, _P, _I]),
     "ecg_op_block_update": (_I, [_P, _P, _P, _I, _P, _P, C.POINTER(C.c_double)]),
     "ecg_op_msdo_generate": (_I, [_P, _P, _P, _P, _I, _P]),
@@ -213,6 +215,7 @@ class Solver:
         restart_at_switch: bool = False,
         block_residual: bool = False,
         stop_rule: int = 0,
+        tensor_cores: bool = True,
         stream=None,
     ):
         lib = load()
@@ -247,6 +250,7 @@ class Solver:
         o.restart_at_switch = 1 if restart_at_switch else 0
         o.block_residual = 1 if block_residual else 0
         o.stop_rule = int(stop_rule)
+        o.tensor_cores = 1 if tensor_cores else 0
         o.stream = stream
         ctx = C.c_void_p()
         rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))
@@ -423,6 +427,25 @@ class Solver:
                 self._ctx, m, C.cast(qp, C.c_void_p), C.cast(vp, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(W), int(w)
             ),
             "ecg_op_cgs2",
+        )
+        return W
+
+    def block_sub(self, Qs, Cm, W):
+        """W - [Q_0 .. Q_{m-1}] C (ecg_op_block_sub) on a copy of W."""
+        w = W.shape[1]
+        _check_tensor(W, (self.n, w), "W")
+        W = W.clone()
+        m = len(Qs)
+        for q in Qs:
+            _check_tensor(q, (self.n, q.shape[1]), "Q")
+        tot = sum(int(q.shape[1]) for q in Qs)
+        _check_tensor(Cm, (tot, w), "C")
+        qp = (C.c_void_p * m)(*[q.data_ptr() for q in Qs])
+        ws = (C.c_int * m)(*[int(q.shape[1]) for q in Qs])
+        self._rc(
+            self._lib.ecg_op_block_sub(self._ctx, m, C.cast(qp, C.c_void_p), C.cast(ws, C.c_void_p), _ptr(Cm), _ptr(W),
+                                       int(w)),
+            "ecg_op_block_sub",
         )
         return W
 

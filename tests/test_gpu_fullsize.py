@@ -9,7 +9,8 @@
   iteration.
 - Three systems of the batched workload's sizes (sides 128, 320, 512,
   log-normal coefficients, t = 8) through the batched solver in FP64, each
-  against its own oracle solve.
+  against its own oracle solve (the envelope spans four perturbed runs and
+  the run with the other orthonormalisation, as for the small systems).
 
 The oracle is the same C source as everywhere else, built with OpenMP and
 run on every host core; it returns the same bits as the single-threaded
@@ -86,10 +87,12 @@ def test_fullsize_ic0_solve_to_tolerance(headline):
 
 
 def history_within_envelope(g_hist, o, perturbed, h0):
-    """Per iteration: |g_k - o_k| <= max(TRACK rho_0, 10 x the largest
-    |v_k - o_k| over the perturbed oracle runs v)."""
+    """Per iteration k: |g_k - o_k| <= max(TRACK rho_0, 10 x the largest
+    |v_j - o_j| over the perturbed oracle runs v and iterations j <= k).  The
+    running maximum: once a chaotic run has drifted, a handful of perturbed
+    runs can all pass close to the oracle at some later k by chance."""
     k = min(len(g_hist), len(o.history), *[len(v.history) for v in perturbed])
-    spread = np.max([np.abs(v.history[:k] - o.history[:k]) for v in perturbed], axis=0)
+    spread = np.maximum.accumulate(np.max([np.abs(v.history[:k] - o.history[:k]) for v in perturbed], axis=0))
     dev_ = np.abs(g_hist[:k] - o.history[:k])
     ok = dev_ <= np.maximum(TRACK * h0, 10.0 * spread)
     return ok, dev_, spread
@@ -106,7 +109,7 @@ def test_fullsize_200_iterations_history(headline):
     o = O.ecg_solve(A, p.part, 16, p.b, tol=0.0, maxit=K + 1, trunc=2)
     rng = np.random.default_rng(99)
     perturbed = [O.ecg_solve(A, p.part, 16, p.b * (1.0 + 1e-15 * rng.standard_normal(p.n)), tol=0.0,
-                             maxit=K + 1, trunc=2) for _ in range(2)]
+                             maxit=K + 1, trunc=2) for _ in range(3)]
     h0 = o.history[0]
     ok, d, spread = history_within_envelope(g.history, o, perturbed, h0)
     onset = K
@@ -134,7 +137,7 @@ def test_fullsize_batched_systems_fp64():
     assert rc == ecg.OK
     ms = []
     for p, g in zip(ps, res):
-        r = envelope_metrics(p, g.iters, g.history, g.x, dict(trunc=2), maxit, nperturbed=2, other_ortho=False)
+        r = envelope_metrics(p, g.iters, g.history, g.x, dict(trunc=2), maxit, nperturbed=4, other_ortho=True)
         report(f"batched_fp64_side{int(p.meta['side'])}", n=p.n, gpu_iters=g.iters, oracle_iters=r["oracle"].iters,
                iters_delta=r["iters_delta"], envelope_iters=r["oracle_iters"], onset=r["onset"],
                hist_dev_to_onset=r["hist_dev_to_onset"], x_rel_err=r["x_rel_err"], x_spread=r["x_spread"])
