@@ -510,15 +510,17 @@ int tc_grid(const ecg_ctx* c) {
 // applies (FP64, W = 16, at most 32 window columns, tensor_cores on), else
 // the CUDA-core kernel.  The tensor-core form runs two CTAs per SM (each
 // holds 256 of the SM's 512 TMEM columns).
+// wmax is the most window columns the launch can see; the CUDA-core
+// kernel's shared memory follows P.wcap, the size that kernel assumes.
 template <typename T, int W>
-void launch_update(ecg_ctx* c, const KP& P, T* X, const double* Cin, int wcap, int gup) {
+void launch_update(ecg_ctx* c, const KP& P, T* X, const double* Cin, int wmax, int gup) {
   if constexpr (tc::update_tc_ok<T, W>(32)) {
-    if (c->opts.tensor_cores && tc::update_tc_ok<T, W>(wcap)) {
+    if (c->opts.tensor_cores && tc::update_tc_ok<T, W>(wmax)) {
       tc::k_update_tc<W><<<tc_grid(c), 256, tc::smem_update_tc<W>(), c->stream>>>(P, W, (double*)X, Cin);
       return;
     }
   }
-  k_update<T, W><<<gup, kThreads, smem_update<T, W>(wcap), c->stream>>>(P, W, X, Cin);
+  k_update<T, W><<<gup, kThreads, smem_update<T, W>(P.wcap), c->stream>>>(P, W, X, Cin);
 }
 
 // C = V^T B over the window (CGS coefficients) into Cout: the tensor-core
@@ -526,16 +528,16 @@ void launch_update(ecg_ctx* c, const KP& P, T* X, const double* Cin, int wcap, i
 // tensor_cores on), else the CUDA-core kernel; then the fixed-order
 // reduction of the per-CTA partials.
 template <typename T, int W>
-void launch_tdot(ecg_ctx* c, const KP& P, const T* B, double* Cout, int wcap, int gy, int gxw) {
+void launch_tdot(ecg_ctx* c, const KP& P, const T* B, double* Cout, int wmax, int gy, int gxw) {
   if constexpr (tc::tdot_tc_ok<T, W>(32)) {
-    if (c->opts.tensor_cores && tc::tdot_tc_ok<T, W>(wcap) && gy == 1) {
+    if (c->opts.tensor_cores && tc::tdot_tc_ok<T, W>(wmax) && gy == 1) {
       const int g = tc_grid(c);
       tc::k_tdot_tc<W><<<g, 256, tc::smem_tdot_tc<W>(), c->stream>>>(P, W, (const double*)B);
       k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, 1), kThreads, 0, c->stream>>>(P, W, g, Cout);
       return;
     }
   }
-  k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(wcap), c->stream>>>(P, W, B);
+  k_tdot_window<T, W><<<dim3(gxw, gy), kThreads, smem_tdot<T, W>(P.wcap), c->stream>>>(P, W, B);
   k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, gy), kThreads, 0, c->stream>>>(P, W, gxw, Cout);
 }
 
