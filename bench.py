@@ -59,8 +59,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # one iteration, from one ncu capture of the current kernels (the first pass
 # of an SRE iteration reads V_{k-1} as both a window block and the block)
 MEASURED_TRAFFIC = {
-    ("cgs_tdot", 16, 2): ((268.72e6 + 3.75e6) + (402.95e6 + 4.84e6)) / 2,
-    ("cgs_update", 16, 2): ((403.09e6 + 115.24e6) + (403.00e6 + 108.42e6)) / 2,
+    ("cgs_tdot", 16, 2, "alu"): ((268.72e6 + 3.75e6) + (402.95e6 + 4.84e6)) / 2,
+    ("cgs_update", 16, 2, "alu"): ((403.09e6 + 115.24e6) + (403.00e6 + 108.42e6)) / 2,
 }
 
 
@@ -157,14 +157,25 @@ class ClockSampler:
         }
 
 
-def algorithmic_counts(n, nnz, t, trunc, K):
-    """FP64 flops per kernel class and bytes per iteration, summed over
-    iterations 1..K (the window holds min(k-1, trunc) blocks at iteration k).
-    Flops count every multiply-add the method's definition needs (2 flops);
-    symmetric Grams count their upper triangle."""
+def algorithmic_counts(n, nnz, t, trunc, K, sre=True):
+    """FP64 flops and algorithmic DRAM bytes per kernel class, summed over
+    iterations 1..K (the window holds m = min(k-1, trunc) blocks at
+    iteration k).  Flops count every multiply-add the method's definition
+    needs (2 flops); symmetric Grams count their upper triangle.  Bytes count
+    each distinct n x t block a class must read or write once per launch
+    (B = 8 n t bytes):
+      cgs_tdot    pass 1 of an SRE iteration reads the m window blocks V_j
+                  (the block itself is V_{k-1}, one of them); pass 2 reads
+                  the m blocks and X: (2m + 1) B per iteration
+      cgs_update  each pass reads the m blocks Q_j and its source, writes X:
+                  2 (m + 2) B
+      gram_e      reads X: B
+      spmm_gram   reads X and A (12 nnz + 4 (n + 1)) and r, writes Y:
+                  2 B + 12 nnz + 4 (n + 1) + 8 n
+      final       reads X, Y, x, r, writes W_k, V_k, x, r: 4 B + 32 n"""
     tri = t * (t + 1) // 2
     fl = {"cgs_tdot": 0.0, "cgs_update": 0.0, "gram_e": 0.0, "spmm_gram": 0.0, "final": 0.0}
-    byts = 0.0
+    by = {k: 0.0 for k in fl}
     B = 8.0 * n * t
     for k in range(1, K + 1):
         m = min(k - 1, trunc)
@@ -173,9 +184,13 @@ def algorithmic_counts(n, nnz, t, trunc, K):
         fl["gram_e"] += 2.0 * tri * n
         fl["spmm_gram"] += 2.0 * (nnz * t + 2 * tri * n + tri * n + t * n)
         fl["final"] += 2.0 * (2 * tri * n + 2 * t * n)
-        passes = 2 * (2 * m + 3) if m > 0 else 0
-        byts += (2 + passes + 1 + 2 + 4) * B + 12.0 * nnz + 4.0 * (n + 1) + 40.0 * n
-    return fl, byts
+        if m > 0:
+            by["cgs_tdot"] += ((2 * m + 1) if sre else (2 * m + 2)) * B
+            by["cgs_update"] += 2 * (m + 2) * B
+        by["gram_e"] += B
+        by["spmm_gram"] += 2 * B + 12.0 * nnz + 4.0 * (n + 1) + 8.0 * n
+        by["final"] += 4 * B + 32.0 * n
+    return fl, by
 
 
 # Algorithmic DRAM bytes of one row-iteration of the batched kernel (FP32,
@@ -347,7 +362,7 @@ def time_to_tol_runs(torch, p, stream, args, names):
         if pre and pb is None:
             pb = Wk.jacobi_blocks(p, args.prec_blocks)
         with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
-                                     stream=stream.cuda_stream) as sv:
+                                     tensor_cores=args.tensor_cores, stream=stream.cuda_stream) as sv:
             ts = time.perf_counter()
             if pre:  # block Jacobi IC(0) (Section 3, Algorithm 5)
                 sv.set_preconditioner(pb, args.prec_blocks)
@@ -395,6 +410,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--trunc", type=int, default=2)
     ap.add_argument("--ortho", type=int, default=0)
+    ap.add_argument("--no-tensor-cores", dest="tensor_cores", action="store_false",
+                    help="run the FP64 CGS products on CUDA-core FMAs instead of the tensor cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-time-to-tol", action="store_true", help="skip the solves to 1e-8")
     ap.add_argument("--time-to-tol-maxit", type=int, default=60000)
@@ -428,7 +445,8 @@ def main():
     assert Wm >= 3, "at least 3 warm-up steps"
     p = headline_problem(seed=2001 + rank)
     stream = torch.cuda.current_stream()
-    solver = ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, stream=stream.cuda_stream)
+    solver = ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, tensor_cores=args.tensor_cores,
+                                     stream=stream.cuda_stream)
     b_dev = torch.from_numpy(p.b).cuda()
     x_dev = torch.empty_like(b_dev)
 
@@ -472,12 +490,30 @@ def main():
     solver.solve(b_dev, tol=0.0, maxit=args.trunc + K + 1, x_out=x_dev)
     prof = solver.profile_read()
     solver.profile(False)
-    fl, bytes_total = algorithmic_counts(p.n, p.nnz, 16, args.trunc, args.trunc + K)
+    fl, by = algorithmic_counts(p.n, p.nnz, 16, args.trunc, args.trunc + K)
+    bytes_total = sum(by.values())
     tot_ms = sum(v[0] for v in prof.values())
-    dom = max((k for k in prof if k in fl), key=lambda k: prof[k][0])
-    dom_ms, dom_launch = prof[dom]
-    achieved = fl[dom] / (dom_ms / 1000.0) / 1e12
     pk = peaks()
+    hbm = pk["hbm_gbs"]
+    # the CGS classes run on the tensor cores (t = 16, window <= 32 columns),
+    # bound by HBM; the other block classes are FP64 FMA-bound
+    tc_classes = {"cgs_tdot", "cgs_update"} if (args.tensor_cores and args.trunc * 16 <= 32) else set()
+    classes = {}
+    for k in fl:
+        if k not in prof or not prof[k][1]:
+            continue
+        ms_k, n_k = prof[k]
+        if k in tc_classes:
+            ach = by[k] / (ms_k / 1000.0) / 1e9
+            classes[k] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                          "ms": ms_k, "launches": n_k, "algorithmic_bytes": by[k]}
+        else:
+            ach = fl[k] / (ms_k / 1000.0) / 1e12
+            classes[k] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": ach / FP64_PEAK_TFLOPS, "ms": ms_k, "launches": n_k,
+                          "hbm_gbs": by[k] / (ms_k / 1000.0) / 1e9}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    dc = classes[dom]
     probe = None
     if world == 1:
         try:
@@ -485,30 +521,28 @@ def main():
         except Exception:
             probe = None
     roofline = {
-        "bound": "alu",
+        "bound": dc["bound"],
         "kernel": dom,
-        "achieved": achieved,
-        "peak": FP64_PEAK_TFLOPS,
-        "unit": "TFLOP/s",
-        "frac": achieved / FP64_PEAK_TFLOPS,
-        "traffic": MEASURED_TRAFFIC.get((dom, 16, args.trunc)),
-        "traffic_note": "DRAM bytes per full-window launch, mean of the two CGS passes, from one ncu capture of "
-        "the current kernel; algorithmic bytes per launch: cgs_tdot reads the two window blocks and the block, "
-        "3 x 8 x n x 16 = 402.7 MB (the first pass of an SRE iteration reads V_{k-1}, already a window block: "
-        "268.4 MB) + 2.5 MB of partial sums; cgs_update 3 x 8 x n x 16 read + 8 x n x 16 written = 536.9 MB "
-        "(part of the write leaves L2 after the kernel)",
-        "peak_source": "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
-        "peak_probe": probe,
-        "frac_of_probe": (achieved / probe) if probe else None,
-        "probe_note": "peak_probe: FP64 FMA rate measured in this run by ecg_probe_fp64 (8 independent chains "
-        "per thread, 8 CTAs x 256 threads per SM)",
-        "launches": dom_launch,
-        "share": dom_ms / tot_ms,
+        "achieved": dc["achieved"],
+        "peak": dc["peak"],
+        "unit": dc["unit"],
+        "frac": dc["frac"],
+        "traffic": MEASURED_TRAFFIC.get((dom, 16, args.trunc, dc["bound"])),
+        "traffic_note": "DRAM bytes (read + write) per launch of this class from one ncu capture of the current "
+        "kernels (null when none was taken since they changed)",
+        "peak_source": (pk["source"] + " HBM copy bandwidth") if dc["bound"] == "hbm" else
+        "derived FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz",
+        "fp64_probe_tflops": probe,
+        "probe_note": "FP64 FMA rate measured in this run by ecg_probe_fp64 (8 independent chains per thread, "
+        "8 CTAs x 256 threads per SM)",
+        "launches": dc["launches"],
+        "share": dc["ms"] / tot_ms,
+        "algorithmic": "bytes or flops per class as bench.algorithmic_counts states them, over the profiled "
+        "trunc + K iterations",
     }
     prof_ms_total = tot_ms
     total_fl = sum(fl.values())
     iter_tflops = total_fl / (prof_ms_total / 1000.0) / 1e12
-    hbm = pk["hbm_gbs"]
     hbm_gbs = bytes_total / (prof_ms_total / 1000.0) / 1e9
 
     line = {
@@ -551,6 +585,7 @@ def main():
             "hbm_peak": hbm,
             "hbm_peak_source": pk["source"],
             "profile_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]},
+            "classes": classes,
             "note": "profiled run of trunc + K iterations (window start-up included); algorithmic bytes and flops "
             "counted for the same iterations",
         },

@@ -267,8 +267,12 @@ int set_all_smem_attrs() {
   int rc = ECG_OK;
   CK(cudaFuncSetAttribute(tc::k_update_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)tc::smem_update_tc<16>()));
-  CK(cudaFuncSetAttribute(tc::k_tdot_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                          (int)tc::smem_tdot_tc<16>()));
+  CK(cudaFuncSetAttribute(tc::k_final_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc::smem_final_tc<16>()));
+  CK(cudaFuncSetAttribute(tc::k_tdot_tc<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc::smem_tdot_tc<double, 16>()));
+  CK(cudaFuncSetAttribute(tc::k_tdot_tc<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)tc::smem_tdot_tc<float, 16>()));
   if ((rc = set_smem_attrs<1>())) return rc;
   if ((rc = set_smem_attrs<2>())) return rc;
   if ((rc = set_smem_attrs<4>())) return rc;
@@ -532,7 +536,7 @@ void launch_tdot(ecg_ctx* c, const KP& P, const T* B, double* Cout, int wmax, in
   if constexpr (tc::tdot_tc_ok<T, W>(32)) {
     if (c->opts.tensor_cores && tc::tdot_tc_ok<T, W>(wmax) && gy == 1) {
       const int g = tc_grid(c);
-      tc::k_tdot_tc<W><<<g, 256, tc::smem_tdot_tc<W>(), c->stream>>>(P, W, (const double*)B);
+      tc::k_tdot_tc<T, W><<<g, 256, tc::smem_tdot_tc<T, W>(), c->stream>>>(P, W, B);
       k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, 1), kThreads, 0, c->stream>>>(P, W, g, Cout);
       return;
     }
@@ -604,7 +608,17 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
     k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
   }
   prof_mark(c, 6);
-  k_final<T, W><<<gfin, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
+  int gf = gfin;  // CTAs that write rho / beta partials
+  bool fin_tc = false;
+  if constexpr (tc::final_tc_ok<T, W>()) {
+    if (c->opts.tensor_cores) {
+      fin_tc = true;
+      gf = tc_grid(c);
+      tc::k_final_tc<W><<<gf, 256, tc::smem_final_tc<W>(), s>>>(P, W, (const double*)X, (const double*)Y, nullptr,
+                                                              nullptr, (double*)x, (double*)r);
+    }
+  }
+  if (!fin_tc) k_final<T, W><<<gfin, kThreads, smem_final<T, W>(), s>>>(P, W, X, Y, nullptr, nullptr, x, r);
   if constexpr (sizeof(T) == 8) {
     if (P.block) {  // block-residual mode: alpha = W_k^T R, R -= V_k alpha, x, r = R 1
       k_block_alpha<W><<<c->gx, kThreads, 0, s>>>(P, W);
@@ -614,7 +628,7 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
     }
   }
   prof_mark(c, 7);
-  k_finish<<<1, kThreads, 0, s>>>(P, W, gfin, (int)sizeof(T));
+  k_finish<<<1, kThreads, 0, s>>>(P, W, gf, (int)sizeof(T));
   prof_mark(c, 8);
   CK(cudaGetLastError());
   return ECG_OK;

@@ -434,50 +434,100 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
 
 // ------------------------------------------------------- CGS coefficients
 
+// Digit splitting of one scalar type: ND digits of 8 bits of a fraction U
+// with FB bits, value = sign * U 2^-FB 2^(S - BIAS) for the biased scale
+// exponent S of the value's column tile; digit pairs (p, r) with p + r <=
+// GMAX are kept.  FP64: 8 digits (64 bits >= the 53-bit significand),
+// pairs up to p + r = 8 (the dropped ones weigh below 2^-80 of the
+// scales).  FP32: 3 digits hold the 24-bit significand exactly and every
+// pair is kept, so the FP32 product is exact before the FP64 sums.
+template <typename T>
+struct Digits;
+template <>
+struct Digits<double> {
+  static constexpr int ND = 8, GMAX = 8, BIAS = 1022, FB = 64, EINF = 2047;
+  __device__ static int bexp(double v) { return tc::bexp(v); }
+  __device__ static unsigned long long fixed(double v, int S) { return fixed64(v, S); }
+  __device__ static bool neg(double v) { return __double_as_longlong(v) < 0; }
+};
+template <>
+struct Digits<float> {
+  static constexpr int ND = 3, GMAX = 4, BIAS = 126, FB = 24, EINF = 255;
+  __device__ static int bexp(float v) { return (int)((__float_as_uint(v) >> 23) & 0xFFu); }
+  // |v| / 2^(S - 126) as a 24-bit fraction, truncated (exact when S = bexp(v))
+  __device__ static unsigned long long fixed(float v, int S) {
+    const uint32_t b = __float_as_uint(v);
+    const int e = (int)((b >> 23) & 0xFFu);
+    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
+    const int sh = S - e;
+    return (e == 0 || sh >= 24) ? 0ull : (unsigned long long)(m >> sh);
+  }
+  __device__ static bool neg(float v) { return (__float_as_uint(v) >> 31) != 0u; }
+};
+
+// Digit pair (shift sh selects the digit) with the signs of two values.
+template <typename T>
+__device__ __forceinline__ uint32_t digit_pair_t(unsigned long long u0, unsigned long long u1, int sh, bool n0,
+                                                 bool n1) {
+  const __half one = __float2half(1.f), mone = __float2half(-1.f);
+  const __half a = n0 ? mone : one, b = n1 ? mone : one;
+  const __half2 sgn = __halves2half2(a, b);
+  const __half2 off = __halves2half2(__hmul(a, __float2half(-1024.f)), __hmul(b, __float2half(-1024.f)));
+  const uint32_t d0 = (uint32_t)(u0 >> sh) & 0xFFu, d1 = (uint32_t)(u1 >> sh) & 0xFFu;
+  const uint32_t raw = 0x64006400u | d0 | (d1 << 16);
+  const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&raw), sgn, off);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // Per-CTA partial sums of C = [V_0 .. V_{nq-1}]^T B for a window of at most
 // 32 columns and W = 16, over the CTA's rows, into the partial-sum layout of
-// k_tdot_window (reduced by k_reduce_C).  128-row tiles are the MMA's K:
-// A = the V digits of the tile, M = (digit p, window column a) = 256 rows
-// in two MMAs (p < 4 and p >= 4), B = the B digits, N = (digit r, column
-// b); the second MMA keeps r <= 4 (pairs with p + r > 8 are dropped).
-// Every accumulator entry sums 128 exact products of at most 255^2:
-// 128 * 65025 < 2^23.  The scales are per tile and column, so each tile's
-// digit-pair sums are combined into 128-bit integers per (p, a, b), summed
-// over p, rounded to FP64 and added to the CTA's FP64 sums.
-template <int W>
+// k_tdot_window (reduced by k_reduce_C).  128-row tiles are the MMA's K.
+// A = the V digits of the tile, M = (digit p, window column a): FP64 256
+// rows in two MMAs (p < 4 and p >= 4; the second keeps B digits r <= 4),
+// FP32 96 rows in one (rows 96..127 zero).  B = the B digits, N = (digit r,
+// column b).  Every accumulator entry sums 128 exact products of at most
+// 255^2: 128 * 65025 < 2^23.  The scales are per tile and column, so each
+// tile's digit-pair sums are combined into 128-bit integers per (p, a, b),
+// summed over p, rounded to FP64 and added to the CTA's FP64 sums.
+template <typename T, int W>
 struct TdotTc {
-  static constexpr int R = 128;             // rows per tile (MMA K)
-  static constexpr int KC = 32;             // window columns
-  static constexpr int MA = 8 * KC;         // A rows (digit, column)
-  static constexpr int NB = 8 * W;          // B rows (digit, column)
-  static constexpr int N2 = 5 * W;          // second MMA: r <= 4
-  static constexpr uint32_t TCOLS = 256;    // NB + N2 = 208 columns used
+  using Dg = Digits<T>;
+  static constexpr int ND = Dg::ND;
+  static constexpr int R = 128;                              // rows per tile (MMA K)
+  static constexpr int KC = 32;                              // window columns
+  static constexpr int MA = (ND * KC > 128) ? ND * KC : 128;  // A rows (digit, column), padded
+  static constexpr int NB = ND * W;                          // B rows (digit, column)
+  static constexpr int N2 = (Dg::GMAX - 4 + 1) * W;           // second MMA (FP64): r <= GMAX - 4
+  static constexpr uint32_t TCOLS = (ND * KC > 128) ? 256u : 64u;
   static constexpr size_t A_BYTES = (size_t)MA * R * 2;
   static constexpr size_t B_BYTES = (size_t)NB * R * 2;
   // the per-(p, a, b) 128-bit partials reuse the A tile once the MMAs are done
-  static constexpr size_t PART_BYTES = (size_t)8 * KC * W * 16;
+  static constexpr size_t PART_BYTES = (size_t)ND * KC * W * 16;
   static constexpr size_t SMEM = A_BYTES + B_BYTES + 4 * (KC + W);
   static_assert(PART_BYTES <= A_BYTES, "partials alias the A tile");
+  static_assert(NB + (ND * KC > 128 ? N2 : 0) <= (int)TCOLS, "accumulator columns");
 };
 
-template <int W>
+template <typename T, int W>
 constexpr size_t smem_tdot_tc() {
-  return TdotTc<W>::SMEM;
+  return TdotTc<T, W>::SMEM;
 }
 
 template <typename T, int W>
 __host__ __device__ constexpr bool tdot_tc_ok(int wcap) {
-  return sizeof(T) == 8 && W == 16 && wcap <= 32;
+  return W == 16 && wcap <= 32;
 }
 
 // float holding an integer of magnitude below 2^24, to int (exact)
 __device__ __forceinline__ int f2i_exact(float f) { return __float2int_rn(f); }
 
-template <int W>
-__global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* B) {
+template <typename T, int W>
+__global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
   static_assert(W == 16, "16 B columns per tile row");
-  using U = TdotTc<W>;
-  constexpr int R = U::R, KC = U::KC, MA = U::MA, NB = U::NB, N2 = U::N2;
+  using U = TdotTc<T, W>;
+  using Dg = typename U::Dg;
+  constexpr int R = U::R, KC = U::KC, NB = U::NB, N2 = U::N2, ND = U::ND;
+  constexpr bool TWO = (ND * KC > 128);  // FP64: two MMAs per k-step
   const DevState* st = P.st;
   if (skip(st, gw)) return;
   const int nq = st->nq;
@@ -491,28 +541,32 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
     }
     return;
   }
-  if (P.sre_src && !P.prec && st->gen == GEN_SRE) B = (const double*)D[nq - 1].V;
+  if (P.sre_src && !P.prec && st->gen == GEN_SRE) B = (const T*)D[nq - 1].V;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __half* sA = (__half*)smem_raw;                       // MA x R, K-major
-  __half* sB = (__half*)(smem_raw + U::A_BYTES);        // NB x R, K-major
+  __half* sA = (__half*)smem_raw;                          // MA x R, K-major
+  __half* sB = (__half*)(smem_raw + U::A_BYTES);           // NB x R, K-major
   int* sSv = (int*)(smem_raw + U::A_BYTES + U::B_BYTES);  // KC column scales of V
   int* sSx = sSv + KC;                                     // W column scales of B
   __shared__ uint64_t bar;
   __shared__ uint32_t tbase;
-  __shared__ const double* colp[KC];
+  __shared__ const T* colp[KC];
   __shared__ int cols[KC];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid < KC) {
-    const double* p = nullptr;
+    const T* p = nullptr;
     int w = 0;
     if (tid < wtot) {
       int j = 0;
       while (j + 1 < nq && D[j + 1].off <= tid) j++;
-      p = (const double*)D[j].V + (tid - D[j].off);
+      p = (const T*)D[j].V + (tid - D[j].off);
       w = D[j].w;
     }
     colp[tid] = p;
     cols[tid] = w;
+  }
+  if constexpr (ND * KC < U::MA) {  // padding rows of A stay zero
+    for (int e = tid; e < (U::MA - ND * KC) * R / 2; e += blockDim.x)
+      reinterpret_cast<uint32_t*>(sA + (size_t)ND * KC * R)[e] = 0u;
   }
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -539,9 +593,9 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
     const int nr = min(R, r1 - row0);
     if (tid < KC + W) sSv[tid] = 0;  // sSx follows sSv
     __syncthreads();
-    double v[8][2], x[4][2];
+    T v[8][2], x[4][2];
     {
-      const double* p = colp[va];
+      const T* p = colp[va];
       const long long cs = cols[va];
       int mx = 0;
 #pragma unroll
@@ -549,8 +603,8 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
         const int rr = 2 * (vg + 8 * j);
 #pragma unroll
         for (int u = 0; u < 2; u++) {
-          v[j][u] = (p && rr + u < nr) ? p[(long long)(row0 + rr + u) * cs] : 0.0;
-          mx = max(mx, bexp(v[j][u]));
+          v[j][u] = (p && rr + u < nr) ? p[(long long)(row0 + rr + u) * cs] : T(0);
+          mx = max(mx, Dg::bexp(v[j][u]));
         }
       }
       atomicMax(&sSv[va], mx);
@@ -560,8 +614,8 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
         const int rr = 2 * (xg + 16 * j);
 #pragma unroll
         for (int u = 0; u < 2; u++) {
-          x[j][u] = (rr + u < nr) ? B[(long long)(row0 + rr + u) * W + xb] : 0.0;
-          mb = max(mb, bexp(x[j][u]));
+          x[j][u] = (rr + u < nr) ? B[(long long)(row0 + rr + u) * W + xb] : T(0);
+          mb = max(mb, Dg::bexp(x[j][u]));
         }
       }
       mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 16));
@@ -569,31 +623,31 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
     }
     __syncthreads();
     {
-      const int Sv = sSv[va] == 2047 ? 0 : sSv[va];
+      const bool vinf = sSv[va] == Dg::EINF;  // non-finite column: zero digits, NaN output below
+      const int Sv = vinf ? 0 : sSv[va];
 #pragma unroll
       for (int j = 0; j < 8; j++) {
-        double a0 = v[j][0], a1 = v[j][1];
-        if (sSv[va] == 2047) a0 = a1 = 0.0;  // non-finite column: NaN output below
-        const unsigned long long u0 = fixed64(a0, Sv), u1 = fixed64(a1, Sv);
-        __half2 sg, of;
-        sign_pair(a0, a1, sg, of);
+        const T a0 = vinf ? T(0) : v[j][0], a1 = vinf ? T(0) : v[j][1];
+        const unsigned long long u0 = Dg::fixed(a0, Sv), u1 = Dg::fixed(a1, Sv);
+        const bool n0 = Dg::neg(a0), n1 = Dg::neg(a1);
         const int k = 2 * (vg + 8 * j);
 #pragma unroll
-        for (int p = 0; p < 8; p++)
-          *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) = digit_pair(u0, u1, p, sg, of);
+        for (int p = 0; p < ND; p++)
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) =
+              digit_pair_t<T>(u0, u1, Dg::FB - 8 * (p + 1), n0, n1);
       }
-      const int Sx = sSx[xb] == 2047 ? 0 : sSx[xb];
+      const bool xinf = sSx[xb] == Dg::EINF;
+      const int Sx = xinf ? 0 : sSx[xb];
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        double b0 = x[j][0], b1 = x[j][1];
-        if (sSx[xb] == 2047) b0 = b1 = 0.0;
-        const unsigned long long u0 = fixed64(b0, Sx), u1 = fixed64(b1, Sx);
-        __half2 sg, of;
-        sign_pair(b0, b1, sg, of);
+        const T b0 = xinf ? T(0) : x[j][0], b1 = xinf ? T(0) : x[j][1];
+        const unsigned long long u0 = Dg::fixed(b0, Sx), u1 = Dg::fixed(b1, Sx);
+        const bool n0 = Dg::neg(b0), n1 = Dg::neg(b1);
         const int k = 2 * (xg + 16 * j);
 #pragma unroll
-        for (int r = 0; r < 8; r++)
-          *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) = digit_pair(u0, u1, r, sg, of);
+        for (int r = 0; r < ND; r++)
+          *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) =
+              digit_pair_t<T>(u0, u1, Dg::FB - 8 * (r + 1), n0, n1);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -606,10 +660,12 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
       for (int ks = 0; ks < R / 16; ks++) {
         const uint32_t ko = (uint32_t)(ks * 16 / 8) * 128u;
         const uint64_t bd = sdesc(b0 + ko, 128u, sbo);
-        // digits p < 4: A rows [0, 128) x all B rows; p >= 4: A rows [128, 256) x B rows r <= 4
+        // FP64: digits p < 4 in A rows [0, 128) x all B rows, p >= 4 in A
+        // rows [128, 256) x B digit rows r <= GMAX - 4; FP32: one MMA
         mma_f16(tmem, sdesc(a0 + ko, 128u, sbo), bd, idesc_f16(128, NB), ks > 0 ? 1u : 0u);
-        mma_f16(tmem + (uint32_t)NB, sdesc(a0 + (uint32_t)(128 / 8) * sbo + ko, 128u, sbo), bd, idesc_f16(128, N2),
-                ks > 0 ? 1u : 0u);
+        if constexpr (TWO)
+          mma_f16(tmem + (uint32_t)NB, sdesc(a0 + (uint32_t)(128 / 8) * sbo + ko, 128u, sbo), bd,
+                  idesc_f16(128, N2), ks > 0 ? 1u : 0u);
       }
       mma_commit(&bar);
     }
@@ -617,43 +673,45 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
     ok = __syncthreads_and(done);
     if (!ok) break;
     tc_fence_after();
-    // drain: warp w holds digit p = 4 (w / 4) + w % 4 of window column a =
-    // lane; it combines its digit pairs (p, r) per b into 128-bit integers
+    // drain: warp w holds digit p = 4 (w / 4) + w % 4 (FP64; FP32: p = w for
+    // w < 3) of window column a = lane; it combines its digit pairs (p, r)
+    // per b into 128-bit integers T = sum_r D_{p r} 2^{8 (GMAX - p - r)}
     {
       const int region = warp >> 2, q = warp & 3;
-      const int p = 4 * region + q;
-      const int rmax = min(7, 8 - p);
-      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
+      const int p = TWO ? 4 * region + q : (region == 0 ? q : ND);
+      const int rmax = min(ND - 1, Dg::GMAX - p);
       // the MMAs have completed (barrier above), so the A tile is free: the
       // 128-bit partials go there
       long long* part = reinterpret_cast<long long*>(smem_raw);
+      if (p < ND) {  // uniform over the warp
+        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
 #pragma unroll
-      for (int bh = 0; bh < W / 8; bh++) {
-        float d[8][8];
+        for (int bh = 0; bh < W / 8; bh++) {
+          float d[ND][8];
 #pragma unroll
-        for (int r = 0; r < 8; r++) {
-          if (r <= rmax) {  // uniform over the warp
-            uint32_t t0[8];
-            tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t0);
-            tmem_wait_ld();
+          for (int r = 0; r < ND; r++) {
+            if (r <= rmax) {  // uniform over the warp
+              uint32_t t0[8];
+              tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t0);
+              tmem_wait_ld();
 #pragma unroll
-            for (int j = 0; j < 8; j++) d[r][j] = __uint_as_float(t0[j]);
-          } else {
+              for (int j = 0; j < 8; j++) d[r][j] = __uint_as_float(t0[j]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 8; j++) d[r][j] = 0.f;
+              for (int j = 0; j < 8; j++) d[r][j] = 0.f;
+            }
           }
-        }
 #pragma unroll
-        for (int j = 0; j < 8; j++) {
-          // T = sum_r D_{p r} 2^{8 (8 - p - r)} over the kept pairs p + r <= 8
-          long long hi = 0;
-          unsigned long long lo = 0;
+          for (int j = 0; j < 8; j++) {
+            long long hi = 0;
+            unsigned long long lo = 0;
 #pragma unroll
-          for (int r = 0; r < 8; r++)
-            if (r <= rmax) i128_add_shifted(hi, lo, (long long)f2i_exact(d[r][j]), 8 * (8 - p - r));
-          const int e = (p * KC + lane) * W + 8 * bh + j;
-          part[2 * e] = hi;
-          part[2 * e + 1] = (long long)lo;
+            for (int r = 0; r < ND; r++)
+              if (r <= rmax) i128_add_shifted(hi, lo, (long long)f2i_exact(d[r][j]), 8 * (Dg::GMAX - p - r));
+            const int e = (p * KC + lane) * W + 8 * bh + j;
+            part[2 * e] = hi;
+            part[2 * e + 1] = (long long)lo;
+          }
         }
       }
     }
@@ -666,16 +724,16 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
         long long hi = 0;
         unsigned long long lo = 0;
         const long long* part = reinterpret_cast<const long long*>(smem_raw);
-        for (int p = 0; p < 8; p++) {
+        for (int p = 0; p < ND; p++) {
           const int e = (p * KC + a) * W + b;
           const unsigned long long l2 = (unsigned long long)part[2 * e + 1];
-          const unsigned long long s = lo + l2;
-          hi += part[2 * e] + (s < lo ? 1ll : 0ll);
-          lo = s;
+          const unsigned long long s2 = lo + l2;
+          hi += part[2 * e] + (s2 < lo ? 1ll : 0ll);
+          lo = s2;
         }
         double val;
-        if (sSv[a] == 2047 || sSx[b] == 2047) val = __longlong_as_double(0x7FF8000000000000ll);
-        else val = i128_to_double(hi, lo, (sSv[a] - 1022) + (sSx[b] - 1022) - 80);
+        if (sSv[a] == Dg::EINF || sSx[b] == Dg::EINF) val = __longlong_as_double(0x7FF8000000000000ll);
+        else val = i128_to_double(hi, lo, (sSv[a] - Dg::BIAS) + (sSx[b] - Dg::BIAS) - 8 * (Dg::GMAX + 2));
         if (h == 0) acc0 += val;
         else acc1 += val;
       }
@@ -696,6 +754,255 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const double* 
   const int a0 = tid >> 4, b = tid & 15;
   if (a0 < wtot) out[a0 * W + b] = acc0;
   if (a0 + 16 < wtot) out[(a0 + 16) * W + b] = acc1;
+}
+
+// ------------------------------------------------------------ final update
+
+// W_k = X R^{-1} and V_k = Y R^{-1} into the window slot, x += W_k alpha,
+// r -= V_k alpha, per-CTA partial ||r||^2 and (MSDO-CG) beta partials
+// V_k^T r: the FP64 k_final with its two triangular transforms on the tensor
+// cores (Algorithm 1, the A-orthonormalised block and the x/r updates).
+// Per 128-row tile: A_X and A_Y = the 8 digit slabs of the X and Y rows
+// (row scales), B = the digits of R^{-1} by column scale, stacked by digit;
+// slab p accumulates into groups p .. 7 (8 groups: pairs p + r <= 7; the
+// dropped ones weigh below 2^-57 of row scale x column scale).  X's groups
+// take TMEM columns [0, 128), Y's [128, 256).  Each group sum is at most
+// 8 * 16 * 255^2 < 2^23.  The dot products with alpha, the residual norm and
+// beta stay FP64, one FMA per entry as in k_final.
+template <int W>
+struct FinTc {
+  static constexpr int R = 128;      // rows per tile
+  static constexpr int ND = 8;       // digits
+  static constexpr int NG = 8;       // groups kept
+  static constexpr int KA = ND * W;  // A tile K (digit, column)
+  static constexpr int NB = NG * W;  // B rows (digit r = 0..7, column b)
+  static constexpr uint32_t TCOLS = 256;
+  static constexpr size_t A_BYTES = (size_t)R * KA * 2;  // one of A_X, A_Y
+  static constexpr size_t B_BYTES = (size_t)NB * W * 2;
+  static constexpr size_t SMEM = 2 * A_BYTES + B_BYTES + 4 * (W + 2 * R) + 8 * (2 * W);
+};
+
+template <int W>
+constexpr size_t smem_final_tc() {
+  return FinTc<W>::SMEM;
+}
+
+template <typename T, int W>
+__host__ __device__ constexpr bool final_tc_ok() {
+  return sizeof(T) == 8 && W == 16;
+}
+
+template <int W>
+__global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double* Xin, const double* Yin,
+                                                     double* Wout, double* Vout, double* xio, double* rio) {
+  static_assert(W == 16, "one 16-column row per slicing thread");
+  using U = FinTc<W>;
+  constexpr int R = U::R, KA = U::KA, NB = U::NB;
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  if (Wout == nullptr) {  // the solver's window slot
+    const long long sl = st->next_slot;
+    Wout = (double*)P.slotW + sl * P.slot_stride;
+    Vout = (double*)P.slotV + sl * P.slot_stride;
+  }
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __half* sAX = (__half*)smem_raw;                                 // R x KA
+  __half* sAY = (__half*)(smem_raw + U::A_BYTES);                  // R x KA
+  __half* sB = (__half*)(smem_raw + 2 * U::A_BYTES);               // NB x W
+  int* sSc = (int*)(smem_raw + 2 * U::A_BYTES + U::B_BYTES);       // W column scales of R^{-1}
+  int* sSr = sSc + W;                                               // 2 R row scales (X rows, Y rows)
+  double* sal = (double*)(sSr + 2 * R);                             // W: alpha
+  double* sbeta = sal + W;                                          // W: beta partial sums
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  __shared__ double sred[8];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* Ri = P.small + kSmallRi;
+  if (tid < W) {
+    int sc = 0;
+    for (int a = 0; a < W; a++) sc = max(sc, bexp(Ri[a * W + tid]));
+    sSc[tid] = sc;
+    sal[tid] = P.block ? 0.0 : P.small[kSmallAl + tid];  // block-residual mode updates x, r elsewhere
+    sbeta[tid] = 0.0;
+  }
+  __syncthreads();
+  for (int e = tid; e < NB * (W / 2); e += blockDim.x) {
+    const int n = e / (W / 2), a = 2 * (e % (W / 2));
+    const int r = n / W, b = n % W;
+    const double c0 = Ri[a * W + b], c1 = Ri[(a + 1) * W + b];
+    __half2 sg, of;
+    sign_pair(c0, c1, sg, of);
+    *reinterpret_cast<uint32_t*>(&sB[kmaj(n, a, W)]) =
+        digit_pair(fixed64(c0, sSc[b]), fixed64(c1, sSc[b]), r, sg, of);
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+  }
+  if (warp == 0) tmem_alloc(&tbase, U::TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  bool cnan = false;
+  for (int b = 0; b < W; b++) cnan = cnan || (sSc[b] == 2047);
+
+  int r0, r1;
+  cta_rows_aligned(P.n, R, r0, r1);
+  const int ntiles = (r1 - r0 + R - 1) / R;
+  // slicing: thread (row = tid / 2, which = tid % 2) takes the X (0) or Y (1) row
+  const int srow = tid >> 1, which = tid & 1;
+  // epilogue: warp w reads rows 32 (w % 4) + lane of X's (w < 4) or Y's groups
+  const int erow = 32 * (warp & 3) + lane, ey = warp >> 2;
+  double rho_acc = 0.0;
+  double bacc[W];
+#pragma unroll
+  for (int b = 0; b < W; b++) bacc[b] = 0.0;
+  bool ok = true;
+  int it = 0;
+  for (; it < ntiles && ok; it++) {
+    const int row0 = r0 + it * R;
+    const int nr = min(R, r1 - row0);
+    {
+      const double* src = which ? Yin : Xin;
+      __half* sA = which ? sAY : sAX;
+      double q[W];
+      int smax = 0;
+#pragma unroll
+      for (int c = 0; c < W; c++) {
+        q[c] = (srow < nr) ? src[(long long)(row0 + srow) * W + c] : 0.0;
+        smax = max(smax, bexp(q[c]));
+      }
+      if (smax == 2047) {
+#pragma unroll
+        for (int c = 0; c < W; c++) q[c] = 0.0;
+      }
+      const int S = (smax == 2047) ? 0 : smax;
+#pragma unroll
+      for (int c = 0; c < W; c += 2) {
+        const unsigned long long u0 = fixed64(q[c], S), u1 = fixed64(q[c + 1], S);
+        __half2 sg, of;
+        sign_pair(q[c], q[c + 1], sg, of);
+#pragma unroll
+        for (int p = 0; p < 8; p++)
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * W + c, KA)]) = digit_pair(u0, u1, p, sg, of);
+      }
+      sSr[which * R + srow] = smax;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t b0 = smem_u32(sB);
+      const uint64_t bd = sdesc(b0, 128u, (uint32_t)(W / 8) * 128u);
+      for (int y = 0; y < 2; y++) {
+        const uint32_t a0 = smem_u32(y ? sAY : sAX);
+        for (int p = 0; p < 8; p++) {
+          const uint64_t ad = sdesc(a0 + (uint32_t)(p * W / 8) * 128u, 128u, (uint32_t)(KA / 8) * 128u);
+          mma_f16(tmem + (uint32_t)(y * NB + p * W), ad, bd, idesc_f16(R, (8 - p) * W), p > 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(&bar);
+    }
+    const bool done = mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+    ok = __syncthreads_and(done);
+    if (!ok) break;
+    tc_fence_after();
+    // epilogue: rows of W_k (ey = 0) or V_k (ey = 1)
+    {
+      // T_b = sum_g D_g 2^{8 (8 - g)}, accumulated group by group
+      long long hia[W];
+      unsigned long long loa[W];
+#pragma unroll
+      for (int b = 0; b < W; b++) {
+        hia[b] = 0;
+        loa[b] = 0;
+      }
+#pragma unroll
+      for (int gi = 0; gi < 8; gi++) {
+        uint32_t v0[8], v1[8];
+        const uint32_t ta = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(ey * NB + gi * W);
+        tmem_ld8(ta, v0);
+        tmem_ld8(ta + 8u, v1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+          i128_add_shifted(hia[j], loa[j], (long long)f2i_exact(__uint_as_float(v0[j])), 8 * (8 - gi));
+          i128_add_shifted(hia[8 + j], loa[8 + j], (long long)f2i_exact(__uint_as_float(v1[j])), 8 * (8 - gi));
+        }
+      }
+      const int Si = sSr[ey * R + erow];
+      double dsum = 0.0;
+      double vk[W];
+#pragma unroll
+      for (int b = 0; b < W; b++) {
+        const long long hi = hia[b];
+        const unsigned long long lo = loa[b];
+        double val;
+        if (Si == 2047 || cnan) val = __longlong_as_double(0x7FF8000000000000ll);
+        else val = i128_to_double(hi, lo, (Si - 1022) + (sSc[b] - 1022) - 80);
+        vk[b] = val;
+        dsum += val * sal[b];
+      }
+      if (erow < nr) {
+        const long long i = row0 + erow;
+        double* out = ey ? Vout : Wout;
+#pragma unroll
+        for (int b = 0; b < W; b++) out[i * W + b] = vk[b];
+        if (ey == 0) {
+          xio[i] += dsum;
+        } else {
+          const double rn = rio[i] - dsum;
+          rio[i] = rn;
+          rho_acc += rn * rn;
+          if (P.want_beta) {
+#pragma unroll
+            for (int b = 0; b < W; b++) bacc[b] = fma(vk[b], rn, bacc[b]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (!ok && tid == 0) {
+    ((DevState*)st)->fault = 1;
+    ((DevState*)st)->status = ST_ECUDA;
+    ((DevState*)st)->stop = 1;
+    mbar_wait_bounded(&bar, (uint32_t)(it & 1));
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
+  if (!ok) return;
+  // fixed-order CTA sums: warp shuffles, then the warps in order
+  double v = rho_acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) sred[warp] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < 8; w++) tot += sred[w];
+    P.rho_part[blockIdx.x] = tot;
+  }
+  if (P.want_beta) {
+#pragma unroll
+    for (int b = 0; b < W; b++) {
+      double bv = bacc[b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) bv += __shfl_xor_sync(0xffffffffu, bv, o);
+      __syncthreads();
+      if (lane == 0) sred[warp] = bv;
+      __syncthreads();
+      if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; w++) tot += sred[w];
+        P.beta_part[(long long)blockIdx.x * 64 + b] = tot;
+      }
+    }
+  }
 }
 
 }  // namespace tc

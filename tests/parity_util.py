@@ -11,7 +11,9 @@ relative, and once with the other orthonormalisation.  The GPU run must
       is chaotic a deviation grows about 100x per iteration, and the
       1e-12 onset leaves those iterations' margin against the 1e-8 bar,
   (b) converge within the iteration range of those runs widened by its
-      width (at least +-2), and
+      width (at least +-2 and +-1% of the count: the perturbed runs inject
+      rounding once, in b, while the GPU's arithmetic differs from the
+      oracle's at every iteration), and
   (c) end within ten times the oracle's own spread of x (at least 1e-8).
 """
 import numpy as np
@@ -69,7 +71,10 @@ def envelope_assert(m, g_iters):
     assert all(v.status == 0 for v in m["variants"])
     its = m["oracle_iters"]
     lo, hi = min(its), max(its)
-    width = max(2, hi - lo)
+    # the perturbed runs inject rounding once (in b); a different FP64
+    # implementation injects it at every iteration, which moves long
+    # truncated runs by a few tenths of a percent more: at least 1%
+    width = max(2, hi - lo, -(-hi // 100))
     assert lo - width <= g_iters <= hi + width, (g_iters, its)
     assert m["hist_dev_to_onset"] <= TRACK, (m["onset"], m["hist_dev_to_onset"])
     assert m["x_rel_err"] <= max(1e-8, 10.0 * m["x_spread"]), (m["x_rel_err"], m["x_spread"])
