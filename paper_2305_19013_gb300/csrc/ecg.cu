@@ -611,7 +611,8 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   int gf = gfin;  // CTAs that write rho / beta partials
   bool fin_tc = false;
   if constexpr (tc::final_tc_ok<T, W>()) {
-    if (c->opts.tensor_cores) {
+    // the block-residual mode takes rho from k_block_update's c->gx partials
+    if (c->opts.tensor_cores && !P.block) {
       fin_tc = true;
       gf = tc_grid(c);
       tc::k_final_tc<W><<<gf, 256, tc::smem_final_tc<W>(), s>>>(P, W, (const double*)X, (const double*)Y, nullptr,
