@@ -95,6 +95,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte
+// aligned), cached in L2 only; cp_async16_wait waits for this thread's
+// copies.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Bounded wait on an mbarrier phase (kWaitNs of %globaltimer time).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -139,6 +148,23 @@ __device__ __forceinline__ uint32_t digit_pair(unsigned long long u0, unsigned l
   const uint32_t raw = 0x64006400u | d0 | (d1 << 16);
   const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&raw), sgn, off);
   return *reinterpret_cast<const uint32_t*>(&h);
+}
+// The digits in byte k (0..3, compile time) of the 32-bit words w0 and w1
+// as an FP16 pair under the exponent of 1024 (two byte permutations), then
+// signed and unbiased by one FP16x2 FMA: (1024 + d) sgn - 1024 sgn = +-d.
+__device__ __forceinline__ uint32_t digit_pair_bytes(uint32_t w0, uint32_t w1, int k, __half2 sgn, __half2 off) {
+  const uint32_t t = __byte_perm(w0, w1, (uint32_t)(k | ((4 + k) << 4)));  // [w0.k, w1.k, -, -]
+  const uint32_t raw = __byte_perm(t, 0x64646464u, 0x4140u);               // [w0.k, 0x64, w1.k, 0x64]
+  const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&raw), sgn, off);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+// Digit p (0: most significant) of two 64-bit fractions.
+__device__ __forceinline__ uint32_t digit_pair64(unsigned long long u0, unsigned long long u1, int p, __half2 sgn,
+                                                 __half2 off) {
+  const int byte = 7 - p;
+  const uint32_t w0 = byte >= 4 ? (uint32_t)(u0 >> 32) : (uint32_t)u0;
+  const uint32_t w1 = byte >= 4 ? (uint32_t)(u1 >> 32) : (uint32_t)u1;
+  return digit_pair_bytes(w0, w1, byte & 3, sgn, off);
 }
 __device__ __forceinline__ void sign_pair(double v0, double v1, __half2& sgn, __half2& off) {
   const __half a = __double_as_longlong(v0) < 0 ? __float2half(-1.f) : __float2half(1.f);
@@ -234,7 +260,8 @@ struct UpdTc {
   // shared memory: A tile, B tile, scales, barrier
   static constexpr size_t A_BYTES = (size_t)R * KA * 2;
   static constexpr size_t B_BYTES = (size_t)NB * KC * 2;
-  static constexpr size_t SMEM = A_BYTES + B_BYTES + 4 * (W + R);  // + column and row scales
+  static constexpr size_t Q_BYTES = (size_t)R * KC * 8;  // the next tile's window rows (FP64)
+  static constexpr size_t SMEM = A_BYTES + B_BYTES + Q_BYTES + 4 * (W + R);  // + column and row scales
 };
 
 template <int W>
@@ -271,11 +298,13 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __half* sA = (__half*)smem_raw;                         // R x KA, K-major
   __half* sB = (__half*)(smem_raw + U::A_BYTES);          // NB x KC, K-major
-  int* sScaleC = (int*)(smem_raw + U::A_BYTES + U::B_BYTES);  // W column scales of C, then R row scales
+  double* sQs = (double*)(smem_raw + U::A_BYTES + U::B_BYTES);  // R x KC staged window rows
+  int* sScaleC = (int*)(smem_raw + U::A_BYTES + U::B_BYTES + U::Q_BYTES);  // W column scales of C, then R row scales
   __shared__ uint64_t bar;
   __shared__ uint32_t tbase;
   __shared__ const double* colp[KC];  // column c of the window: pointer to row 0's entry
   __shared__ int cols[KC];            // and its row stride (block width)
+  __shared__ int staged;              // 1: window rows arrive by 16-byte cp.async
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // window columns
@@ -290,6 +319,11 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
     }
     colp[tid] = p;
     cols[tid] = w;
+  }
+  if (tid == 0) {  // every block 16-byte aligned with an even width: pairs of columns are 16-byte chunks
+    int okst = 1;
+    for (int j = 0; j < nq; j++) okst &= ((((uintptr_t)D[j].W) & 15) == 0) && ((D[j].w & 1) == 0);
+    staged = okst;
   }
   // C's column scales and digits: B[r W + b][a] = digit r of C[a][b] (r < 8),
   // zero for r = 8 and for a >= wtot
@@ -330,11 +364,27 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
   // slicing: thread (row = tid / 2, half = tid % 2) takes window columns
   // [16 half, 16 half + 16) of its row
   const int srow = tid >> 1, shalf = tid & 1;
+  const bool use_stage = staged != 0;
+  // the window rows of tile i: 16-byte chunks (row, column pair), 8 per thread
+  auto stage_tile = [&](int i) {
+    const int rb = r0 + i * R, nrr = min(R, r1 - rb);
+    for (int ch = tid; ch < R * (KC / 2); ch += blockDim.x) {
+      const int rr = ch / (KC / 2), c2 = 2 * (ch % (KC / 2));
+      const double* p = colp[c2];
+      if (p && rr < nrr) cp_async16(&sQs[rr * KC + c2], p + (long long)(rb + rr) * cols[c2]);
+    }
+    cp_async16_commit();
+  };
+  if (use_stage && ntiles > 0) stage_tile(0);
   bool ok = true;
   int it = 0;
   for (; it < ntiles && ok; it++) {
     const int row0 = r0 + it * R;
     const int nr = min(R, r1 - row0);
+    if (use_stage) {
+      cp_async16_wait();
+      __syncthreads();  // tile it is in sQs
+    }
     {
       const int grow = row0 + srow;
       double q[16];
@@ -343,7 +393,8 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
       for (int c = 0; c < 16; c++) {
         const int col = 16 * shalf + c;
         const double* p = colp[col];
-        q[c] = (p && srow < nr) ? p[(long long)grow * cols[col]] : 0.0;
+        if (use_stage) q[c] = (p && srow < nr) ? sQs[srow * KC + col] : 0.0;
+        else q[c] = (p && srow < nr) ? p[(long long)grow * cols[col]] : 0.0;
         smax = max(smax, bexp(q[c]));
       }
       smax = max(smax, __shfl_xor_sync(0xffffffffu, smax, 1));
@@ -359,13 +410,15 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
         sign_pair(q[c], q[c + 1], sg, of);
 #pragma unroll
         for (int p = 0; p < 8; p++)
-          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * KC + 16 * shalf + c, KA)]) = digit_pair(u0, u1, p, sg, of);
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * KC + 16 * shalf + c, KA)]) = digit_pair64(u0, u1, p, sg, of);
       }
       if (shalf == 0) sScaleC[W + srow] = smax;  // the row scale, for the epilogue
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
+    // every thread has read sQs: bring in the next tile while this one runs
+    if (use_stage && it + 1 < ntiles) stage_tile(it + 1);
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
@@ -392,13 +445,16 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
       const int row = 32 * (warp & 3) + lane;
       const int bq = 8 * (warp >> 2);
       float g[8][9];
+      {
+        uint32_t v[9][8];
 #pragma unroll
-      for (int gi = 0; gi < 9; gi++) {
-        uint32_t v[8];
-        tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(gi * W + bq), v);
+        for (int gi = 0; gi < 9; gi++)
+          tmem_ld8(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(gi * W + bq), v[gi]);
         tmem_wait_ld();
 #pragma unroll
-        for (int j = 0; j < 8; j++) g[j][gi] = __uint_as_float(v[j]);
+        for (int gi = 0; gi < 9; gi++)
+#pragma unroll
+          for (int j = 0; j < 8; j++) g[j][gi] = __uint_as_float(v[gi][j]);
       }
       const int Si = sScaleC[W + row];
       if (row < nr) {
@@ -427,6 +483,7 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
     // give the MMAs in flight a second bounded wait before the columns are freed
     mbar_wait_bounded(&bar, (uint32_t)(it & 1));
   }
+  cp_async16_wait();  // no copy may still be landing when the CTA exits
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
@@ -465,18 +522,20 @@ struct Digits<float> {
   __device__ static bool neg(float v) { return (__float_as_uint(v) >> 31) != 0u; }
 };
 
-// Digit pair (shift sh selects the digit) with the signs of two values.
-template <typename T>
-__device__ __forceinline__ uint32_t digit_pair_t(unsigned long long u0, unsigned long long u1, int sh, bool n0,
-                                                 bool n1) {
+// Signs of two values as the FP16 pair (sgn, off) that digit_pair_bytes
+// takes.
+__device__ __forceinline__ void sign_pair_b(bool n0, bool n1, __half2& sgn, __half2& off) {
   const __half one = __float2half(1.f), mone = __float2half(-1.f);
-  const __half a = n0 ? mone : one, b = n1 ? mone : one;
-  const __half2 sgn = __halves2half2(a, b);
-  const __half2 off = __halves2half2(__hmul(a, __float2half(-1024.f)), __hmul(b, __float2half(-1024.f)));
-  const uint32_t d0 = (uint32_t)(u0 >> sh) & 0xFFu, d1 = (uint32_t)(u1 >> sh) & 0xFFu;
-  const uint32_t raw = 0x64006400u | d0 | (d1 << 16);
-  const __half2 h = __hfma2(*reinterpret_cast<const __half2*>(&raw), sgn, off);
-  return *reinterpret_cast<const uint32_t*>(&h);
+  const __half m1024 = __float2half(-1024.f), p1024 = __float2half(1024.f);
+  sgn = __halves2half2(n0 ? mone : one, n1 ? mone : one);
+  off = __halves2half2(n0 ? p1024 : m1024, n1 ? p1024 : m1024);
+}
+// Digit p of two fractions of scalar type T (FP64: 64 bits, FP32: 24 bits).
+template <typename T>
+__device__ __forceinline__ uint32_t digit_pair_t(unsigned long long u0, unsigned long long u1, int p, __half2 sgn,
+                                                 __half2 off) {
+  if constexpr (sizeof(T) == 8) return digit_pair64(u0, u1, p, sgn, off);
+  else return digit_pair_bytes((uint32_t)u0, (uint32_t)u1, 2 - p, sgn, off);
 }
 
 // Per-CTA partial sums of C = [V_0 .. V_{nq-1}]^T B for a window of at most
@@ -520,6 +579,35 @@ __host__ __device__ constexpr bool tdot_tc_ok(int wcap) {
 
 // float holding an integer of magnitude below 2^24, to int (exact)
 __device__ __forceinline__ int f2i_exact(float f) { return __float2int_rn(f); }
+
+// The drain of one warp of k_tdot_tc holding digit P of 32 window columns
+// (lane = column a): for every b, T = sum_r D_{P r} 2^{8 (GMAX - P - r)}
+// over the kept pairs, as a 128-bit integer into part[(P KC + a) W + b].
+// P is a template argument so that every shift is a constant.
+template <typename T, int W, int P>
+__device__ __forceinline__ void tdot_drain(uint32_t base, long long* part, int lane) {
+  using Dg = Digits<T>;
+  constexpr int ND = Dg::ND, KC = 32;
+  constexpr int RMAX = (ND - 1 < Dg::GMAX - P) ? ND - 1 : Dg::GMAX - P;
+#pragma unroll
+  for (int bh = 0; bh < W / 8; bh++) {
+    uint32_t t[RMAX + 1][8];
+#pragma unroll
+    for (int r = 0; r <= RMAX; r++) tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t[r]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      long long hi = 0;
+      unsigned long long lo = 0;
+#pragma unroll
+      for (int r = 0; r <= RMAX; r++)
+        i128_add_shifted(hi, lo, (long long)f2i_exact(__uint_as_float(t[r][j])), 8 * (Dg::GMAX - P - r));
+      const int e = (P * KC + lane) * W + 8 * bh + j;
+      part[2 * e] = hi;
+      part[2 * e + 1] = (long long)lo;
+    }
+  }
+}
 
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
@@ -629,12 +717,12 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
       for (int j = 0; j < 8; j++) {
         const T a0 = vinf ? T(0) : v[j][0], a1 = vinf ? T(0) : v[j][1];
         const unsigned long long u0 = Dg::fixed(a0, Sv), u1 = Dg::fixed(a1, Sv);
-        const bool n0 = Dg::neg(a0), n1 = Dg::neg(a1);
+        __half2 sg, of;
+        sign_pair_b(Dg::neg(a0), Dg::neg(a1), sg, of);
         const int k = 2 * (vg + 8 * j);
 #pragma unroll
         for (int p = 0; p < ND; p++)
-          *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) =
-              digit_pair_t<T>(u0, u1, Dg::FB - 8 * (p + 1), n0, n1);
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) = digit_pair_t<T>(u0, u1, p, sg, of);
       }
       const bool xinf = sSx[xb] == Dg::EINF;
       const int Sx = xinf ? 0 : sSx[xb];
@@ -642,12 +730,12 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
       for (int j = 0; j < 4; j++) {
         const T b0 = xinf ? T(0) : x[j][0], b1 = xinf ? T(0) : x[j][1];
         const unsigned long long u0 = Dg::fixed(b0, Sx), u1 = Dg::fixed(b1, Sx);
-        const bool n0 = Dg::neg(b0), n1 = Dg::neg(b1);
+        __half2 sg, of;
+        sign_pair_b(Dg::neg(b0), Dg::neg(b1), sg, of);
         const int k = 2 * (xg + 16 * j);
 #pragma unroll
         for (int r = 0; r < ND; r++)
-          *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) =
-              digit_pair_t<T>(u0, u1, Dg::FB - 8 * (r + 1), n0, n1);
+          *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) = digit_pair_t<T>(u0, u1, r, sg, of);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -679,40 +767,26 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
     {
       const int region = warp >> 2, q = warp & 3;
       const int p = TWO ? 4 * region + q : (region == 0 ? q : ND);
-      const int rmax = min(ND - 1, Dg::GMAX - p);
       // the MMAs have completed (barrier above), so the A tile is free: the
       // 128-bit partials go there
       long long* part = reinterpret_cast<long long*>(smem_raw);
-      if (p < ND) {  // uniform over the warp
-        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
-#pragma unroll
-        for (int bh = 0; bh < W / 8; bh++) {
-          float d[ND][8];
-#pragma unroll
-          for (int r = 0; r < ND; r++) {
-            if (r <= rmax) {  // uniform over the warp
-              uint32_t t0[8];
-              tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t0);
-              tmem_wait_ld();
-#pragma unroll
-              for (int j = 0; j < 8; j++) d[r][j] = __uint_as_float(t0[j]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 8; j++) d[r][j] = 0.f;
+      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
+      switch (p) {  // uniform over the warp
+        case 0: tdot_drain<T, W, 0>(base, part, lane); break;
+        case 1: tdot_drain<T, W, 1>(base, part, lane); break;
+        case 2: tdot_drain<T, W, 2>(base, part, lane); break;
+        default:
+          if constexpr (ND > 3) {
+            switch (p) {
+              case 3: tdot_drain<T, W, 3>(base, part, lane); break;
+              case 4: tdot_drain<T, W, 4>(base, part, lane); break;
+              case 5: tdot_drain<T, W, 5>(base, part, lane); break;
+              case 6: tdot_drain<T, W, 6>(base, part, lane); break;
+              case 7: tdot_drain<T, W, 7>(base, part, lane); break;
+              default: break;
             }
           }
-#pragma unroll
-          for (int j = 0; j < 8; j++) {
-            long long hi = 0;
-            unsigned long long lo = 0;
-#pragma unroll
-            for (int r = 0; r < ND; r++)
-              if (r <= rmax) i128_add_shifted(hi, lo, (long long)f2i_exact(d[r][j]), 8 * (Dg::GMAX - p - r));
-            const int e = (p * KC + lane) * W + 8 * bh + j;
-            part[2 * e] = hi;
-            part[2 * e + 1] = (long long)lo;
-          }
-        }
+          break;
       }
     }
     tc_fence_before();
@@ -779,7 +853,8 @@ struct FinTc {
   static constexpr uint32_t TCOLS = 256;
   static constexpr size_t A_BYTES = (size_t)R * KA * 2;  // one of A_X, A_Y
   static constexpr size_t B_BYTES = (size_t)NB * W * 2;
-  static constexpr size_t SMEM = 2 * A_BYTES + B_BYTES + 4 * (W + 2 * R) + 8 * (2 * W);
+  static constexpr size_t S_BYTES = (size_t)2 * R * W * 8;  // the next tile's X and Y rows (FP64)
+  static constexpr size_t SMEM = 2 * A_BYTES + B_BYTES + S_BYTES + 4 * (W + 2 * R) + 8 * (2 * W);
 };
 
 template <int W>
@@ -809,7 +884,8 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
   __half* sAX = (__half*)smem_raw;                                 // R x KA
   __half* sAY = (__half*)(smem_raw + U::A_BYTES);                  // R x KA
   __half* sB = (__half*)(smem_raw + 2 * U::A_BYTES);               // NB x W
-  int* sSc = (int*)(smem_raw + 2 * U::A_BYTES + U::B_BYTES);       // W column scales of R^{-1}
+  double* sXs = (double*)(smem_raw + 2 * U::A_BYTES + U::B_BYTES);  // R x W staged X rows, then R x W Y rows
+  int* sSc = (int*)(smem_raw + 2 * U::A_BYTES + U::B_BYTES + U::S_BYTES);  // W column scales of R^{-1}
   int* sSr = sSc + W;                                               // 2 R row scales (X rows, Y rows)
   double* sal = (double*)(sSr + 2 * R);                             // W: alpha
   double* sbeta = sal + W;                                          // W: beta partial sums
@@ -852,6 +928,19 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
   const int ntiles = (r1 - r0 + R - 1) / R;
   // slicing: thread (row = tid / 2, which = tid % 2) takes the X (0) or Y (1) row
   const int srow = tid >> 1, which = tid & 1;
+  // X and Y rows arrive by 16-byte cp.async one tile ahead when both blocks
+  // are 16-byte aligned (their rows are 128 bytes)
+  const bool use_stage = ((((uintptr_t)Xin) | ((uintptr_t)Yin)) & 15) == 0;
+  auto stage_tile = [&](int i) {
+    const int rb = r0 + i * R, nrr = min(R, r1 - rb);
+    for (int ch = tid; ch < 2 * R * (W / 2); ch += blockDim.x) {
+      const int y = ch / (R * (W / 2)), e = ch % (R * (W / 2));
+      const int rr = e / (W / 2), c2 = 2 * (e % (W / 2));
+      if (rr < nrr) cp_async16(&sXs[(y * R + rr) * W + c2], (y ? Yin : Xin) + (long long)(rb + rr) * W + c2);
+    }
+    cp_async16_commit();
+  };
+  if (use_stage && ntiles > 0) stage_tile(0);
   // epilogue: warp w reads rows 32 (w % 4) + lane of X's (w < 4) or Y's groups
   const int erow = 32 * (warp & 3) + lane, ey = warp >> 2;
   double rho_acc = 0.0;
@@ -863,6 +952,10 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
   for (; it < ntiles && ok; it++) {
     const int row0 = r0 + it * R;
     const int nr = min(R, r1 - row0);
+    if (use_stage) {
+      cp_async16_wait();
+      __syncthreads();  // tile it is in sXs
+    }
     {
       const double* src = which ? Yin : Xin;
       __half* sA = which ? sAY : sAX;
@@ -870,7 +963,8 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
       int smax = 0;
 #pragma unroll
       for (int c = 0; c < W; c++) {
-        q[c] = (srow < nr) ? src[(long long)(row0 + srow) * W + c] : 0.0;
+        if (use_stage) q[c] = (srow < nr) ? sXs[(which * R + srow) * W + c] : 0.0;
+        else q[c] = (srow < nr) ? src[(long long)(row0 + srow) * W + c] : 0.0;
         smax = max(smax, bexp(q[c]));
       }
       if (smax == 2047) {
@@ -885,13 +979,14 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
         sign_pair(q[c], q[c + 1], sg, of);
 #pragma unroll
         for (int p = 0; p < 8; p++)
-          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * W + c, KA)]) = digit_pair(u0, u1, p, sg, of);
+          *reinterpret_cast<uint32_t*>(&sA[kmaj(srow, p * W + c, KA)]) = digit_pair64(u0, u1, p, sg, of);
       }
       sSr[which * R + srow] = smax;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
     __syncthreads();
+    if (use_stage && it + 1 < ntiles) stage_tile(it + 1);  // every thread has read sXs
     if (tid == 0) {
       tc_fence_after();
       const uint32_t b0 = smem_u32(sB);
@@ -972,6 +1067,7 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
     ((DevState*)st)->stop = 1;
     mbar_wait_bounded(&bar, (uint32_t)(it & 1));
   }
+  cp_async16_wait();  // no copy may still be landing when the CTA exits
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
