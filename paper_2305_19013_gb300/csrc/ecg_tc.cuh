@@ -371,7 +371,9 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
     for (int ch = tid; ch < R * (KC / 2); ch += blockDim.x) {
       const int rr = ch / (KC / 2), c2 = 2 * (ch % (KC / 2));
       const double* p = colp[c2];
-      if (p && rr < nrr) cp_async16(&sQs[rr * KC + c2], p + (long long)(rb + rr) * cols[c2]);
+      // 16-byte chunk c2 / 2 of row rr lands at chunk (c2 / 2) ^ (rr % 16): the
+      // slicing threads of a warp (16 rows) then read distinct bank groups
+      if (p && rr < nrr) cp_async16(&sQs[rr * KC + 2 * ((c2 >> 1) ^ (rr & 15))], p + (long long)(rb + rr) * cols[c2]);
     }
     cp_async16_commit();
   };
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(256, 2) k_update_tc(KP P, int gw, double* Xio,
       for (int c = 0; c < 16; c++) {
         const int col = 16 * shalf + c;
         const double* p = colp[col];
-        if (use_stage) q[c] = (p && srow < nr) ? sQs[srow * KC + col] : 0.0;
+        if (use_stage) q[c] = (p && srow < nr) ? sQs[srow * KC + 2 * ((col >> 1) ^ (srow & 15)) + (col & 1)] : 0.0;
         else q[c] = (p && srow < nr) ? p[(long long)grow * cols[col]] : 0.0;
         smax = max(smax, bexp(q[c]));
       }
@@ -538,6 +540,18 @@ __device__ __forceinline__ uint32_t digit_pair_t(unsigned long long u0, unsigned
   else return digit_pair_bytes((uint32_t)u0, (uint32_t)u1, 2 - p, sgn, off);
 }
 
+// Digit pairs (p, r) kept by k_tdot_tc, numbered p by p: slot(p, r) =
+// first(p) + r for r <= rmax(p) = min(ND - 1, GMAX - p).
+template <typename T>
+struct PairSlots {
+  using Dg = Digits<T>;
+  static constexpr __host__ __device__ int rmax(int p) {
+    return (Dg::ND - 1 < Dg::GMAX - p) ? Dg::ND - 1 : Dg::GMAX - p;
+  }
+  static constexpr __host__ __device__ int first(int p) { return p == 0 ? 0 : first(p - 1) + rmax(p - 1) + 1; }
+  static constexpr int COUNT = first(Dg::ND);
+};
+
 // Per-CTA partial sums of C = [V_0 .. V_{nq-1}]^T B for a window of at most
 // 32 columns and W = 16, over the CTA's rows, into the partial-sum layout of
 // k_tdot_window (reduced by k_reduce_C).  128-row tiles are the MMA's K.
@@ -560,10 +574,11 @@ struct TdotTc {
   static constexpr uint32_t TCOLS = (ND * KC > 128) ? 256u : 64u;
   static constexpr size_t A_BYTES = (size_t)MA * R * 2;
   static constexpr size_t B_BYTES = (size_t)NB * R * 2;
-  // the per-(p, a, b) 128-bit partials reuse the A tile once the MMAs are done
-  static constexpr size_t PART_BYTES = (size_t)ND * KC * W * 16;
+  // the int32 digit-pair sums, one slot per kept pair (p, r) and output
+  // (b, a), reuse the A and B tiles once the MMAs are done
+  static constexpr size_t PART_BYTES = (size_t)PairSlots<T>::COUNT * KC * W * 4;
   static constexpr size_t SMEM = A_BYTES + B_BYTES + 4 * (KC + W);
-  static_assert(PART_BYTES <= A_BYTES, "partials alias the A tile");
+  static_assert(PART_BYTES <= A_BYTES + B_BYTES, "pair sums alias the A and B tiles");
   static_assert(NB + (ND * KC > 128 ? N2 : 0) <= (int)TCOLS, "accumulator columns");
 };
 
@@ -579,35 +594,6 @@ __host__ __device__ constexpr bool tdot_tc_ok(int wcap) {
 
 // float holding an integer of magnitude below 2^24, to int (exact)
 __device__ __forceinline__ int f2i_exact(float f) { return __float2int_rn(f); }
-
-// The drain of one warp of k_tdot_tc holding digit P of 32 window columns
-// (lane = column a): for every b, T = sum_r D_{P r} 2^{8 (GMAX - P - r)}
-// over the kept pairs, as a 128-bit integer into part[(P KC + a) W + b].
-// P is a template argument so that every shift is a constant.
-template <typename T, int W, int P>
-__device__ __forceinline__ void tdot_drain(uint32_t base, long long* part, int lane) {
-  using Dg = Digits<T>;
-  constexpr int ND = Dg::ND, KC = 32;
-  constexpr int RMAX = (ND - 1 < Dg::GMAX - P) ? ND - 1 : Dg::GMAX - P;
-#pragma unroll
-  for (int bh = 0; bh < W / 8; bh++) {
-    uint32_t t[RMAX + 1][8];
-#pragma unroll
-    for (int r = 0; r <= RMAX; r++) tmem_ld8(base + (uint32_t)(r * W + 8 * bh), t[r]);
-    tmem_wait_ld();
-#pragma unroll
-    for (int j = 0; j < 8; j++) {
-      long long hi = 0;
-      unsigned long long lo = 0;
-#pragma unroll
-      for (int r = 0; r <= RMAX; r++)
-        i128_add_shifted(hi, lo, (long long)f2i_exact(__uint_as_float(t[r][j])), 8 * (Dg::GMAX - P - r));
-      const int e = (P * KC + lane) * W + 8 * bh + j;
-      part[2 * e] = hi;
-      part[2 * e + 1] = (long long)lo;
-    }
-  }
-}
 
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
@@ -669,10 +655,15 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
   int r0, r1;
   cta_rows_aligned(P.n, R, r0, r1);
   const int ntiles = (r1 - r0 + R - 1) / R;
-  // loading: V column va = lane, row pairs vg + 8 j (vg = warp); B column
-  // xb = tid % 16, row pairs xg + 16 j (xg = tid / 16)
-  const int va = lane, vg = warp, xb = tid & 15, xg = tid >> 4;
-  // outputs of this thread: (a, b) = (tid / 16, tid % 16) and (tid / 16 + 16, tid % 16)
+  // loading and slicing.  V: column va = tid % 8 + 8 (warp % 4), row pairs
+  // kp = (tid / 8) % 4 + 4 (warp / 4 + 2 j), j < 8; B: column xb = tid % 8 +
+  // 8 (warp % 2), row pairs (tid / 8) % 4 + 4 (warp / 2 + 4 j), j < 4.  A
+  // warp then covers 8 columns x 4 row pairs, and its 32 digit-pair stores
+  // hit 32 different banks of the K-major core matrices.
+  const int kpl = (tid >> 3) & 3;
+  const int va = (tid & 7) + 8 * (warp & 3), vg = warp >> 2;
+  const int xb = (tid & 7) + 8 * (warp & 1), xg = warp >> 1;
+  // outputs of this thread: (a, b) = (tid % 32, tid / 32) and (tid % 32, tid / 32 + 8)
   double acc0 = 0.0, acc1 = 0.0;
   bool ok = true;
   int it = 0;
@@ -688,26 +679,30 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
       int mx = 0;
 #pragma unroll
       for (int j = 0; j < 8; j++) {
-        const int rr = 2 * (vg + 8 * j);
+        const int rr = 2 * (kpl + 4 * (vg + 2 * j));
 #pragma unroll
         for (int u = 0; u < 2; u++) {
           v[j][u] = (p && rr + u < nr) ? p[(long long)(row0 + rr + u) * cs] : T(0);
           mx = max(mx, Dg::bexp(v[j][u]));
         }
       }
-      atomicMax(&sSv[va], mx);
+      // lanes with the same column differ in bits 3 and 4
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+      if (kpl == 0) atomicMax(&sSv[va], mx);
       int mb = 0;
 #pragma unroll
       for (int j = 0; j < 4; j++) {
-        const int rr = 2 * (xg + 16 * j);
+        const int rr = 2 * (kpl + 4 * (xg + 4 * j));
 #pragma unroll
         for (int u = 0; u < 2; u++) {
           x[j][u] = (rr + u < nr) ? B[(long long)(row0 + rr + u) * W + xb] : T(0);
           mb = max(mb, Dg::bexp(x[j][u]));
         }
       }
+      mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 8));
       mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, 16));
-      if (lane < 16) atomicMax(&sSx[xb], mb);
+      if (kpl == 0) atomicMax(&sSx[xb], mb);
     }
     __syncthreads();
     {
@@ -719,7 +714,7 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
         const unsigned long long u0 = Dg::fixed(a0, Sv), u1 = Dg::fixed(a1, Sv);
         __half2 sg, of;
         sign_pair_b(Dg::neg(a0), Dg::neg(a1), sg, of);
-        const int k = 2 * (vg + 8 * j);
+        const int k = 2 * (kpl + 4 * (vg + 2 * j));
 #pragma unroll
         for (int p = 0; p < ND; p++)
           *reinterpret_cast<uint32_t*>(&sA[kmaj(p * KC + va, k, R)]) = digit_pair_t<T>(u0, u1, p, sg, of);
@@ -732,7 +727,7 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
         const unsigned long long u0 = Dg::fixed(b0, Sx), u1 = Dg::fixed(b1, Sx);
         __half2 sg, of;
         sign_pair_b(Dg::neg(b0), Dg::neg(b1), sg, of);
-        const int k = 2 * (xg + 16 * j);
+        const int k = 2 * (kpl + 4 * (xg + 4 * j));
 #pragma unroll
         for (int r = 0; r < ND; r++)
           *reinterpret_cast<uint32_t*>(&sB[kmaj(r * W + xb, k, R)]) = digit_pair_t<T>(u0, u1, r, sg, of);
@@ -762,31 +757,28 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
     if (!ok) break;
     tc_fence_after();
     // drain: warp w holds digit p = 4 (w / 4) + w % 4 (FP64; FP32: p = w for
-    // w < 3) of window column a = lane; it combines its digit pairs (p, r)
-    // per b into 128-bit integers T = sum_r D_{p r} 2^{8 (GMAX - p - r)}
+    // w < 3) of window column a = lane; every kept digit-pair sum D_{p r}[a][b]
+    // (an exact integer below 2^23) goes to its int32 slot
     {
       const int region = warp >> 2, q = warp & 3;
       const int p = TWO ? 4 * region + q : (region == 0 ? q : ND);
-      // the MMAs have completed (barrier above), so the A tile is free: the
-      // 128-bit partials go there
-      long long* part = reinterpret_cast<long long*>(smem_raw);
-      const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
-      switch (p) {  // uniform over the warp
-        case 0: tdot_drain<T, W, 0>(base, part, lane); break;
-        case 1: tdot_drain<T, W, 1>(base, part, lane); break;
-        case 2: tdot_drain<T, W, 2>(base, part, lane); break;
-        default:
-          if constexpr (ND > 3) {
-            switch (p) {
-              case 3: tdot_drain<T, W, 3>(base, part, lane); break;
-              case 4: tdot_drain<T, W, 4>(base, part, lane); break;
-              case 5: tdot_drain<T, W, 5>(base, part, lane); break;
-              case 6: tdot_drain<T, W, 6>(base, part, lane); break;
-              case 7: tdot_drain<T, W, 7>(base, part, lane); break;
-              default: break;
-            }
+      // the MMAs have completed (barrier above): the A and B tiles are free
+      int* slots = reinterpret_cast<int*>(smem_raw);
+      if (p < ND) {  // uniform over the warp
+        const int rmax = PairSlots<T>::rmax(p), s0 = PairSlots<T>::first(p);
+        const uint32_t base = tmem + ((uint32_t)(32 * q) << 16) + (region ? (uint32_t)NB : 0u);
+        for (int r = 0; r <= rmax; r++) {
+          uint32_t t0[8], t1[8];
+          tmem_ld8(base + (uint32_t)(r * W), t0);
+          tmem_ld8(base + (uint32_t)(r * W + 8), t1);
+          tmem_wait_ld();
+          int* dst = slots + (s0 + r) * (KC * W) + lane;  // [slot][b][a]
+#pragma unroll
+          for (int j = 0; j < 8; j++) {
+            dst[j * KC] = f2i_exact(__uint_as_float(t0[j]));
+            dst[(8 + j) * KC] = f2i_exact(__uint_as_float(t1[j]));
           }
-          break;
+        }
       }
     }
     tc_fence_before();
@@ -794,17 +786,23 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
     {
 #pragma unroll
       for (int h = 0; h < 2; h++) {
-        const int a = (tid >> 4) + 16 * h, b = tid & 15;
+        // output (a, b) = (tid % 32, tid / 32 + 8 h): a warp reads 32 consecutive slots
+        const int a = tid & 31, b = (tid >> 5) + 8 * h;
+        const int* slots = reinterpret_cast<const int*>(smem_raw);
+        // group sums in int32 (at most 8 pairs x 2^23 < 2^31), then one
+        // 128-bit combine T = sum_g G_g 2^{8 (GMAX - g)}
+        int G[Dg::GMAX + 1];
+#pragma unroll
+        for (int g = 0; g <= Dg::GMAX; g++) G[g] = 0;
+#pragma unroll
+        for (int p = 0; p < ND; p++)
+#pragma unroll
+          for (int r = 0; r <= PairSlots<T>::rmax(p); r++)
+            G[p + r] += slots[(PairSlots<T>::first(p) + r) * (KC * W) + b * KC + a];
         long long hi = 0;
         unsigned long long lo = 0;
-        const long long* part = reinterpret_cast<const long long*>(smem_raw);
-        for (int p = 0; p < ND; p++) {
-          const int e = (p * KC + a) * W + b;
-          const unsigned long long l2 = (unsigned long long)part[2 * e + 1];
-          const unsigned long long s2 = lo + l2;
-          hi += part[2 * e] + (s2 < lo ? 1ll : 0ll);
-          lo = s2;
-        }
+#pragma unroll
+        for (int g = 0; g <= Dg::GMAX; g++) i128_add_shifted(hi, lo, (long long)G[g], 8 * (Dg::GMAX - g));
         double val;
         if (sSv[a] == Dg::EINF || sSx[b] == Dg::EINF) val = __longlong_as_double(0x7FF8000000000000ll);
         else val = i128_to_double(hi, lo, (sSv[a] - Dg::BIAS) + (sSx[b] - Dg::BIAS) - 8 * (Dg::GMAX + 2));
@@ -825,9 +823,11 @@ __global__ void __launch_bounds__(256, 2) k_tdot_tc(KP P, int gw, const T* B) {
   if (warp == 0) tmem_dealloc(tmem, U::TCOLS);
   if (!ok) return;
   double* out = P.part_buf + (long long)blockIdx.x * (kChunk * W);
-  const int a0 = tid >> 4, b = tid & 15;
-  if (a0 < wtot) out[a0 * W + b] = acc0;
-  if (a0 + 16 < wtot) out[(a0 + 16) * W + b] = acc1;
+  const int a0 = tid & 31, b0 = tid >> 5;
+  if (a0 < wtot) {
+    out[a0 * W + b0] = acc0;
+    out[a0 * W + b0 + 8] = acc1;
+  }
 }
 
 // ------------------------------------------------------------ final update
@@ -936,7 +936,9 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
     for (int ch = tid; ch < 2 * R * (W / 2); ch += blockDim.x) {
       const int y = ch / (R * (W / 2)), e = ch % (R * (W / 2));
       const int rr = e / (W / 2), c2 = 2 * (e % (W / 2));
-      if (rr < nrr) cp_async16(&sXs[(y * R + rr) * W + c2], (y ? Yin : Xin) + (long long)(rb + rr) * W + c2);
+      // chunk c2 / 2 of a row lands at chunk (c2 / 2) ^ (rr % 8) (bank groups)
+      if (rr < nrr)
+        cp_async16(&sXs[(y * R + rr) * W + 2 * ((c2 >> 1) ^ (rr & 7))], (y ? Yin : Xin) + (long long)(rb + rr) * W + c2);
     }
     cp_async16_commit();
   };
@@ -963,7 +965,7 @@ __global__ void __launch_bounds__(256, 2) k_final_tc(KP P, int gw, const double*
       int smax = 0;
 #pragma unroll
       for (int c = 0; c < W; c++) {
-        if (use_stage) q[c] = (srow < nr) ? sXs[(which * R + srow) * W + c] : 0.0;
+        if (use_stage) q[c] = (srow < nr) ? sXs[(which * R + srow) * W + 2 * ((c >> 1) ^ (srow & 7)) + (c & 1)] : 0.0;
         else q[c] = (srow < nr) ? src[(long long)(row0 + srow) * W + c] : 0.0;
         smax = max(smax, bexp(q[c]));
       }
