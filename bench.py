@@ -51,16 +51,19 @@ UNIT = "iterations/s"
 WORKLOAD = "diffusion2d_1024_t16"
 # FP64 peak of a GB300: 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one full-window launch of the dominant kernel
-# classes, from one ncu capture of the kernels as they stand
-# (profiles/k_tdot_window_16_diffusion2d_1024_t16.md), n = 1,048,576, t = 16,
-# window of 2 blocks.  Any other shape reports null.
-# DRAM bytes (read + write) per launch, averaged over the two CGS passes of
-# one iteration, from one ncu capture of the current kernels (the first pass
-# of an SRE iteration reads V_{k-1} as both a window block and the block)
+# DRAM bytes (read + write) per full-window launch of a kernel class, averaged
+# over the two CGS passes of one iteration (the first pass of an SRE
+# iteration reads V_{k-1} as both a window block and the block), from one ncu
+# capture of the kernels as they stand; n = 1,048,576, t = 16, window of 2
+# blocks.  Any other shape reports null.
 MEASURED_TRAFFIC = {
+    # CUDA-core kernels (--no-tensor-cores)
     ("cgs_tdot", 16, 2, "alu"): ((268.72e6 + 3.75e6) + (402.95e6 + 4.84e6)) / 2,
     ("cgs_update", 16, 2, "alu"): ((403.09e6 + 115.24e6) + (403.00e6 + 108.42e6)) / 2,
+    # tensor-core kernels (profiles/cgs_final_tc_kernels_diffusion2d_1024_t16.md)
+    ("cgs_tdot", 16, 2, "hbm"): ((268.50e6 + 4.38e6) + (402.86e6 + 4.42e6)) / 2,
+    ("cgs_update", 16, 2, "hbm"): ((407.02e6 + 113.51e6) + (402.75e6 + 99.93e6)) / 2,
+    ("final", 16, 2, "alu"): 287.18e6 + 236.88e6,
 }
 
 
@@ -378,6 +381,49 @@ def time_to_tol_runs(torch, p, stream, args, names):
     return out
 
 
+def other_configs_run(torch, stream, args, K=20):
+    """The other workloads of the measurement plan, each at its full size:
+    the 1024 x 1024 diffusion system with t = 8 and t = 32, and the 3D
+    anisotropic 128^3 system with t = 16 (SRE-CG, trunc 2, Pre-CholQR).
+    Per workload: FP64 iterations/s over K full-window iterations (as the
+    headline value), and time to 1e-8 with the block Jacobi IC(0)
+    preconditioner on 64 blocks, FP64 and mixed precision."""
+    from paper_2305_19013_gb300 import ecg
+    from paper_2305_19013_gb300 import workloads as Wk
+
+    cases = [
+        ("diffusion2d_1024_t8", lambda: Wk.blocky_diffusion2d(1024, 8, blocks=16, seed=2001)),
+        ("diffusion2d_1024_t32", lambda: Wk.blocky_diffusion2d(1024, 32, blocks=16, seed=2001)),
+        ("aniso3d_128_t16", lambda: Wk.anisotropic_diffusion3d(128, 16, seed=3000)),
+    ]
+    out = {}
+    for name, make in cases:
+        p = make()
+        b_dev = torch.from_numpy(p.b).cuda()
+        x_dev = torch.empty_like(b_dev)
+        entry = {"n": p.n, "nnz": p.nnz, "t": p.t}
+        with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, tensor_cores=args.tensor_cores,
+                                     stream=stream.cuda_stream) as sv:
+            sv.solve(b_dev, tol=0.0, maxit=4, x_out=x_dev)
+            ms, _, _, _ = full_window_ms(sv, b_dev, x_dev, K, args.trunc, stream, lambda: None, torch)
+            entry["fp64_iterations_per_s"] = K / (ms / 1000.0)
+            entry["fp64_ms_per_iteration"] = ms / K
+        pb = Wk.jacobi_blocks(p, args.prec_blocks)
+        for label, prec in (("fp64", ecg.FP64), ("mixed", ecg.MIXED)):
+            with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=prec,
+                                         tensor_cores=args.tensor_cores, stream=stream.cuda_stream) as sv:
+                sv.set_preconditioner(pb, args.prec_blocks)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = sv.solve(b_dev, tol=1e-8, maxit=args.time_to_tol_maxit, x_out=x_dev, raise_on_error=False)
+                torch.cuda.synchronize()
+                entry[f"time_to_tol_{label}_ic0_{args.prec_blocks}"] = {
+                    "seconds": time.perf_counter() - t0, "iters": r.iters, "status": r.status,
+                    "relres_true": r.relres_true}
+        out[name] = entry
+    return out
+
+
 def full_window_ms(solver, b_dev, x_dev, K, trunc, stream, barrier, torch):
     """CUDA-event time of K full-window iterations: a solve of trunc + K
     iterations minus a solve of trunc iterations, each bracketed by a barrier
@@ -418,6 +464,8 @@ def main():
     ap.add_argument("--time-to-tol-all", action="store_true",
                     help="also run mixed precision without a preconditioner (it stalls on this problem)")
     ap.add_argument("--prec-blocks", type=int, default=64, help="block Jacobi blocks for the preconditioned runs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other workloads (t = 8, t = 32, the 3D anisotropic system)")
     ap.add_argument("--warmstart", action="store_true",
                     help="also train the warm-start network on GRF diffusion problems and compare solves")
     ap.add_argument("--batch", action="store_true",
@@ -597,6 +645,8 @@ def main():
         if args.time_to_tol_all:
             names.insert(1, "mixed")
         line["time_to_tol"] = time_to_tol_runs(torch, p, stream, args, names)
+    if world == 1 and not args.no_configs:
+        line["other_configs"] = other_configs_run(torch, stream, args)
     if args.batch:
         line["batch"] = batch_run(torch)
     if args.warmstart:

@@ -142,3 +142,52 @@ def test_fullsize_batched_systems_fp64():
     for p, g, r in zip(ps, res, ms):
         assert g.status == ecg.OK and g.relres <= 1e-8
         envelope_assert(r, g.iters)
+
+
+@pytest.fixture(scope="module")
+def aniso3d():
+    return W.anisotropic_diffusion3d(128, 16, seed=3000)
+
+
+def test_fullsize_3d_first_iterations(aniso3d):
+    """The 3D anisotropic workload at full size (128^3 = 2,097,152 rows,
+    t = 16 as 4 x 2 x 2 boxes, SRE-CG): the first five iterates of the GPU
+    (tensor-core CGS and final products) equal the oracle's to 1e-10."""
+    p = aniso3d
+    o = O.ecg_solve(p.scipy(), p.part, 16, p.b, tol=0.0, maxit=6, trunc=2)
+    with ecg.Solver.from_problem(p, trunc=2) as s:
+        g = s.solve(dev(p.b), tol=0.0, maxit=6)
+        xg = g.x.cpu().numpy()
+    report("fullsize_3d_first_iterations", n=p.n, iters=g.iters, x_rel_err=rel(xg, o.x),
+           hist_dev_over_rho0=float(np.max(np.abs(g.history - o.history)) / o.history[0]))
+    assert g.iters == o.iters == 5
+    assert rel(xg, o.x) < 1e-10
+    assert np.all(np.abs(g.history - o.history) <= 1e-10 * o.history[0])
+
+
+def test_fullsize_3d_ic0_solve_to_tolerance(aniso3d):
+    """The 3D workload with the block Jacobi IC(0) preconditioner on 64
+    boxes, solved to 1e-8 in FP64 and in mixed precision; FP64 against the
+    oracle's iteration count (within 1% and +-2), x within 1e-7 of the
+    oracle's; mixed precision meets the FP64 tolerance on the true
+    residual."""
+    p = aniso3d
+    A = p.scipy()
+    pb = W.jacobi_blocks(p, 64)
+    pc = O.BlockJacobi(A, pb, 64, O.PREC_IC0)
+    o = O.ecg_solve(A, p.part, 16, p.b, tol=1e-8, maxit=3000, trunc=2, prec=pc)
+    res = {}
+    for prec in (ecg.FP64, ecg.MIXED):
+        with ecg.Solver.from_problem(p, trunc=2, precision=prec) as s:
+            s.set_preconditioner(pb, 64)
+            g = s.solve(dev(p.b), tol=1e-8, maxit=20000)
+            res[prec] = (g, g.x.cpu().numpy())
+    g, xg = res[ecg.FP64]
+    gm, xm = res[ecg.MIXED]
+    report("fullsize_3d_ic0_to_1e-8", n=p.n, gpu_iters=g.iters, oracle_iters=o.iters, iters_delta=g.iters - o.iters,
+           x_rel_err=rel(xg, o.x), mixed_iters=gm.iters, mixed_relres_true=gm.relres_true,
+           mixed_x_rel_err=rel(xm, o.x))
+    assert o.status == 0 and g.status == ecg.OK and gm.status == ecg.OK
+    assert abs(g.iters - o.iters) <= max(2, -(-o.iters // 100))
+    assert rel(xg, o.x) < 1e-7
+    assert gm.relres_true <= 1e-8
