@@ -424,6 +424,30 @@ def other_configs_run(torch, stream, args, K=20):
     return out
 
 
+def mixed_profile(torch, p, stream, args, K=40):
+    """Per-class device time of the mixed method's FP32 inner iterations on
+    the headline system (K inner iterations, tol = 0, CUDA events around each
+    kernel class), with the FP32 CGS coefficient Grams on the tensor cores
+    and on CUDA cores."""
+    from paper_2305_19013_gb300 import ecg
+
+    b_dev = torch.from_numpy(p.b).cuda()
+    out = {}
+    for tcores in (True, False):
+        with ecg.Solver.from_problem(p, trunc=args.trunc, ortho=args.ortho, precision=ecg.MIXED,
+                                     tensor_cores=tcores, stream=stream.cuda_stream) as sv:
+            sv.solve(b_dev, tol=0.0, maxit=6)
+            sv.profile(True)
+            r = sv.solve(b_dev, tol=0.0, maxit=K + 1)
+            prof = sv.profile_read()
+            sv.profile(False)
+        tot = sum(v[0] for v in prof.values())
+        out["tensor_cores" if tcores else "cuda_cores"] = {
+            "inner_iterations": r.iters, "ms_per_inner_iteration": tot / max(r.iters, 1),
+            "profile_ms": {k: round(v[0], 3) for k, v in prof.items() if v[1]}}
+    return out
+
+
 def full_window_ms(solver, b_dev, x_dev, K, trunc, stream, barrier, torch):
     """CUDA-event time of K full-window iterations: a solve of trunc + K
     iterations minus a solve of trunc iterations, each bracketed by a barrier
@@ -646,6 +670,7 @@ def main():
             names.insert(1, "mixed")
         line["time_to_tol"] = time_to_tol_runs(torch, p, stream, args, names)
     if world == 1 and not args.no_configs:
+        line["mixed_inner_profile"] = mixed_profile(torch, p, stream, args)
         line["other_configs"] = other_configs_run(torch, stream, args)
     if args.batch:
         line["batch"] = batch_run(torch)
