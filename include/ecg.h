@@ -113,12 +113,15 @@ typedef struct {
                            x_k = x_0 + X_k 1 and rho_k = ||R_k 1||.  SRE-CG2
                            directions, FP64, no switch, restart or
                            preconditioner (ECG_EINVAL otherwise) */
-  int tensor_cores;     /* 1 (default): the FP64 CGS update W -= Q C runs on
-                           the tensor cores (exact digit products, FP64
-                           result) when the block width is 16 and the window
-                           has at most 32 columns; 0: always on CUDA-core FP64
-                           FMAs.  Not a choice of the paper: both compute the
-                           same FP64 product up to rounding */
+  int tensor_cores;     /* 1 (default): the FP64 CGS products (W -= Q C,
+                           C = V^T W) and the final transforms W R^{-1},
+                           Y R^{-1} run on the tensor cores (exact digit
+                           products, FP64 results) when the block width is 16
+                           and the window has at most 32 columns; 2: also the
+                           CGS coefficient Grams of the mixed method's FP32
+                           inner solves; 0: CUDA-core FMAs throughout.  Not a
+                           choice of the paper: all compute the same products
+                           up to rounding */
   void* stream;      /* cudaStream_t for all work; NULL: a stream the
                         context creates */
 } ecg_opts;

@@ -534,7 +534,10 @@ void launch_update(ecg_ctx* c, const KP& P, T* X, const double* Cin, int wmax, i
 template <typename T, int W>
 void launch_tdot(ecg_ctx* c, const KP& P, const T* B, double* Cout, int wmax, int gy, int gxw) {
   if constexpr (tc::tdot_tc_ok<T, W>(32)) {
-    if (c->opts.tensor_cores && tc::tdot_tc_ok<T, W>(wmax) && gy == 1) {
+    // FP64 with tensor_cores >= 1; the FP32 Grams of the mixed method only
+    // with tensor_cores == 2 (slower than the CUDA-core FP32 kernel here)
+    const bool want = sizeof(T) == 8 ? c->opts.tensor_cores >= 1 : c->opts.tensor_cores == 2;
+    if (want && tc::tdot_tc_ok<T, W>(wmax) && gy == 1) {
       const int g = tc_grid(c);
       tc::k_tdot_tc<T, W><<<g, 256, tc::smem_tdot_tc<T, W>(), c->stream>>>(P, W, B);
       k_reduce_C<W><<<dim3((kChunk * W * 32 + kThreads - 1) / kThreads, 1), kThreads, 0, c->stream>>>(P, W, g, Cout);
@@ -819,7 +822,7 @@ int validate_opts(const ecg_opts* o, int t) {
   if (o->restart_at_switch && !(o->switch_tol > 0.0)) return ECG_EINVAL;
   if (o->block_residual != 0 && o->block_residual != 1) return ECG_EINVAL;
   if (o->stop_rule != ECG_STOP_R0 && o->stop_rule != ECG_STOP_B) return ECG_EINVAL;
-  if (o->tensor_cores != 0 && o->tensor_cores != 1) return ECG_EINVAL;
+  if (o->tensor_cores < 0 || o->tensor_cores > 2) return ECG_EINVAL;
   if (o->block_residual && (o->variant != ECG_SRE || o->switch_tol > 0.0 || o->precision != ECG_FP64 ||
                             o->restart_every || o->restart_tol > 0.0))
     return ECG_EINVAL;

@@ -1356,73 +1356,6 @@ __device__ void cta_triu_inverse(const double* sR, const double* sInv, double* s
   __syncthreads();
 }
 
-// cta_cholesky followed by cta_triu_inverse, by one warp and without CTA
-// barriers, for W <= 16: lane j holds column j of G, of R and of R^{-1}, and
-// the entries other lanes need arrive by shuffles.  Every entry is computed
-// by the same operations in the same order as in the CTA form, so the
-// results are the same bits.  Reads sG (full symmetric W x W), writes the
-// upper triangle of R^{-1} into sRi (the rest zero) and returns false on
-// breakdown (uniform over the warp).  Executed by the 32 lanes of one warp.
-template <int W>
-__device__ bool warp_chol_inv(const double* sG, double* sRi, double ratio) {
-  static_assert(W <= 16, "one lane per column, arrays in registers");
-  const int j = threadIdx.x & 31;
-  const bool on = j < W;
-  double g[W], r[W], x[W], invd[W];
-#pragma unroll
-  for (int i = 0; i < W; i++) g[i] = on ? sG[i * W + j] : 0.0;
-  const double diag0 = on ? sG[j * W + j] : 1.0;
-#pragma unroll
-  for (int k = 0; k < W; k++) {
-    const double d = __shfl_sync(0xffffffffu, g[k], k);
-    const double d0 = __shfl_sync(0xffffffffu, diag0, k);
-    if (!(d > ratio * d0) || !isfinite(d)) return false;
-    const double inv = rsqrt_newton(d);
-    invd[k] = inv;
-    const double rk = (j == k) ? d * inv : ((j > k) ? g[k] * inv : 0.0);  // R[k][j]
-    r[k] = rk;
-#pragma unroll
-    for (int i = k + 1; i < W; i++) {
-      const double rki = __shfl_sync(0xffffffffu, rk, i);  // R[k][i]
-      if (j > k && i <= j) g[i] = fma(-rki, rk, g[i]);
-    }
-  }
-#pragma unroll
-  for (int i = W - 1; i >= 0; i--) {
-    double sacc = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-    for (int l = i + 1; l < W; l++) {
-      const double ril = __shfl_sync(0xffffffffu, r[i], l);  // R[i][l]
-      if (l <= j) sacc = fma(-ril, x[l], sacc);
-    }
-    x[i] = (i <= j) ? sacc * invd[i] : 0.0;
-  }
-  if (on) {
-#pragma unroll
-    for (int i = 0; i < W; i++) sRi[i * W + j] = x[i];
-  }
-  return true;
-}
-
-// Cholesky and triangular inverse of sG into sRi: one warp for W <= 16, the
-// whole CTA otherwise.  Returns false on breakdown (uniform over the CTA).
-// sR and sD are the CTA form's work arrays.
-template <int W>
-__device__ bool chol_inv(double* sG, double* sR, double* sRi, double* sD, int* sflag, double ratio) {
-  if constexpr (W <= 16) {
-    if (threadIdx.x < 32) {
-      const bool ok = warp_chol_inv<W>(sG, sRi, ratio);
-      if (threadIdx.x == 0) *sflag = ok ? 0 : 1;
-    }
-    __syncthreads();
-    return *sflag == 0;
-  } else {
-    if (!cta_cholesky<W>(sG, sR, sD, sflag, ratio)) return false;
-    cta_triu_inverse<W>(sR, sD, sRi);
-    return true;
-  }
-}
-
 // Euclidean step of Pre-CholQR: reduce X^T X, factor, store R_e^{-1}.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
@@ -1445,13 +1378,14 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
   }
   (void)gx;
   __syncthreads();
-  if (!chol_inv<W>(sG, sR, sRi, sD, &sflag, st->breakdown_ratio)) {
+  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
     }
     return;
   }
+  cta_triu_inverse<W>(sR, sD, sRi);
   for (int i = threadIdx.x; i < W * W; i += blockDim.x) P.small[kSmallRe + i] = sRi[i];
 }
 
@@ -1791,13 +1725,14 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   }
   (void)gx;
   __syncthreads();
-  if (!chol_inv<W>(sG, sR, sSi, sD, &sflag, st->breakdown_ratio)) {
+  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
     }
     return;
   }
+  cta_triu_inverse<W>(sR, sD, sSi);
   for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
     int a = e / W, b = e % W;
     double s = 0.0;

@@ -250,7 +250,7 @@ class Solver:
         o.restart_at_switch = 1 if restart_at_switch else 0
         o.block_residual = 1 if block_residual else 0
         o.stop_rule = int(stop_rule)
-        o.tensor_cores = 1 if tensor_cores else 0
+        o.tensor_cores = int(tensor_cores)  # 0, 1 (True) or 2
         o.stream = stream
         ctx = C.c_void_p()
         rc = lib.ecg_create(C.byref(csr), _ptr(part), self.t, C.byref(o), C.byref(ctx))

@@ -36,6 +36,11 @@ CASES = [
     ("blocky64_t16_trunc2", lambda: W.blocky_diffusion2d(64, 16, blocks=8, seed=53), dict(trunc=2)),
     ("blocky64_t8_msdo_trunc3", lambda: W.blocky_diffusion2d(64, 8, blocks=8, seed=54), dict(variant="msdo", trunc=3)),
     ("aniso3d_16_t16_trunc2", lambda: W.anisotropic_diffusion3d(16, 16, seed=55), dict(trunc=2)),
+    # the FP32 CGS coefficient Grams on the tensor cores (tensor_cores = 2)
+    ("blocky64_t16_trunc2_tcgrams", lambda: W.blocky_diffusion2d(64, 16, blocks=8, seed=53),
+     dict(trunc=2, tensor_cores=2)),
+    ("aniso3d_16_t16_trunc2_tcgrams", lambda: W.anisotropic_diffusion3d(16, 16, seed=55),
+     dict(trunc=2, tensor_cores=2)),
 ]
 
 
@@ -98,6 +103,9 @@ FP32_CASES = [
     ("spd350_t16_msdo_trunc2", lambda: W.random_spd_grid(350, 16, seed=64), dict(variant="msdo", trunc=2)),
     ("spd500_t8_msdo_trunc3", lambda: W.random_spd_grid(500, 8, seed=62), dict(variant="msdo", trunc=3)),
     ("spd500_t4_trunc2_acholqr", lambda: W.random_spd_grid(500, 4, seed=63), dict(trunc=2, ortho=ecg.A_CHOLQR)),
+    ("spd350_t16_trunc2_tcgrams", lambda: W.random_spd_grid(350, 16, seed=61), dict(trunc=2, tensor_cores=2)),
+    ("spd350_t16_msdo_trunc2_tcgrams", lambda: W.random_spd_grid(350, 16, seed=64),
+     dict(variant="msdo", trunc=2, tensor_cores=2)),
 ]
 
 
