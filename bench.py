@@ -247,7 +247,7 @@ def batch_run(torch):
 
 
 
-def warmstart_run(torch, side=64, ntrain=256, nheld=8, epochs=30):
+def warmstart_run(torch, side=64, ntrain=256, nheld=8, epochs=30, width=16, batch=8, lr=3e-3):
     """The learned warm start at a reduced scale: GRF diffusion problems
     (side x side, correlation length 0.1, sigma 1, t = 16), ntrain training
     solves, the U-Net trained with the energy-norm loss, and held-out solves
@@ -259,12 +259,16 @@ def warmstart_run(torch, side=64, ntrain=256, nheld=8, epochs=30):
     train = WS.make_dataset(ntrain, side=side, t=16, seed0=7000, prec_blocks=16 if side <= 64 else 64)
     t1 = time.perf_counter()
     held = WS.make_dataset(nheld, side=side, t=16, seed0=9000, solve=False)
-    net = WS.WarmStartNet(side=side, batch=8, seed=2)
-    hist = WS.train(net, train, epochs=epochs, lr=3e-3)
+    net = WS.WarmStartNet(side=side, batch=batch, seed=2, width=width)
+    hist = WS.train(net, train, epochs=epochs, lr=lr)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     rows = WS.evaluate(net, held, tol=1e-8, trunc=2, sweeps=16)
+    it0 = np.array([r["iters_zero"] for r in rows], dtype=float)
+    it1 = np.array([r["iters_net"] for r in rows], dtype=float)
     return {
+        "saving_iters_median": float(np.median(1.0 - it1 / it0)),
+        "raw_relres_mean": float(np.mean([r["raw_relres"] for r in rows])),
         "workload": f"GRF diffusion {side}x{side}, t=16, {ntrain} training solves, {nheld} held-out problems",
         "params": net.n_params(),
         "data_seconds": t1 - t0,
@@ -492,6 +496,11 @@ def main():
                     help="skip the other workloads (t = 8, t = 32, the 3D anisotropic system)")
     ap.add_argument("--warmstart", action="store_true",
                     help="also train the warm-start network on GRF diffusion problems and compare solves")
+    ap.add_argument("--ws-side", type=int, default=64, help="warm start: grid side")
+    ap.add_argument("--ws-train", type=int, default=256, help="warm start: training solves")
+    ap.add_argument("--ws-held", type=int, default=8, help="warm start: held-out problems")
+    ap.add_argument("--ws-epochs", type=int, default=30, help="warm start: epochs")
+    ap.add_argument("--ws-width", type=int, default=16, help="warm start: U-Net width (16: 118K, 20: 184K parameters)")
     ap.add_argument("--batch", action="store_true",
                     help="also solve the batched workload (64 uneven 2D diffusion systems, t=8) and report it")
     args = ap.parse_args()
@@ -675,7 +684,8 @@ def main():
     if args.batch:
         line["batch"] = batch_run(torch)
     if args.warmstart:
-        line["warmstart"] = warmstart_run(torch)
+        line["warmstart"] = warmstart_run(torch, side=args.ws_side, ntrain=args.ws_train, nheld=args.ws_held,
+                                          epochs=args.ws_epochs, width=args.ws_width)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_rate(p, 8, 0, args.trunc)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}

@@ -13,8 +13,9 @@ upsampling, the loss, Adam, input packing) runs in the kernels of
 libecg.so (include/ecg_nn.h).  Activations are bf16 NHWC, weights bf16 with
 FP32 master copies, gradients FP32.
 
-Network (117,697 parameters): two 3x3 conv + ReLU layers per level at
-side^2 (16 channels), (side/2)^2 (32) and (side/4)^2 (64), 2x2 average
+Network (width 16: 118,129 parameters; width 20: 184,381): two 3x3 conv +
+ReLU layers per level at side^2 (width channels), (side/2)^2 (2 width) and
+(side/4)^2 (4 width), 2x2 average
 pooling down, nearest upsampling up with skip connections concatenated,
 and a 1x1 head.  Targets are the ECG solutions scaled by 1 / std(b) (the
 problem is linear in b), so the proposal is x_0 = std(b) * net(...).  The
@@ -81,34 +82,43 @@ def _ok(rc, what):
         raise ecg.EcgError(rc, what)
 
 
-# (name, input A channels, input B channels (skip), output channels, K, relu)
-LAYERS = [
-    ("enc0a", 2, 0, 16, 3, 1),
-    ("enc0b", 16, 0, 16, 3, 1),
-    ("enc1a", 16, 0, 32, 3, 1),
-    ("enc1b", 32, 0, 32, 3, 1),
-    ("mid_a", 32, 0, 64, 3, 1),
-    ("mid_b", 64, 0, 64, 3, 1),
-    ("dec1a", 64, 32, 32, 3, 1),
-    ("dec1b", 32, 0, 32, 3, 1),
-    ("dec0a", 32, 16, 16, 3, 1),
-    ("dec0b", 16, 0, 16, 3, 1),
-    ("head", 16, 0, 1, 1, 0),
-]
+def layers(width: int = 16):
+    """(name, input A channels, input B channels (skip), output channels, K,
+    relu) of the U-Net with `width`, 2 `width` and 4 `width` channels at its
+    three levels (width 16: 118,129 parameters; 20: 184,381)."""
+    w1, w2, w4 = width, 2 * width, 4 * width
+    return [
+        ("enc0a", 2, 0, w1, 3, 1),
+        ("enc0b", w1, 0, w1, 3, 1),
+        ("enc1a", w1, 0, w2, 3, 1),
+        ("enc1b", w2, 0, w2, 3, 1),
+        ("mid_a", w2, 0, w4, 3, 1),
+        ("mid_b", w4, 0, w4, 3, 1),
+        ("dec1a", w4, w2, w2, 3, 1),
+        ("dec1b", w2, 0, w2, 3, 1),
+        ("dec0a", w2, w1, w1, 3, 1),
+        ("dec0b", w1, 0, w1, 3, 1),
+        ("head", w1, 0, 1, 1, 0),
+    ]
+
+
+LAYERS = layers(16)
 
 
 class WarmStartNet:
-    def __init__(self, side: int = 256, batch: int = 8, seed: int = 0, device="cuda"):
+    def __init__(self, side: int = 256, batch: int = 8, seed: int = 0, device="cuda", width: int = 16):
         import torch
 
         if side % 4:
             raise ValueError("side must be a multiple of 4")
         self.side, self.batch, self.dev = side, batch, device
+        self.w1, self.w2, self.w4 = width, 2 * width, 4 * width
+        self.layers = layers(width)
         self.t = torch
         self.L = lib()
         g = torch.Generator().manual_seed(seed)
         self.params = {}
-        for name, ca, cb, co, k, _ in LAYERS:
+        for name, ca, cb, co, k, _ in self.layers:
             fan_in = k * k * (ca + cb)
             w = torch.randn(k, k, ca + cb, co, generator=g) * np.sqrt(2.0 / fan_in)
             if name == "head":
@@ -127,7 +137,7 @@ class WarmStartNet:
                 "vb": torch.zeros_like(b32),
             }
         self.step_count = 0
-        smax = max(self.L.ecg_nn_wgrad_scratch(ca + cb, co, k) for _, ca, cb, co, k, _ in LAYERS)
+        smax = max(self.L.ecg_nn_wgrad_scratch(ca + cb, co, k) for _, ca, cb, co, k, _ in self.layers)
         self.scratch = torch.empty(int(smax), dtype=torch.float32, device=device)
         self.loss_buf = torch.zeros(257, dtype=torch.float64, device=device)
         self._acts = None
@@ -145,15 +155,15 @@ class WarmStartNet:
             return t.empty(N, h, h, c, dtype=dt, device=self.dev)
 
         a = {
-            "x": A(s, 2), "a0a": A(s, 16), "s0": A(s, 16), "p0": A(s // 2, 16), "a1a": A(s // 2, 32),
-            "s1": A(s // 2, 32), "p1": A(s // 4, 32), "ma": A(s // 4, 64), "mb": A(s // 4, 64),
-            "u1": A(s // 2, 64), "d1a": A(s // 2, 32), "d1b": A(s // 2, 32), "u0": A(s, 32), "d0a": A(s, 16),
-            "d0b": A(s, 16), "out": A(s, 1, t.float32),
+            "x": A(s, 2), "a0a": A(s, self.w1), "s0": A(s, self.w1), "p0": A(s // 2, self.w1), "a1a": A(s // 2, self.w2),
+            "s1": A(s // 2, self.w2), "p1": A(s // 4, self.w2), "ma": A(s // 4, self.w4), "mb": A(s // 4, self.w4),
+            "u1": A(s // 2, self.w4), "d1a": A(s // 2, self.w2), "d1b": A(s // 2, self.w2), "u0": A(s, self.w2), "d0a": A(s, self.w1),
+            "d0b": A(s, self.w1), "out": A(s, 1, t.float32),
         }
         return a
 
     def _conv(self, name, inA, inB, out, N, H, out32=False):
-        _, ca, cb, co, k, relu = next(l for l in LAYERS if l[0] == name)
+        _, ca, cb, co, k, relu = next(l for l in self.layers if l[0] == name)
         p = self.params[name]
         _ok(self.L.ecg_nn_conv(_p(inA), ca, _p(inB), cb, _p(p["w16"]), _p(p["b"]), _p(out), 1 if out32 else 0, N, H,
                                H, co, k, relu, None), name)
@@ -170,16 +180,16 @@ class WarmStartNet:
         L = self.L
         self._conv("enc0a", a["x"], None, a["a0a"], N, s)
         self._conv("enc0b", a["a0a"], None, a["s0"], N, s)
-        _ok(L.ecg_nn_pool2(_p(a["s0"]), _p(a["p0"]), N, s, s, 16, None), "pool0")
+        _ok(L.ecg_nn_pool2(_p(a["s0"]), _p(a["p0"]), N, s, s, self.w1, None), "pool0")
         self._conv("enc1a", a["p0"], None, a["a1a"], N, s // 2)
         self._conv("enc1b", a["a1a"], None, a["s1"], N, s // 2)
-        _ok(L.ecg_nn_pool2(_p(a["s1"]), _p(a["p1"]), N, s // 2, s // 2, 32, None), "pool1")
+        _ok(L.ecg_nn_pool2(_p(a["s1"]), _p(a["p1"]), N, s // 2, s // 2, self.w2, None), "pool1")
         self._conv("mid_a", a["p1"], None, a["ma"], N, s // 4)
         self._conv("mid_b", a["ma"], None, a["mb"], N, s // 4)
-        _ok(L.ecg_nn_up2(_p(a["mb"]), _p(a["u1"]), N, s // 4, s // 4, 64, None), "up1")
+        _ok(L.ecg_nn_up2(_p(a["mb"]), _p(a["u1"]), N, s // 4, s // 4, self.w4, None), "up1")
         self._conv("dec1a", a["u1"], a["s1"], a["d1a"], N, s // 2)
         self._conv("dec1b", a["d1a"], None, a["d1b"], N, s // 2)
-        _ok(L.ecg_nn_up2(_p(a["d1b"]), _p(a["u0"]), N, s // 2, s // 2, 32, None), "up0")
+        _ok(L.ecg_nn_up2(_p(a["d1b"]), _p(a["u0"]), N, s // 2, s // 2, self.w2, None), "up0")
         self._conv("dec0a", a["u0"], a["s0"], a["d0a"], N, s)
         self._conv("dec0b", a["d0a"], None, a["d0b"], N, s)
         self._conv("head", a["d0b"], None, a["out"], N, s, out32=True)
@@ -189,7 +199,7 @@ class WarmStartNet:
     def _grads(self, name, inA, inB, dout, N, H, dA=None, dB=None, accumulate=0):
         """Weight/bias gradients of layer `name` and (when dA is given) its
         input gradients; dout already masked by the ReLU derivative."""
-        _, ca, cb, co, k, _ = next(l for l in LAYERS if l[0] == name)
+        _, ca, cb, co, k, _ = next(l for l in self.layers if l[0] == name)
         p = self.params[name]
         _ok(self.L.ecg_nn_conv_wgrad(_p(inA), ca, _p(inB), cb, _p(dout), _p(p["gw"]), _p(p["gb"]), _p(self.scratch),
                                      N, H, H, co, k, None), name + " wgrad")
@@ -211,40 +221,40 @@ class WarmStartNet:
         def G(h, c):
             return t.empty(N, h, h, c, dtype=t.float32, device=self.dev)
 
-        d_d0b = G(s, 16)
+        d_d0b = G(s, self.w1)
         self._grads("head", a["d0b"], None, dout, N, s, d_d0b)
         self._relu_bwd(a["d0b"], d_d0b)
-        d_d0a = G(s, 16)
+        d_d0a = G(s, self.w1)
         self._grads("dec0b", a["d0a"], None, d_d0b, N, s, d_d0a)
         self._relu_bwd(a["d0a"], d_d0a)
-        d_u0, d_s0 = G(s, 32), G(s, 16)
+        d_u0, d_s0 = G(s, self.w2), G(s, self.w1)
         self._grads("dec0a", a["u0"], a["s0"], d_d0a, N, s, d_u0, d_s0)
-        d_d1b = G(s // 2, 32)
-        _ok(L.ecg_nn_up2_bwd(_p(d_u0), _p(d_d1b), N, s // 2, s // 2, 32, None), "up0 bwd")
+        d_d1b = G(s // 2, self.w2)
+        _ok(L.ecg_nn_up2_bwd(_p(d_u0), _p(d_d1b), N, s // 2, s // 2, self.w2, None), "up0 bwd")
         self._relu_bwd(a["d1b"], d_d1b)
-        d_d1a = G(s // 2, 32)
+        d_d1a = G(s // 2, self.w2)
         self._grads("dec1b", a["d1a"], None, d_d1b, N, s // 2, d_d1a)
         self._relu_bwd(a["d1a"], d_d1a)
-        d_u1, d_s1 = G(s // 2, 64), G(s // 2, 32)
+        d_u1, d_s1 = G(s // 2, self.w4), G(s // 2, self.w2)
         self._grads("dec1a", a["u1"], a["s1"], d_d1a, N, s // 2, d_u1, d_s1)
-        d_mb = G(s // 4, 64)
-        _ok(L.ecg_nn_up2_bwd(_p(d_u1), _p(d_mb), N, s // 4, s // 4, 64, None), "up1 bwd")
+        d_mb = G(s // 4, self.w4)
+        _ok(L.ecg_nn_up2_bwd(_p(d_u1), _p(d_mb), N, s // 4, s // 4, self.w4, None), "up1 bwd")
         self._relu_bwd(a["mb"], d_mb)
-        d_ma = G(s // 4, 64)
+        d_ma = G(s // 4, self.w4)
         self._grads("mid_b", a["ma"], None, d_mb, N, s // 4, d_ma)
         self._relu_bwd(a["ma"], d_ma)
-        d_p1 = G(s // 4, 32)
+        d_p1 = G(s // 4, self.w2)
         self._grads("mid_a", a["p1"], None, d_ma, N, s // 4, d_p1)
-        _ok(L.ecg_nn_pool2_bwd(_p(d_p1), _p(d_s1), N, s // 2, s // 2, 32, None), "pool1 bwd")
+        _ok(L.ecg_nn_pool2_bwd(_p(d_p1), _p(d_s1), N, s // 2, s // 2, self.w2, None), "pool1 bwd")
         self._relu_bwd(a["s1"], d_s1)
-        d_a1a = G(s // 2, 32)
+        d_a1a = G(s // 2, self.w2)
         self._grads("enc1b", a["a1a"], None, d_s1, N, s // 2, d_a1a)
         self._relu_bwd(a["a1a"], d_a1a)
-        d_p0 = G(s // 2, 16)
+        d_p0 = G(s // 2, self.w1)
         self._grads("enc1a", a["p0"], None, d_a1a, N, s // 2, d_p0)
-        _ok(L.ecg_nn_pool2_bwd(_p(d_p0), _p(d_s0), N, s, s, 16, None), "pool0 bwd")
+        _ok(L.ecg_nn_pool2_bwd(_p(d_p0), _p(d_s0), N, s, s, self.w1, None), "pool0 bwd")
         self._relu_bwd(a["s0"], d_s0)
-        d_a0a = G(s, 16)
+        d_a0a = G(s, self.w1)
         self._grads("enc0b", a["a0a"], None, d_s0, N, s, d_a0a)
         self._relu_bwd(a["a0a"], d_a0a)
         self._grads("enc0a", a["x"], None, d_a0a, N, s)
