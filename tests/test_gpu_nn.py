@@ -238,7 +238,8 @@ def test_training_and_warm_started_solves():
     # the energy-norm loss must fall, every warm-started solve must reach
     # the tolerance, and the smoothed proposal must start below ||b||
     # (whether it saves iterations is measured by bench.py --warmstart; at
-    # this training scale it does not, see the design notes)
+    # these training scales it does not; a warm start must not cost more than
+    # 5 % extra iterations)
     train = WS.make_dataset(48, side=64, t=16, seed0=7000, prec_blocks=16)
     held = WS.make_dataset(4, side=64, t=16, seed0=9000, solve=False)
     net = WS.WarmStartNet(side=64, batch=8, seed=2)
@@ -249,4 +250,4 @@ def test_training_and_warm_started_solves():
         assert r["status_zero"] == 0 and r["status_net"] == 0, r
         assert r["relres_true_net"] <= 1.0000001e-8, r
         assert r["used"] and r["x0_relres"] < 1.0, r
-        assert r["iters_net"] <= 1.15 * r["iters_zero"], r
+        assert r["iters_net"] <= 1.05 * r["iters_zero"], r
