@@ -311,6 +311,24 @@ __device__ __forceinline__ void tri_pair2(const T* x, const T* z, const T* U, in
   z2 = sz2;
 }
 
+// y = x U for one row x and an upper-triangular W x W matrix U, for the
+// column pair (bp, W-1-bp), as in tri_pair2 for a single row.
+template <typename T, int W>
+__device__ __forceinline__ void tri_pair1(const T* x, const T* U, int bp, T& x1, T& x2) {
+  const int b1 = bp, b2 = W - 1 - bp;
+  T s1 = 0, s2 = 0;
+#pragma unroll 4
+  for (int j = 0; j <= W; j++) {
+    const bool first = (j <= b1);
+    const int a = first ? j : j - b1 - 1;
+    const T v = fma(x[a], U[a * W + (first ? b1 : b2)], first ? s1 : s2);
+    if (first) s1 = v;
+    else s2 = v;
+  }
+  x1 = s1;
+  x2 = s2;
+}
+
 // Sum of in[c * stride + e] over c < count for every e < nent, written to
 // out[e] via `store(e, sum)`: one warp per entry, lanes over c (lane l takes
 // c = l, l+32, ...), then a fixed shuffle tree, so the result does not
@@ -1303,57 +1321,116 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
   return y;
 }
 
-// Cholesky G = R^T R of the W x W matrix in sG (full symmetric storage) into
-// sR (upper), with the pivot test pivot <= ratio * G_jj.  Returns false on
-// breakdown.  sG is destroyed; sD (W doubles) ends holding 1 / R_jj.  All
-// threads of the CTA must call it.
+// 1/d for a positive normal d: the hardware's FP32 reciprocal estimate of
+// d's significand (relative error below 2^-22), rescaled by d's exponent
+// with integer arithmetic, then one third-order Newton-Raphson step
+// y <- y (1 + e + e^2), e = 1 - d y, which cubes the relative error.  Three
+// dependent FP64 FMAs instead of a division: the pivots of the
+// factorisation below form a serial chain of them.  Exponents at the ends
+// of the range take the plain quotient.
+__device__ __forceinline__ double recip_pos(double d) {
+  const long long b = __double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 2 || e > 2044) return 1.0 / d;
+  const uint32_t fb = (127u << 23) | (uint32_t)((b >> 29) & 0x7FFFFF);  // d's significand in [1, 2)
+  float yf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(fb)));
+  const uint32_t yb = __float_as_uint(yf);
+  const long long ye = (long long)((yb >> 23) & 0xFF) - 127 + 1023 - (e - 1023);
+  const double y0 = __longlong_as_double((ye << 52) | ((long long)(yb & 0x7FFFFF) << 29));
+  const double r = fma(-d, y0, 1.0);
+  const double p = fma(r, r, r);
+  return fma(y0, p, y0);
+}
+
+// The breakdown test of a pivot: d > thr (thr = ratio x the original
+// diagonal entry, >= 0) and d finite and positive.  Positive doubles order
+// like their bit patterns, so the test is integer compares.
+__device__ __forceinline__ bool pivot_ok(double d, double thr) {
+  const long long b = __double_as_longlong(d), t = __double_as_longlong(thr);
+  return b > 0 && b > t && ((b >> 52) & 0x7FF) != 0x7FF;
+}
+
+// R^{-1} for the Cholesky factor R (G = R^T R, R upper with positive
+// diagonal) of the W x W Gram in sA (full symmetric storage; overwritten by
+// R^{-1}, zeros below the diagonal), by way of G = L D L^T:
+//   - right-looking LDL^T, one thread per upper-triangle entry; the thread
+//     that finishes pivot j + 1 tests it (pivot <= ratio G_jj or not finite
+//     is a breakdown, as in the Cholesky form) and forms 1/d_{j+1}, so each
+//     column costs one barrier and no square root;
+//   - M = L^{-1} by a column sweep (unit diagonal, no division);
+//   - R = D^{1/2} L^T, so R^{-1} = M^T D^{-1/2}: (R^{-1})_kc = M_ck / sqrt(d_c).
+// GB300 issues FP64 at a few instructions per SM and cycle with long
+// latencies, and a Cholesky's chain of square roots and divisions made the
+// t x t steps a visible part of an iteration; this form keeps three FP64
+// FMAs per column on the chain.  sM: W x W scratch; sInv, sThr: W doubles.
+// Needs kThreads threads, all of which must call it; returns false (the
+// same on every thread) on breakdown.
 template <int W>
-__device__ bool cta_cholesky(double* sG, double* sR, double* sD, int* sflag, double ratio) {
-  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sR[i] = 0.0;
-  for (int i = threadIdx.x; i < W; i += blockDim.x) sD[i] = sG[i * W + i];
-  if (threadIdx.x == 0) *sflag = 0;
+__device__ bool cta_ldl_rinv(double* sA, double* sM, double* sInv, double* sThr, int* sflag, double ratio) {
+  constexpr int E = W * (W + 1) / 2, EPT = (E + kThreads - 1) / kThreads;
+  const int tid = threadIdx.x;
+  int ei[EPT], ek[EPT];  // this thread's entries (i, k), i <= k
+#pragma unroll
+  for (int q = 0; q < EPT; q++) {
+    const int e = tid + q * kThreads;
+    if (e < E) upper_ab(e, W, ei[q], ek[q]);
+    else ei[q] = ek[q] = -1;
+  }
+  for (int j = tid; j < W; j += kThreads) sThr[j] = ratio * sA[j * W + j];
+  if (tid == 0) {
+    *sflag = 0;
+    const double d = sA[0];
+    if (!pivot_ok(d, ratio * d)) *sflag = 1;
+    else sInv[0] = recip_pos(d);
+  }
   __syncthreads();
-  for (int j = 0; j < W; j++) {
-    if (threadIdx.x == 0) {
-      double d = sG[j * W + j];
-      if (!(d > ratio * sD[j]) || !isfinite(d)) {
-        *sflag = 1;
-      } else {
-        const double inv = rsqrt_newton(d);
-        sR[j * W + j] = d * inv;
-        sD[j] = inv;  // the pivot test of column j is done
+  if (*sflag) return false;
+  for (int j = 0; j < W - 1; j++) {
+    const double inv = sInv[j];
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+      const int i = ei[q], k = ek[q];
+      if (i > j) {
+        const double t = sA[j * W + i] * inv;
+        const double v = fma(-t, sA[j * W + k], sA[i * W + k]);
+        sA[i * W + k] = v;
+        if (k == j + 1) {  // then i == j + 1: the next pivot
+          if (!pivot_ok(v, sThr[j + 1])) *sflag = 1;
+          else sInv[j + 1] = recip_pos(v);
+        }
       }
     }
     __syncthreads();
-    if (*sflag) return false;
-    const double inv = sD[j];
-    for (int i = j + 1 + threadIdx.x; i < W; i += blockDim.x) sR[j * W + i] = sG[j * W + i] * inv;
-    __syncthreads();
-    const int m = W - j - 1;
-    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      int i = j + 1 + idx / m, l = j + 1 + idx % m;
-      if (l >= i) sG[i * W + l] = fma(-sR[j * W + i], sR[j * W + l], sG[i * W + l]);
+  }
+  if (*sflag) return false;  // a failed pivot only leaves later ones meaningless
+  // L_ki = a_ik / d_i (i < k) into the upper part; M starts as -L
+#pragma unroll
+  for (int q = 0; q < EPT; q++) {
+    const int i = ei[q], k = ek[q];
+    if (i >= 0 && i < k) {
+      const double l = sA[i * W + k] * sInv[i];
+      sA[i * W + k] = l;
+      sM[k * W + i] = -l;
+    }
+  }
+  for (int j = tid; j < W; j += kThreads) sThr[j] = rsqrt_newton(sA[j * W + j]);
+  __syncthreads();
+  // M_ic -= L_ik M_kc for i > k > c: after step k, rows <= k + 1 are final
+  for (int k = 1; k < W - 1; k++) {
+#pragma unroll
+    for (int q = 0; q < EPT; q++) {
+      const int c = ei[q], i = ek[q];
+      if (c >= 0 && i > k && k > c) sM[i * W + c] = fma(-sA[k * W + i], sM[k * W + c], sM[i * W + c]);
     }
     __syncthreads();
   }
+  for (int e = tid; e < W * W; e += kThreads) {
+    const int k = e / W, c = e % W;
+    sA[e] = (k == c) ? sThr[c] : (k < c) ? sM[c * W + k] * sThr[c] : 0.0;
+  }
+  __syncthreads();
   return true;
-}
-
-// Inverse of the upper-triangular sR into sRi (upper), one column per
-// thread; sInv holds 1 / R_ii (from cta_cholesky).
-template <int W>
-__device__ void cta_triu_inverse(const double* sR, const double* sInv, double* sRi) {
-  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sRi[i] = 0.0;
-  __syncthreads();
-  if (threadIdx.x < W) {
-    const int c = threadIdx.x;
-    for (int i = c; i >= 0; i--) {
-      double s = (i == c) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= c; l++) s = fma(-sR[i * W + l], sRi[l * W + c], s);
-      sRi[i * W + c] = s * sInv[i];
-    }
-  }
-  __syncthreads();
 }
 
 // Euclidean step of Pre-CholQR: reduce X^T X, factor, store R_e^{-1}.
@@ -1364,9 +1441,9 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
   if (skip(st, gw)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sG = (double*)smem_raw;
-  double* sR = sG + W * W;
-  double* sRi = sR + W * W;
-  double* sD = sRi + W * W;
+  double* sM = sG + W * W;
+  double* sInv = sM + W * W;
+  double* sThr = sInv + W;
   __shared__ int sflag;
   const double* red = P.small + kSmallG;  // X^T X reduced by k_reduce_partials
   for (int e = threadIdx.x; e < E; e += blockDim.x) {
@@ -1378,15 +1455,14 @@ __global__ void __launch_bounds__(kThreads) k_small_e(KP P, int gw, int gx) {
   }
   (void)gx;
   __syncthreads();
-  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
+  if (!cta_ldl_rinv<W>(sG, sM, sInv, sThr, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
     }
     return;
   }
-  cta_triu_inverse<W>(sR, sD, sRi);
-  for (int i = threadIdx.x; i < W * W; i += blockDim.x) P.small[kSmallRe + i] = sRi[i];
+  for (int i = threadIdx.x; i < W * W; i += blockDim.x) P.small[kSmallRe + i] = sG[i];
 }
 
 // 4 x 4 blocks of the FP32 spmm_gram: the upper blocks (ab <= bb) of G and
@@ -1706,10 +1782,10 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   if (skip(st, gw)) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sG = (double*)smem_raw;
-  double* sR = sG + W * W;
-  double* sSi = sR + W * W;
-  double* sD = sSi + W * W;
-  double* sg = sD + W;
+  double* sM = sG + W * W;
+  double* sInv = sM + W * W;
+  double* sThr = sInv + W;
+  double* sg = sThr + W;
   __shared__ int sflag;
   const double* red = P.small + kSmallG;  // [G upper | g] reduced by k_reduce_partials
   for (int e = threadIdx.x; e < E + W; e += blockDim.x) {
@@ -1725,22 +1801,26 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   }
   (void)gx;
   __syncthreads();
-  if (!cta_cholesky<W>(sG, sR, sD, &sflag, st->breakdown_ratio)) {
+  if (!cta_ldl_rinv<W>(sG, sM, sInv, sThr, &sflag, st->breakdown_ratio)) {
     if (threadIdx.x == 0) {
       st->stop = 1;
       st->status = ST_EBREAKDOWN;
     }
     return;
   }
-  cta_triu_inverse<W>(sR, sD, sSi);
+  // sG = S^{-1}; R^{-1} = R_e^{-1} S^{-1} (Pre-CholQR) or S^{-1}
+  if (PRE) {
+    for (int i = threadIdx.x; i < W * W; i += blockDim.x) sM[i] = P.small[kSmallRe + i];
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < W * W; e += blockDim.x) {
     int a = e / W, b = e % W;
     double s = 0.0;
     if (a <= b) {
       if (PRE) {
-        for (int l = a; l <= b; l++) s = fma(P.small[kSmallRe + a * W + l], sSi[l * W + b], s);
+        for (int l = a; l <= b; l++) s = fma(sM[a * W + l], sG[l * W + b], s);
       } else {
-        s = sSi[e];
+        s = sG[e];
       }
     }
     P.small[kSmallRi + e] = s;
@@ -1748,7 +1828,7 @@ __global__ void __launch_bounds__(kThreads) k_small_a(KP P, int gw, int gx) {
   if (threadIdx.x < W) {
     const int b = threadIdx.x;
     double s = 0.0;
-    for (int a = 0; a <= b; a++) s = fma(sSi[a * W + b], sg[a], s);
+    for (int a = 0; a <= b; a++) s = fma(sG[a * W + b], sg[a], s);
     P.small[kSmallAl + b] = s;
   }
 }
@@ -1973,6 +2053,75 @@ __global__ void __launch_bounds__(kThreads) k_final(KP P, int gw, const T* Xin, 
   double tot = block_sum(rho_acc, sbuf);
   if (threadIdx.x == 0) P.rho_part[blockIdx.x] = tot;
   if (P.want_beta && threadIdx.x < W) P.beta_part[(long long)blockIdx.x * 64 + threadIdx.x] = beta_acc.value();
+}
+
+// X <- X R_e^{-1} in place (R_e^{-1} upper, in P.small): the Euclidean half
+// of Pre-CholQR made explicit, q = X R_e^{-1}, so that the SpMM that follows
+// applies A to the orthonormalised block (Pre-CholQR's order: Q_e, then
+// A Q_e) and the A-CholQR step needs no per-row transform.  One (row,
+// column pair) per thread, W + 1 FMAs each; tiles of Tile<W>::R rows
+// through the bulk-copy pipeline when X suits it.
+template <typename T, int W>
+__host__ __device__ constexpr size_t smem_tri_right() {
+  return 64 + sizeof(T) * ((size_t)Stages<T>::S * Tile<W>::R * W + W * W);
+}
+template <typename T, int W>
+__global__ void __launch_bounds__(kThreads) k_tri_right(KP P, int gw, T* X) {
+  constexpr int R = Tile<W>::R;
+  constexpr int H = (W > 1) ? W / 2 : 1;
+  constexpr int S = Stages<T>::S;
+  const DevState* st = P.st;
+  if (skip(st, gw)) return;
+  __shared__ BulkStream sst[kMaxStreams];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint64_t* sbar = (uint64_t*)smem_raw;  // 64 bytes
+  T* sX = (T*)(smem_raw + 64);           // S stages of R x W (one tile on the register path)
+  T* sU = sX + S * R * W;                // W x W
+  for (int i = threadIdx.x; i < W * W; i += blockDim.x) sU[i] = (T)P.small[kSmallRe + i];
+  BulkTiles<S> bt;
+  bt.st = sst;
+  bt.bar = sbar;
+  bt.stage = (unsigned char*)sX;
+  bt.R = R;
+  const bool bulk = bt.add(X, W * (int)sizeof(T));
+  int r0, r1;
+  if (bulk) {
+    cta_rows_aligned(P.n, R, r0, r1);
+    bt.r0 = r0;
+    bt.r1 = r1;
+    bt.ntiles = (r1 - r0 + R - 1) / R;
+    bt.start();  // its barrier also publishes sU
+  } else {
+    cta_rows(P.n, r0, r1);
+  }
+  for (int i = 0, row0 = r0; row0 < r1; i++, row0 += R) {
+    const int nr = min(R, r1 - row0);
+    const T* tX = sX;
+    if (bulk) {
+      if (!bt.ready(i, (DevState*)st)) return;
+      tX = (const T*)bt.tile(i);
+    } else {
+      for (int idx = threadIdx.x; idx < R * W; idx += blockDim.x)
+        sX[idx] = (idx / W < nr) ? X[(long long)row0 * W + idx] : T(0);
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < R * H; idx += blockDim.x) {
+      const int r = idx / H, bp = idx - r * H;
+      if (r < nr) {
+        const long long o = (long long)(row0 + r) * W;
+        if (W == 1) {
+          X[o] = tX[r] * sU[0];
+        } else {
+          T y1, y2;
+          tri_pair1<T, W>(tX + r * W, sU, bp, y1, y2);
+          X[o + bp] = y1;
+          X[o + W - 1 - bp] = y2;
+        }
+      }
+    }
+    __syncthreads();  // tile i is no longer read
+    if (bulk) bt.refill(i);
+  }
 }
 
 // ------------------------------------------------ block Jacobi preconditioner
