@@ -375,6 +375,12 @@ int or_dense_spd_solve(int n, const double* A, const double* b, double* x) {
  * V holds A W_k.  mode 0: Pre-CholQR (Householder QR W = Q_e R_e, then
  * A-CholQR of Q_e: Q_e^T A Q_e = S^T S, W_k = Q_e S^{-1}, A W_k =
  * (A Q_e) S^{-1}).  mode 1: A-CholQR (W^T A W = R^T R, W_k = W R^{-1}).
+ * mode 2: Pre-CholQR with CholQR as the Euclidean step (W^T W = R_e^T R_e,
+ * Q_e = W R_e^{-1}, then the A-CholQR of Q_e as in mode 0); Section 5 cites
+ * Pre-CholQR without its body, and this is the reading the GPU follows.  In
+ * exact arithmetic modes 0 and 2 give the same Q_e (the thin QR with a
+ * positive diagonal is unique); in floating point CholQR's Q_e loses
+ * orthogonality like eps kappa(W)^2, Householder's like eps.
  * Returns 0 or OR_EBREAKDOWN. */
 int or_a_orthonormalize(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
                         int w, int mode, double* W, double* V) {
@@ -390,6 +396,10 @@ int or_a_orthonormalize(int64_t n, const int64_t* rowptr, const int32_t* col, co
     if (qs < 0) { status = OR_ENOMEM; goto done; }
     if (qs > 0) { status = OR_EBREAKDOWN; goto done; }
     or_copy(n * w, W, Qe);
+  } else if (mode == 2) {
+    or_block_tdot(n, w, W, w, W, G);
+    if (or_cholesky(w, G, R) != 0) { status = OR_EBREAKDOWN; goto done; }
+    or_right_trsm(n, w, R, W);
   }
   or_spmm(n, rowptr, col, val, w, W, V);
   or_block_tdot(n, w, W, w, V, G);
@@ -725,7 +735,8 @@ void or_msdo_direction(int64_t n, int w, const double* Pprev, const double* Vpre
  * trunc == 0 orthonormalises against every stored block; trunc >= 1 against
  * the last trunc blocks only (Section 3; trunc = 2 on variant 0 is SRE-CG).
  * switch_tol > 0 enables the flexible halving of Algorithms 3 and 4.
- * ortho: 0 Pre-CholQR, 1 A-CholQR.  k_max follows Algorithm 1 (at most
+ * ortho: 0 Pre-CholQR, 1 A-CholQR, 2 Pre-CholQR with a CholQR Euclidean
+ * step (or_a_orthonormalize).  k_max follows Algorithm 1 (at most
  * k_max - 1 iterations).  history (length k_max, may be NULL) receives rho_k
  * for k = 0..iters.  xhist (n * (k_max - 1), may be NULL) receives x_k after
  * iteration k at offset (k-1)*n.  basis (may be NULL) receives every W_k
@@ -747,7 +758,7 @@ int or_ecg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const dou
   or_restart rsz;
   memset(&rsz, 0, sizeof(rsz));
   if (!rs) rs = &rsz;
-  if (n <= 0 || t < 1 || variant < 0 || variant > 2 || trunc < 0 || ortho < 0 || ortho > 1 ||
+  if (n <= 0 || t < 1 || variant < 0 || variant > 2 || trunc < 0 || ortho < 0 || ortho > 2 ||
       !(eps >= 0.0) || (switch_tol > 0.0 && (t % 2 != 0)) || rs->every == 1 || rs->every < 0 ||
       !(rs->tol >= 0.0) || rs->max_count < 0 || (rs->at_switch && !(switch_tol > 0.0))) {
     res->status = OR_EINVAL;
@@ -978,7 +989,7 @@ int or_becg_solve(int64_t n, const int64_t* rowptr, const int32_t* col, const do
                   double eps, int kmax, double* x, double* history, double* xhist, double* Xout,
                   or_result* res) {
   memset(res, 0, sizeof(*res));
-  if (n <= 0 || t < 1 || trunc < 0 || ortho < 0 || ortho > 1 || !(eps >= 0.0)) {
+  if (n <= 0 || t < 1 || trunc < 0 || ortho < 0 || ortho > 2 || !(eps >= 0.0)) {
     res->status = OR_EINVAL;
     return OR_EINVAL;
   }

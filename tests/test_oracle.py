@@ -103,10 +103,12 @@ def test_dense_spd_solve_matches_numpy():
     assert rel(x, np.linalg.solve(Ad, p.b)) < 1e-13
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_a_orthonormalize_gives_the_unique_factor(mode):
     """W = W_k R with W_k^T A W_k = I and R upper triangular with positive
-    diagonal has one solution; compute it with scipy and compare."""
+    diagonal has one solution; compute it with scipy and compare.  Mode 0
+    (Householder Euclidean step), 1 (A-CholQR alone) and 2 (CholQR Euclidean
+    step) reach it by different routes."""
     p = W.random_spd_grid(10, 4, seed=6)
     A = p.scipy()
     rng = np.random.default_rng(7)
@@ -126,7 +128,7 @@ def test_a_orthonormalize_flags_dependent_block():
     rng = np.random.default_rng(9)
     Wm = rng.standard_normal((p.n, 4))
     Wm[:, 3] = Wm[:, 1]
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         _, _, st = O.a_orthonormalize(p.scipy(), Wm, mode)
         assert st == O.EBREAKDOWN
 
@@ -601,3 +603,43 @@ def test_restart_options_are_validated():
     A = p.scipy()
     assert O.ecg_solve(A, p.part, 4, p.b, restart_every=1).status == O.EINVAL
     assert O.ecg_solve(A, p.part, 4, p.b, restart_at_switch=True).status == O.EINVAL
+
+
+def test_cholqr_euclidean_step_follows_householder_solve():
+    """A whole solve with the CholQR Euclidean step (ortho 2) against the
+    Householder one (ortho 0) on a well-conditioned system: the same method
+    in exact arithmetic, so the same iteration count and, before rounding
+    differences grow, the same history."""
+    p = W.random_spd_grid(16, 4, seed=31)
+    A = p.scipy()
+    o0 = O.ecg_solve(A, p.part, 4, p.b, tol=1e-10, maxit=400, trunc=2, ortho=0)
+    o2 = O.ecg_solve(A, p.part, 4, p.b, tol=1e-10, maxit=400, trunc=2, ortho=2)
+    assert o0.status == 0 and o2.status == 0
+    assert abs(o0.iters - o2.iters) <= 1
+    k = min(10, o0.iters)
+    assert np.all(np.abs(o0.history[:k] - o2.history[:k]) <= 1e-10 * o0.history[0])
+    assert rel(o2.x, o0.x) < 1e-8
+
+
+def test_euclidean_step_rescues_ill_conditioned_block():
+    """W = Q M with M of condition 1e6: A-CholQR alone factors a Gram of
+    condition ~1e12 kappa(A) and loses A-orthogonality, while either
+    Pre-CholQR (Householder or CholQR Euclidean step) first removes M and
+    keeps W_k^T A W_k = I to rounding.  Both keep span(W)."""
+    p = W.random_spd_grid(12, 4, seed=33)
+    A = p.scipy()
+    rng = np.random.default_rng(34)
+    Q, _ = np.linalg.qr(rng.standard_normal((p.n, 4)))
+    U, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    V, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    M = U @ np.diag([1.0, 1e-2, 1e-4, 1e-6]) @ V.T
+    Wm = Q @ M
+    err = {}
+    for mode in (0, 1, 2):
+        Wk, Vk, st = O.a_orthonormalize(A, Wm, mode)
+        assert st == 0
+        err[mode] = np.abs(Wk.T @ (A @ Wk) - np.eye(4)).max()
+        # span: W = W_k (W_k^T A W)
+        assert rel(Wk @ (Wk.T @ (A @ Wm)), Wm) < 1e-6
+    assert err[0] < 1e-12 and err[2] < 1e-12, err
+    assert err[1] > 1e-9, err
