@@ -172,10 +172,12 @@ def algorithmic_counts(n, nnz, t, trunc, K, sre=True):
                   the m blocks and X: (2m + 1) B per iteration
       cgs_update  each pass reads the m blocks Q_j and its source, writes X:
                   2 (m + 2) B
-      gram_e      reads X: B
-      spmm_gram   reads X and A (12 nnz + 4 (n + 1)) and r, writes Y:
-                  2 B + 12 nnz + 4 (n + 1) + 8 n
-      final       reads X, Y, x, r, writes W_k, V_k, x, r: 4 B + 32 n"""
+      gram_e      X^T X reads X; q = X R_e^{-1} in place reads and writes
+                  it: 3 B
+      spmm_gram   Y = A q with q^T Y and q^T r: reads q and A (12 nnz +
+                  4 (n + 1)) and r, writes Y: 2 B + 12 nnz + 4 (n + 1) + 8 n
+      final       reads X, Y, x, r, writes W_k, V_k, x, r: 4 B + 32 n
+    (the FP64 Pre-CholQR form, which materialises q before the SpMM)."""
     tri = t * (t + 1) // 2
     fl = {"cgs_tdot": 0.0, "cgs_update": 0.0, "gram_e": 0.0, "spmm_gram": 0.0, "final": 0.0}
     by = {k: 0.0 for k in fl}
@@ -184,13 +186,13 @@ def algorithmic_counts(n, nnz, t, trunc, K, sre=True):
         m = min(k - 1, trunc)
         fl["cgs_tdot"] += 2 * 2.0 * (m * t) * t * n
         fl["cgs_update"] += 2 * 2.0 * (m * t) * t * n
-        fl["gram_e"] += 2.0 * tri * n
-        fl["spmm_gram"] += 2.0 * (nnz * t + 2 * tri * n + tri * n + t * n)
+        fl["gram_e"] += 2.0 * 2 * tri * n
+        fl["spmm_gram"] += 2.0 * (nnz * t + tri * n + t * n)
         fl["final"] += 2.0 * (2 * tri * n + 2 * t * n)
         if m > 0:
             by["cgs_tdot"] += ((2 * m + 1) if sre else (2 * m + 2)) * B
             by["cgs_update"] += 2 * (m + 2) * B
-        by["gram_e"] += B
+        by["gram_e"] += 3 * B
         by["spmm_gram"] += 2 * B + 12.0 * nnz + 4.0 * (n + 1) + 8.0 * n
         by["final"] += 4 * B + 32.0 * n
     return fl, by

@@ -228,6 +228,8 @@ int set_smem_attrs_t() {
   CK(cudaFuncSetAttribute(k_final<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_final<T, W>()));
   CK(cudaFuncSetAttribute(k_gram_self<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                           (int)smem_gram_self<T, W>()));
+  CK(cudaFuncSetAttribute(k_tri_right<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                          (int)smem_tri_right<T, W>()));
   if constexpr (F32Rows<T, W>::on) {
     CK(cudaFuncSetAttribute(k_spmm_gram_rows<W, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)smem_spmm_rows<W>()));
@@ -315,6 +317,7 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   P.Rb = c->d_Rb;
   P.wcap = kChunk;
   P.sre_src = 0;
+  P.rev = 0;
   return P;
 }
 
@@ -581,14 +584,36 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   P.sre_src = 1;  // an SRE block goes from V_{k-1} straight into the first CGS pass
   k_generate<T, W><<<ggen, kThreads, 0, s>>>(P, W);
   prof_mark(c, 0);
+  // FP32 launches alternate the direction of their row wavefront (see
+  // BulkTiles::wave), so that each starts on the rows its predecessor left
+  // in L2: coefficients forward, update backward (twice), the Euclidean
+  // Gram and the SpMM forward (X fits in L2 after the Gram), the final
+  // update backward, which ends where the next iteration's first pass starts
   for (int pass = 0; pass < 2; pass++) {
     P.sre_src = (pass == 0) ? 1 : 0;
+    P.rev = 0;
     launch_tdot<T, W>(c, P, X, c->d_C, wcap, gy, gxw);
     prof_mark(c, 1);
+    P.rev = fp32 ? 1 : 0;
     launch_update<T, W>(c, P, X, c->d_C, wcap, gup);
     prof_mark(c, 2);
   }
-  if (pre) {
+  P.rev = 0;
+  if (pre && !fp32) {
+    // FP64: q = X R_e^{-1} explicitly, then the A-CholQR step on q (the
+    // SpMM's FP64 FMAs are its bound, and a per-row transform would double them)
+    k_gram_self<T, W><<<ggs, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
+    prof_mark(c, 3);
+    reduce_small(c, P, W, W * (W + 1) / 2, ggs);
+    k_small_e<W><<<1, kThreads, smem_small<W>(), s>>>(P, W, c->gx);
+    prof_mark(c, 4);
+    k_tri_right<T, W><<<c->gx, kThreads, smem_tri_right<T, W>(), s>>>(P, W, X);
+    prof_mark(c, 3);
+    k_spmm_gram<T, W, true, false><<<gsp, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
+    prof_mark(c, 5);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W, gsp);
+    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
+  } else if (pre) {
     k_gram_self<T, W><<<ggs, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
     prof_mark(c, 3);
     reduce_small(c, P, W, W * (W + 1) / 2, ggs);
@@ -611,6 +636,7 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
     k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
   }
   prof_mark(c, 6);
+  P.rev = fp32 ? 1 : 0;
   int gf = gfin;  // CTAs that write rho / beta partials
   bool fin_tc = false;
   if constexpr (tc::final_tc_ok<T, W>()) {
@@ -854,9 +880,10 @@ struct Ops {
       k_gram_self<double, W><<<c->gx, kThreads, smem_gram_self<double, W>(), c->stream>>>(P, W, Wio);
       reduce_small(c, P, W, W * (W + 1) / 2);
       k_small_e<W><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
-      k_spmm_gram<double, W, true, true><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
+      k_tri_right<double, W><<<c->gx, kThreads, smem_tri_right<double, W>(), c->stream>>>(P, W, Wio);
+      k_spmm_gram<double, W, true, false><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
       reduce_small(c, P, W, W * (W + 1) / 2 + W);
-      k_small_a<W, true><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
+      k_small_a<W, false><<<1, kThreads, smem_small<W>(), c->stream>>>(P, W, c->gx);
     } else {
       k_spmm_gram<double, W, true, false><<<c->gx, kThreads, smem_spmm<double, W>(), c->stream>>>(P, W, Wio, Y);
       reduce_small(c, P, W, W * (W + 1) / 2 + W);
