@@ -317,7 +317,6 @@ KP make_kp(ecg_ctx* c, DevState* st, BlockDesc* desc, bool fp32) {
   P.Rb = c->d_Rb;
   P.wcap = kChunk;
   P.sre_src = 0;
-  P.rev = 0;
   return P;
 }
 
@@ -584,21 +583,13 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   P.sre_src = 1;  // an SRE block goes from V_{k-1} straight into the first CGS pass
   k_generate<T, W><<<ggen, kThreads, 0, s>>>(P, W);
   prof_mark(c, 0);
-  // FP32 launches alternate the direction of their row wavefront (see
-  // BulkTiles::wave), so that each starts on the rows its predecessor left
-  // in L2: coefficients forward, update backward (twice), the Euclidean
-  // Gram and the SpMM forward (X fits in L2 after the Gram), the final
-  // update backward, which ends where the next iteration's first pass starts
   for (int pass = 0; pass < 2; pass++) {
     P.sre_src = (pass == 0) ? 1 : 0;
-    P.rev = 0;
     launch_tdot<T, W>(c, P, X, c->d_C, wcap, gy, gxw);
     prof_mark(c, 1);
-    P.rev = fp32 ? 1 : 0;
     launch_update<T, W>(c, P, X, c->d_C, wcap, gup);
     prof_mark(c, 2);
   }
-  P.rev = 0;
   if (pre && !fp32) {
     // FP64: q = X R_e^{-1} explicitly, then the A-CholQR step on q (the
     // SpMM's FP64 FMAs are its bound, and a per-row transform would double them)
@@ -636,7 +627,6 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
     k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
   }
   prof_mark(c, 6);
-  P.rev = fp32 ? 1 : 0;
   int gf = gfin;  // CTAs that write rho / beta partials
   bool fin_tc = false;
   if constexpr (tc::final_tc_ok<T, W>()) {

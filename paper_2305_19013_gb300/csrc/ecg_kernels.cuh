@@ -132,8 +132,6 @@ struct KP {
   int sre_src;       // 1: an SRE block is read from V_{k-1} where it is
                      // used (k_generate skips the copy into X, the first
                      // CGS pass reads V_{k-1} and writes X)
-  int rev;           // 1: the row-tile kernels that sweep a wavefront walk
-                     // it from the last tile to the first (BulkTiles::wave)
 };
 
 // Block Jacobi preconditioner M = L L^T, L = diag(L_1 .. L_nb), L_i the
@@ -459,30 +457,6 @@ struct BulkTiles {
   unsigned char* stage;  // S stages of stage_bytes
   int stage_bytes = 0;
   int r0 = 0, r1 = 0, R = 0, ntiles = 0;
-  // wavefront order (wave()): tile i of this CTA is tile first + i stride
-  // of the n rows' T tiles, counted from the end when rev is set
-  int wv = 0, n = 0, T = 0, first = 0, stride = 1, rev = 0;
-
-  // All CTAs sweep one wavefront over the rows: at any time they work on
-  // neighbouring tiles, and a launch that walks the other way starts on the
-  // rows its predecessor touched last, which are still in L2.  The grid
-  // size does not change the order, so kernels of different grids chain.
-  __device__ void wave(int n_, int rev_) {
-    wv = 1;
-    n = n_;
-    T = (n_ + R - 1) / R;
-    first = blockIdx.x;
-    stride = gridDim.x;
-    rev = rev_;
-    ntiles = first < T ? (T - first + stride - 1) / stride : 0;
-  }
-  // first row of tile i
-  __device__ int row0(int i) const {
-    if (!wv) return r0 + i * R;
-    int t = first + i * stride;
-    if (rev) t = T - 1 - t;
-    return t * R;
-  }
 
   __device__ bool add(const void* base, int row_bytes) {
     if (ns >= kMaxStreams || (row_bytes & 15) || (((uintptr_t)base) & 15)) return false;
@@ -495,10 +469,10 @@ struct BulkTiles {
     ns++;
     return true;
   }
-  __device__ int rows(int i) const { return min(R, (wv ? n : r1) - row0(i)); }
+  __device__ int rows(int i) const { return min(R, r1 - (r0 + i * R)); }
   // thread 0 only
   __device__ void issue(int i) {
-    const int row0 = this->row0(i), nr = rows(i), s = i % S;
+    const int row0 = r0 + i * R, nr = rows(i), s = i % S;
     uint32_t tx = 0;
     for (int j = 0; j < ns; j++) tx += (uint32_t)(nr * st[j].row_bytes);
     mbar_expect_tx(&bar[s], tx);
@@ -785,7 +759,8 @@ __global__ void __launch_bounds__(kThreads) k_tdot_window(KP P, int gw, const T*
   bulk = bulk && span <= kChunk && bt.add(B, WB * (int)sizeof(T));
   bulk = bulk && 64u + (uint32_t)S * (uint32_t)bt.stage_bytes <= dyn_smem_bytes();
   if (bulk) {
-    bt.wave(P.n, P.rev);
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
     // block j's tile starts R * (D[j].off - D[jlo].off) elements into a stage
     if (threadIdx.x < ncol) {
       const int cg = c0 + threadIdx.x;
@@ -989,7 +964,8 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
       cstr[cg] = D[lo].w;
     }
     for (int idx = threadIdx.x; idx < wtot * W; idx += blockDim.x) sC[idx] = (T)Cin[idx];
-    bt.wave(P.n, P.rev);
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
     const int xofs = R * wtot;
     if constexpr (sizeof(T) == 4 && W % 4 == 0) {
       // FP32: each thread owns 2 rows x 4 columns of the tile and reads, per
@@ -1009,7 +985,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
         for (int i = 0; i < bt.ntiles; i++) {
           if (!bt.ready(i, (DevState*)st)) return;
           const float* stg = (const float*)bt.tile(i);
-          const int row0 = bt.row0(i), nr = bt.rows(i);
+          const int row0 = bt.r0 + i * R, nr = bt.rows(i);
           float acc[2][4];
           if (active) {
 #pragma unroll
@@ -1056,7 +1032,7 @@ __global__ void __launch_bounds__(kThreads) k_update(KP P, int gw, T* Xio, const
     for (int i = 0; i < bt.ntiles; i++) {
       if (!bt.ready(i, (DevState*)st)) return;
       const T* stg = (const T*)bt.tile(i);
-      const int row0 = bt.row0(i), nr = bt.rows(i);
+      const int row0 = bt.r0 + i * R, nr = bt.rows(i);
       T acc[EPT];
 #pragma unroll
       for (int q = 0; q < EPT; q++) {
@@ -1208,7 +1184,8 @@ __device__ __forceinline__ bool gram_self_f32(const KP& P, const DevState* st, c
   bt.stage = smem_raw + 64;
   bt.R = R;
   bt.add(Xin, W * (int)sizeof(float));
-  bt.wave(P.n, P.rev);
+  cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+  bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
   const int eb = threadIdx.x % EU, rs = threadIdx.x / EU;
   const bool active = rs < RS;
   int ab, bb;
@@ -1297,7 +1274,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_self(KP P, int gw, const T* X
   bt.stage = smem_raw + 64;
   bt.R = R;
   if (bt.add(Xin, W * (int)sizeof(T))) {
-    bt.wave(P.n, P.rev);
+    cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+    bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
     bt.start();
     for (int i = 0; i < bt.ntiles; i++) {
       if (!bt.ready(i, (DevState*)st)) return;
@@ -1526,11 +1504,6 @@ template <int W>
 __host__ __device__ constexpr size_t smem_spmm_f32_tiles() {
   return sizeof(float) * (2 * kThreads * PadStride<W>::SP + W * W);
 }
-// Nonzeros of a 256-row tile that the FP32 spmm_gram stages in shared
-// memory (a column index and a value each, in the X and Y tiles' space,
-// which holds at least 2 x 256 x 8 floats): 8 per row on average.  A tile
-// with more reads its nonzeros from global memory.
-constexpr int kCsrCap = 2048;
 template <int W>
 constexpr size_t smem_spmm_f32() {
   return smem_spmm_f32_tiles<W>() + sizeof(double) * 16 * kThreads;
@@ -1575,59 +1548,45 @@ __device__ __forceinline__ bool spmm_gram_f32(const KP& P, const float* Xin, flo
   }
 #pragma unroll
   for (int k = 0; k < 16; k++) acc[k * kThreads + threadIdx.x] = 0.0;
-  const int ntile = (P.n + R - 1) / R;  // the rows' tiles, swept as a wavefront (BulkTiles::wave)
-  // the tile's nonzeros go to shared memory (coalesced loads) in the X and Y
-  // tile space, which is free until the products are stored, so that each
-  // gather waits on a shared-memory index instead of a global one
-  int* sCol = reinterpret_cast<int*>(sX);
-  float* sVal = reinterpret_cast<float*>(sX) + kCsrCap;
-  for (int tt = blockIdx.x; tt < ntile; tt += gridDim.x) {
-    const int row0 = (P.rev ? ntile - 1 - tt : tt) * R;
-    const int nr = min(R, P.n - row0);
-    const int p0 = P.rowptr[row0], p1 = P.rowptr[row0 + nr];
-    const bool staged = (p1 - p0) <= kCsrCap;
-    if (staged)
-      for (int p = p0 + threadIdx.x; p < p1; p += kThreads) {
-        sCol[p - p0] = P.col[p];
-        sVal[p - p0] = val[p];
-      }
+  int r0, r1;
+  cta_rows(P.n, r0, r1);
+  for (int row0 = r0; row0 < r1; row0 += R) {
+    const int nr = min(R, r1 - row0);
     int pb[IT], pe[IT];
-    float4 y[IT], xv[IT];
+    float4 y[IT];
     int kmax = 0;
 #pragma unroll
     for (int q = 0; q < IT; q++) {
-      const int idx = threadIdx.x + q * kThreads, r = idx / C4;
+      const int r = (threadIdx.x + q * kThreads) / C4;
       pb[q] = pe[q] = 0;
-      xv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (r < nr) {
         pb[q] = P.rowptr[row0 + r];
         pe[q] = P.rowptr[row0 + r + 1];
-        xv[q] = X4[(long long)(row0 + r) * C4 + idx % C4];
       }
       kmax = max(kmax, pe[q] - pb[q]);
       y[q] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncthreads();  // the staged nonzeros
-#pragma unroll 2
     for (int k = 0; k < kmax; k++) {
 #pragma unroll
       for (int q = 0; q < IT; q++) {
         const int p = pb[q] + k;
         if (p < pe[q]) {
           const int c = (threadIdx.x + q * kThreads) % C4;
-          const int cj = staged ? sCol[p - p0] : P.col[p];
-          const float vj = staged ? sVal[p - p0] : val[p];
-          f4fma(y[q], vj, X4[(long long)cj * C4 + c]);
+          f4fma(y[q], val[p], X4[(long long)P.col[p] * C4 + c]);
         }
       }
     }
-    __syncthreads();  // every staged nonzero read before the tiles overwrite them
 #pragma unroll
     for (int q = 0; q < IT; q++) {
       const int idx = threadIdx.x + q * kThreads, r = idx / C4, c = idx % C4;
-      if (r < nr) Y4[(long long)(row0 + r) * C4 + c] = y[q];
+      float4 xv = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (r < nr) {
+        const long long o = (long long)(row0 + r) * C4 + c;
+        Y4[o] = y[q];
+        xv = X4[o];
+      }
       *reinterpret_cast<float4*>(sY + r * SP + 4 * c) = y[q];
-      *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = xv[q];
+      *reinterpret_cast<float4*>(sX + r * SP + 4 * c) = xv;
     }
     {
       const int r = threadIdx.x;
@@ -1904,7 +1863,8 @@ __device__ __forceinline__ bool final_f32(const KP& P, const DevState* st, const
   bt.R = R;
   bt.add(Xin, W * (int)sizeof(float));
   bt.add(Yin, W * (int)sizeof(float));
-  bt.wave(P.n, P.rev);
+  cta_rows_aligned(P.n, R, bt.r0, bt.r1);
+  bt.ntiles = (bt.r1 - bt.r0 + R - 1) / R;
   bt.start();  // its barrier also publishes sRi and sal
   double rho_acc = 0.0;
   RowAcc<float> beta_acc;
@@ -1914,7 +1874,7 @@ __device__ __forceinline__ bool final_f32(const KP& P, const DevState* st, const
     if (!bt.ready(i, (DevState*)st)) return true;
     float* tX = (float*)bt.tile(i);
     float* tY = tX + R * W;
-    const int nr = bt.rows(i), row0 = bt.row0(i);
+    const int nr = bt.rows(i), row0 = bt.r0 + i * R;
     const int r = threadIdx.x;
     float rn = 0.f;
     if (r < nr) {
@@ -2637,9 +2597,22 @@ __global__ void __launch_bounds__(kThreads) k_block_update(KP P, int gw) {
 
 // End of iteration k: rho_k, tol1, window push, stop and switch tests.
 // elem_bytes is the size of the solve's scalar type (slot addresses).
+__device__ void finish_state(const KP& P, DevState* st, int W, double s, int elem_bytes);
+
+// The device state is copied into shared memory with coalesced loads, thread
+// 0 updates the copy, and the CTA writes it back: the updates are a chain of
+// dependent field reads and writes, each a round trip to L2 when done in
+// global memory.
 __global__ void k_finish(KP P, int gw, int gx, int elem_bytes) {
   __shared__ double sbuf[kThreads];
-  DevState* st = P.st;
+  __shared__ DevState sdev;
+  static_assert(sizeof(DevState) % 4 == 0, "DevState is copied as 32-bit words");
+  constexpr int NW = (int)(sizeof(DevState) / 4);
+  DevState* gst = P.st;
+  for (int i = threadIdx.x; i < NW; i += blockDim.x)
+    reinterpret_cast<int*>(&sdev)[i] = reinterpret_cast<const int*>(gst)[i];
+  __syncthreads();
+  DevState* st = &sdev;
   if (skip(st, gw)) return;
   double s = 0.0;
   for (int c = threadIdx.x; c < gx; c += blockDim.x) s += P.rho_part[c];
@@ -2652,7 +2625,15 @@ __global__ void k_finish(KP P, int gw, int gx, int elem_bytes) {
       if (lane == 0) P.small[kSmallBe + col] = -bsum;
     }
   }
-  if (threadIdx.x != 0) return;
+  if (threadIdx.x == 0) finish_state(P, st, W, s, elem_bytes);
+  __syncthreads();
+  for (int i = threadIdx.x; i < NW; i += blockDim.x)
+    reinterpret_cast<int*>(gst)[i] = reinterpret_cast<const int*>(&sdev)[i];
+}
+
+// k_finish's serial part (one thread) on the state st: rho_k, the history,
+// the window push, the stopping test, restarts and the flexible switch.
+__device__ void finish_state(const KP& P, DevState* st, int W, double s, int elem_bytes) {
   const int k = st->k;
   const double rho = sqrt(s);
   st->rho = rho;
