@@ -570,7 +570,10 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
   const int gfin = F32Rows<T, W>::on ? c->gx_fin32[width_index(W)] : c->gx;
   const int ggs = F32Rows<T, W>::on ? c->gx_gram32[width_index(W)] : c->gx;
   const long long tot = (long long)c->n * W;
-  const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 8LL * c->num_sms));
+  // the generator is a no-op on the SRE iterations of the FP32 and
+  // preconditioned solves, where the cost of a launch is its CTAs: two per SM,
+  // grid-stride otherwise
+  const int ggen = (int)std::max<long long>(1, std::min<long long>((tot + kThreads - 1) / kThreads, 2LL * c->num_sms));
   prof_mark(c, -1);
   if (c->prec_nb > 0) {  // preconditioned generators (Section 3, Algorithm 5)
     const PrecP Q = make_precp(c, fp32);
