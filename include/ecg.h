@@ -90,7 +90,11 @@ typedef struct {
                         iterations when the window size is fixed (default 1) */
   int precision;     /* ECG_FP64 (default) or ECG_MIXED */
   double inner_tol;  /* ECG_MIXED: relative residual reduction each FP32
-                        inner solve aims for (default 1e-5; 0 = default) */
+                        inner solve aims for (default 1e-5; 0 = default).
+                        An inner solve also ends after 200 iterations
+                        without a 1% smaller residual (FP32 stalls near
+                        its rounding times the conditioning); the FP64
+                        refinement then starts the next one */
   int restart_every; /* Section 3, restarted methods: j >= 2 restarts at the
                         iterations k with k mod j == 1 (0: off) */
   double restart_tol;   /* > 0: restart when |rho_{k-1} - rho_{k-2}| / rho_c

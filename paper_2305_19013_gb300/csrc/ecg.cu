@@ -43,6 +43,9 @@ namespace {
 constexpr int kWidths[] = {1, 2, 4, 8, 16, 32, 64};
 constexpr double kBreakdownFP64 = 1e-14;  // Cholesky pivot test, FP64 data
 constexpr double kBreakdownFP32 = 1e-8;   // FP32 blocks: Grams carry ~1e-7 rounding
+// FP32 rounds of mixed precision end after this many iterations without a 1%
+// smaller residual (see run_solve)
+constexpr int kStagIters = 200;
 constexpr int kMaxOuter = 64;             // refinement steps of the mixed method
 
 int width_index(int w) {
@@ -742,6 +745,11 @@ int run_solve(ecg_ctx* c, bool fp32, int kmax, int cap, double eps, int hist_off
   init.restart_tol = c->opts.restart_tol;
   init.restart_max = c->opts.restart_max;
   init.restart_at_switch = c->opts.restart_at_switch;
+  // an FP32 round that stalls above its target (its floor lies near FP32
+  // rounding times the conditioning) ends after kStagIters iterations without
+  // a 1% smaller residual, instead of running to k_max
+  init.stag_iters = fp32 ? kStagIters : 0;
+  init.rho_best = HUGE_VAL;
   CK(cudaMemcpyAsync(c->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, s));
   KP P = make_kp(c, c->d_st, c->d_desc, fp32);
   prof_mark(c, -1);

@@ -81,6 +81,10 @@ struct DevState {
   int restart_max;        // restarts allowed by restart_tol (0: unlimited)
   int restart_at_switch;  // 1: the flexible switch also restarts
   int fault;              // 1: a bounded wait on a bulk copy ran out
+  int stag_iters;         // > 0: end the solve when rho_k has not fallen below
+                          // 0.99 rho_best for this many iterations (the FP32
+                          // rounds of mixed precision; the refinement goes on)
+  int best_k;             // iteration of rho_best
   double restart_tol;     // > 0: restart when rtol1 < restart_tol
   double rho_cycle;       // residual norm at the start of the current cycle
   double rtol1;           // |rho_k - rho_{k-1}| / rho_cycle
@@ -88,6 +92,7 @@ struct DevState {
   double eps, switch_tol;
   double breakdown_ratio;  // Cholesky pivot test: pivot > ratio * diagonal
   double rho0, rho_prev, tol1, rho;
+  double rho_best;        // smallest rho_k so far, up to 1% (stag_iters)
 };
 
 // Offsets of the small matrices inside KP::small (t <= 64).
@@ -2642,6 +2647,10 @@ __device__ void finish_state(const KP& P, DevState* st, int W, double s, int ele
   st->rtol1 = fabs(rho - st->rho_prev) / st->rho_cycle;
   st->rho_prev = rho;
   st->iters = k;
+  if (st->stag_iters > 0 && !(rho >= 0.99 * st->rho_best)) {
+    st->rho_best = rho;
+    st->best_k = k;
+  }
   // memory count: the window used this iteration plus the new block
   long long stored = W;
   for (int j = 0; j < st->nq; j++) stored += P.desc[j].w;
@@ -2675,6 +2684,9 @@ __device__ void finish_state(const KP& P, DevState* st, int W, double s, int ele
     st->status = ST_OK;
   } else if (knext >= st->kmax) {
     st->stop = 1;
+    st->status = ST_ENOCONV;
+  } else if (st->stag_iters > 0 && k - st->best_k >= st->stag_iters) {
+    st->stop = 1;  // stagnated: the caller's refinement continues from x_k
     st->status = ST_ENOCONV;
   } else {
     const bool do_switch = st->switch_tol > 0.0 && st->counter == 0 && st->tol1 < st->switch_tol;
