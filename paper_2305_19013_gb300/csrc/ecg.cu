@@ -1133,9 +1133,10 @@ int prec_build(ecg_ctx* c, const std::vector<int>& pb, int nb) {
   if (local) {
     const int K = std::max(Kf, Kb);
     const size_t fixed = 2 * (size_t)maxw * kPrecCols * sizeof(double);
-    const size_t budget = 104 * 1024, per = prec_chunk_bytes(1, K, (int)sizeof(double)) - sizeof(int) * (kChunkLevels + 1);
-    const size_t lev_bytes = sizeof(int) * (kChunkLevels + 1);
-    if (budget > fixed + lev_bytes) qc = (int)std::min<size_t>(4096, (budget - fixed - lev_bytes) / per);
+    const size_t budget = 104 * 1024;
+    const size_t per = sizeof(double) * (1 + K + kPrecCols) + sizeof(int) * (2 + K);
+    const size_t extra = prec_chunk_bytes(0, K, (int)sizeof(double)) + 112;  // level bounds, slack, rounding
+    if (budget > fixed + extra) qc = (int)std::min<size_t>(4096, (budget - fixed - extra) / per);
     if (qc < maxw) qc = 0;
   }
   auto chunks = [&](const std::vector<int>& blk, const std::vector<int>& lev, ecg_ctx::Sweep& w) {

@@ -2339,10 +2339,15 @@ __device__ void prec_sweep_local(const PrecSweep& S, int b, const T* in, T* out,
 // two memory latencies; a level no global load.
 constexpr int kChunkLevels = 256;
 
-// Bytes of the chunk buffers for qc positions, K entries per row and T.
+// Bytes of the chunk buffers for qc positions, K entries per row and T: one
+// 16-byte-aligned region per array, each but the right-hand sides with 16
+// bytes of slack, so that a chunk's copy of a contiguous range can start at
+// the same address modulo 16 as its source (prec_sweep_chunks).
+__host__ __device__ constexpr size_t pad16(size_t x) { return (x + 15) & ~(size_t)15; }
 __host__ __device__ constexpr size_t prec_chunk_bytes(int qc, int K, int tsize) {
-  return (size_t)qc * tsize * (1 + K + kPrecCols) + (size_t)qc * sizeof(int) * (2 + K) +
-         sizeof(int) * (kChunkLevels + 1);
+  return pad16((size_t)qc * tsize + 16) + pad16((size_t)qc * K * tsize + 16) +
+         pad16((size_t)qc * kPrecCols * tsize) + 2 * pad16((size_t)qc * sizeof(int) + 16) +
+         pad16((size_t)qc * K * sizeof(int) + 16) + pad16(sizeof(int) * (kChunkLevels + 1) + 16);
 }
 
 // Asynchronous 4- or 8-byte copies global -> shared (cp.async): a thread
@@ -2354,41 +2359,82 @@ __device__ __forceinline__ void cp_async_elem(void* sdst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(sdst)), "l"(gsrc), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+// The n elements of E bytes at gsrc into sdst (the same address modulo 16),
+// by the CTA: 16-byte copies for the aligned body, element copies for the
+// ends.
+template <int E>
+__device__ __forceinline__ void cp_async_span(void* sdst, const void* gsrc, int n) {
+  unsigned char* d = (unsigned char*)sdst;
+  const unsigned char* g = (const unsigned char*)gsrc;
+  const int bytes = n * E;
+  const int head = min(bytes, (int)((16 - ((uintptr_t)g & 15)) & 15));
+  const int body = (bytes - head) & ~15;
+  for (int i = threadIdx.x; i < head / E; i += blockDim.x) cp_async_elem<E>(d + i * E, g + i * E);
+  for (int i = threadIdx.x; i < body / 16; i += blockDim.x) cp_async_16(d + head + 16 * i, g + head + 16 * i);
+  for (int i = threadIdx.x; i < (bytes - head - body) / E; i += blockDim.x)
+    cp_async_elem<E>(d + head + body + i * E, g + head + body + i * E);
+}
+// The first address at or after p with the same remainder modulo 16 as g.
+__device__ __forceinline__ unsigned char* align_like(unsigned char* p, const void* g) {
+  const uintptr_t pp = (uintptr_t)p;
+  return (unsigned char*)(pp + ((((uintptr_t)g & 15) - pp) & 15));
+}
 
 template <typename T, int KM, bool FWD>
 __device__ void prec_sweep_chunks(const PrecSweep& S, int b, const T* in, T* out, int w, int c0, int nc, int qc,
                                   T* sprev, T* scur, unsigned char* cbuf) {
   const int K = S.K;
-  T* s_diag = (T*)cbuf;                          // qc
-  T* s_val = s_diag + qc;                        // qc x K
-  T* s_rhs = s_val + (size_t)qc * K;             // qc x kPrecCols
-  int* s_rows = (int*)(s_rhs + (size_t)qc * kPrecCols);  // qc
-  int* s_cnt = s_rows + qc;                      // qc
-  int* s_dep = s_cnt + qc;                       // qc x K
-  int* s_lev = s_dep + (size_t)qc * K;           // kChunkLevels + 1
+  // regions of the chunk buffer (prec_chunk_bytes); each chunk places its
+  // arrays at the alignment of their sources, so that the contiguous ranges
+  // move as 16-byte copies
+  unsigned char* r_diag = cbuf;
+  unsigned char* r_val = r_diag + pad16((size_t)qc * sizeof(T) + 16);
+  T* s_rhs = (T*)(r_val + pad16((size_t)qc * K * sizeof(T) + 16));  // qc x kPrecCols
+  unsigned char* r_rows = (unsigned char*)s_rhs + pad16((size_t)qc * kPrecCols * sizeof(T));
+  unsigned char* r_cnt = r_rows + pad16((size_t)qc * sizeof(int) + 16);
+  unsigned char* r_dep = r_cnt + pad16((size_t)qc * sizeof(int) + 16);
+  unsigned char* r_lev = r_dep + pad16((size_t)qc * K * sizeof(int) + 16);
   const T* val = (const T*)S.val;
   const T* diag = (const T*)S.diag;
   const T* src = FWD ? in : out;  // backward: y = L^{-1} in, already in out
+  // a position's kPrecCols right-hand sides are one or two 16-byte pieces
+  constexpr int RB = kPrecCols * (int)sizeof(T);
+  const bool rhs16 = (nc == kPrecCols) && (RB % 16 == 0) && ((w * (int)sizeof(T)) % 16 == 0) &&
+                     ((c0 * (int)sizeof(T)) % 16 == 0) && (((uintptr_t)src & 15) == 0);
   for (int j = S.cblk[b]; j < S.cblk[b + 1]; j++) {
     const int la = S.cpos[j], lb = S.cpos[j + 1];
     const int qa = S.cq[j], nq = S.cq[j + 1] - qa, nl = lb - la;
+    T* s_diag = (T*)align_like(r_diag, diag + qa);                      // nq
+    T* s_val = (T*)align_like(r_val, val + (long long)qa * K);           // nq x K
+    int* s_rows = (int*)align_like(r_rows, S.rows + qa);                 // nq
+    int* s_cnt = (int*)align_like(r_cnt, S.cnt + qa);                    // nq
+    int* s_dep = (int*)align_like(r_dep, S.dep + (long long)qa * K);     // nq x K
+    int* s_lev = (int*)align_like(r_lev, S.lev + la);                    // nl + 1
     __syncthreads();  // the previous chunk's buffers are no longer read
     // level bounds stay global positions (the level loop subtracts qa)
-    for (int i = threadIdx.x; i <= nl; i += blockDim.x) cp_async_elem<4>(&s_lev[i], &S.lev[la + i]);
-    for (int i = threadIdx.x; i < nq; i += blockDim.x) {
-      cp_async_elem<4>(&s_rows[i], &S.rows[qa + i]);
-      cp_async_elem<4>(&s_cnt[i], &S.cnt[qa + i]);
-      cp_async_elem<sizeof(T)>(&s_diag[i], &diag[qa + i]);
-    }
-    for (int i = threadIdx.x; i < nq * K; i += blockDim.x) {
-      cp_async_elem<sizeof(T)>(&s_val[i], &val[(long long)qa * K + i]);
-      cp_async_elem<4>(&s_dep[i], &S.dep[(long long)qa * K + i]);
-    }
+    cp_async_span<4>(s_lev, S.lev + la, nl + 1);
+    cp_async_span<4>(s_rows, S.rows + qa, nq);
+    cp_async_span<4>(s_cnt, S.cnt + qa, nq);
+    cp_async_span<sizeof(T)>(s_diag, diag + qa, nq);
+    cp_async_span<sizeof(T)>(s_val, val + (long long)qa * K, nq * K);
+    cp_async_span<4>(s_dep, S.dep + (long long)qa * K, nq * K);
     cp_async_wait_all();
     __syncthreads();
-    for (int i = threadIdx.x; i < nq * nc; i += blockDim.x) {
-      const int qi = i / nc, c = i - qi * nc;
-      cp_async_elem<sizeof(T)>(&s_rhs[qi * kPrecCols + c], &src[(long long)s_rows[qi] * w + c0 + c]);
+    if (rhs16) {
+      constexpr int PC = RB / 16;  // 16-byte pieces per position
+      for (int i = threadIdx.x; i < nq * PC; i += blockDim.x) {
+        const int qi = i / PC, h = i - qi * PC;
+        cp_async_16((unsigned char*)&s_rhs[qi * kPrecCols] + 16 * h,
+                    (const unsigned char*)&src[(long long)s_rows[qi] * w + c0] + 16 * h);
+      }
+    } else {
+      for (int i = threadIdx.x; i < nq * nc; i += blockDim.x) {
+        const int qi = i / nc, c = i - qi * nc;
+        cp_async_elem<sizeof(T)>(&s_rhs[qi * kPrecCols + c], &src[(long long)s_rows[qi] * w + c0 + c]);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
