@@ -91,7 +91,7 @@ typedef struct {
   int precision;     /* ECG_FP64 (default) or ECG_MIXED */
   double inner_tol;  /* ECG_MIXED: relative residual reduction each FP32
                         inner solve aims for (default 1e-5; 0 = default).
-                        An inner solve also ends after 200 iterations
+                        An inner solve also ends after 400 iterations
                         without a 1% smaller residual (FP32 stalls near
                         its rounding times the conditioning); the FP64
                         refinement then starts the next one */

@@ -45,7 +45,7 @@ constexpr double kBreakdownFP64 = 1e-14;  // Cholesky pivot test, FP64 data
 constexpr double kBreakdownFP32 = 1e-8;   // FP32 blocks: Grams carry ~1e-7 rounding
 // FP32 rounds of mixed precision end after this many iterations without a 1%
 // smaller residual (see run_solve)
-constexpr int kStagIters = 200;
+constexpr int kStagIters = 400;
 constexpr int kMaxOuter = 64;             // refinement steps of the mixed method
 
 int width_index(int w) {

@@ -78,7 +78,7 @@ def test_mixed_at_full_size_reports_its_true_residual():
     FP32 blocks make fast early progress but stall near 1e-5, so the mixed
     method does not reach 1e-8 here (the FP64 method does).  What must hold
     is that the status says so and that the reported true residual is the
-    FP64 residual of the returned x.  A stalled round ends after 200
+    FP64 residual of the returned x.  A stalled round ends after 400
     iterations without a 1% smaller residual, and the refinement stops when
     a round brings no progress, so the solve may end before maxit."""
     if not torch.cuda.is_available():
@@ -97,7 +97,7 @@ def test_mixed_at_full_size_reports_its_true_residual():
 
 def test_stalled_rounds_end_and_refinement_converges():
     """An inner tolerance below what the FP32 rounds reach (1e-9; they stall
-    near FP32 rounding times the conditioning): each round ends after 200
+    near FP32 rounding times the conditioning): each round ends after 400
     iterations without a 1% smaller residual instead of running to maxit,
     and the FP64 refinement still meets the FP64 tolerance."""
     if not torch.cuda.is_available():
