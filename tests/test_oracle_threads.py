@@ -5,7 +5,8 @@ fixed chunks of rows added in chunk order, so the number of threads cannot
 change a result.  These cases have several chunks and a ragged last one
 (10,000 rows), and cover every function the full-size parity tests and the
 benchmark's CPU baseline run through threads: the products, the Householder
-QR, the solvers (SRE, MSDO, flexible, truncated) and the block Jacobi
+QR, both Pre-CholQR readings, the solvers (SRE, MSDO, flexible, truncated)
+and the block Jacobi
 preconditioner (setup, substitutions, preconditioned solve).  CPU only.
 """
 import numpy as np
@@ -34,22 +35,24 @@ def test_products_and_qr_bitwise_equal():
     rng = np.random.default_rng(3)
     X = rng.standard_normal((p.n, 16))
     Y = rng.standard_normal((p.n, 8))
-    a, b = both(lambda: (O.spmm(A, X), O.block_tdot(X, Y), O.householder_qr(X), O.a_orthonormalize(A, X, 0)))
+    a, b = both(lambda: (O.spmm(A, X), O.block_tdot(X, Y), O.householder_qr(X), O.a_orthonormalize(A, X, 0),
+                         O.a_orthonormalize(A, X, 2)))
     assert np.array_equal(a[0], b[0])
     assert np.array_equal(a[1], b[1])
-    for u, v in zip(a[2], b[2]):
-        assert np.array_equal(u, v)
-    for u, v in zip(a[3], b[3]):
-        assert np.array_equal(u, v)
+    for k in (2, 3, 4):
+        for u, v in zip(a[k], b[k]):
+            assert np.array_equal(u, v)
 
 
-@pytest.mark.parametrize("variant,trunc,switch", [("sre", 2, 0.0), ("msdo", 3, 0.0), ("sre", 0, 1e-4)])
-def test_solves_bitwise_equal(variant, trunc, switch):
+@pytest.mark.parametrize("variant,trunc,switch,ortho", [("sre", 2, 0.0, 0), ("msdo", 3, 0.0, 0), ("sre", 0, 1e-4, 0),
+                                                        ("sre", 2, 0.0, 2)])
+def test_solves_bitwise_equal(variant, trunc, switch, ortho):
     p = W.random_spd_grid(100, 8, seed=12)
     A = p.scipy()
 
     def run():
-        return O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=60, variant=variant, trunc=trunc, switch_tol=switch)
+        return O.ecg_solve(A, p.part, p.t, p.b, tol=1e-8, maxit=60, variant=variant, trunc=trunc, switch_tol=switch,
+                           ortho=ortho)
 
     a, b = both(run)
     assert a.iters == b.iters and a.status == b.status and a.switch_it == b.switch_it
