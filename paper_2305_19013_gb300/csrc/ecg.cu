@@ -105,6 +105,7 @@ struct ecg_ctx {
   // FP32 spmm_gram / final grids by block width index (log2 W): one wave at
   // the kernels' occupancy, at most gx
   int gx_spmm32[7] = {}, gx_fin32[7] = {}, gx_gram32[7] = {};
+  int gx_spmm64[7] = {};  // FP64 A-CholQR SpMM + Gram: one wave at its occupancy (not capped at gx)
   // occupancy-sized grids of the CGS kernels by (kernel, shared memory)
   struct OccEntry {
     const void* kernel;
@@ -502,11 +503,34 @@ void set_f32_grid(ecg_ctx* c, int wi) {
   c->gx_gram32[wi] = occupancy_grid(c, (const void*)k_gram_self<float, W>, smem_gram_self<float, W>());
 }
 
+// The FP64 SpMM + Gram on q waits on its gathers between FMA phases; it
+// runs at its full occupancy (8 CTAs per SM at t = 16), beyond gx, and at most
+// one CTA per 32 rows.
+template <int W>
+void set_f64_spmm_grid(ecg_ctx* c) {
+  int per_sm = 0;
+  int g = c->gx;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_spmm_gram<double, W, true, false>, kThreads,
+                                                    smem_spmm<double, W>()) == cudaSuccess &&
+      per_sm > 0)
+    g = std::max(1, std::min(per_sm * c->num_sms, (c->n + 31) / 32));
+  else
+    cudaGetLastError();
+  c->gx_spmm64[width_index(W)] = std::max(g, 1);
+}
+
 void set_f32_grids(ecg_ctx* c) {
   for (int i = 0; i < 7; i++) c->gx_spmm32[i] = c->gx_fin32[i] = c->gx_gram32[i] = c->gx;
   set_f32_grid<4>(c, width_index(4));
   set_f32_grid<8>(c, width_index(8));
   set_f32_grid<16>(c, width_index(16));
+  set_f64_spmm_grid<1>(c);
+  set_f64_spmm_grid<2>(c);
+  set_f64_spmm_grid<4>(c);
+  set_f64_spmm_grid<8>(c);
+  set_f64_spmm_grid<16>(c);
+  set_f64_spmm_grid<32>(c);
+  set_f64_spmm_grid<64>(c);
 }
 
 // Grid of the tensor-core kernels: two CTAs per SM, at most one per
@@ -606,10 +630,11 @@ int enqueue_iteration(ecg_ctx* c, int gy, int wcap) {
     prof_mark(c, 4);
     k_tri_right<T, W><<<c->gx, kThreads, smem_tri_right<T, W>(), s>>>(P, W, X);
     prof_mark(c, 3);
-    k_spmm_gram<T, W, true, false><<<gsp, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
+    const int gsp64 = c->gx_spmm64[width_index(W)];
+    k_spmm_gram<T, W, true, false><<<gsp64, kThreads, smem_spmm<T, W>(), s>>>(P, W, X, Y);
     prof_mark(c, 5);
-    reduce_small(c, P, W, W * (W + 1) / 2 + W, gsp);
-    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp);
+    reduce_small(c, P, W, W * (W + 1) / 2 + W, gsp64);
+    k_small_a<W, false><<<1, kThreads, smem_small<W>(), s>>>(P, W, gsp64);
   } else if (pre) {
     k_gram_self<T, W><<<ggs, kThreads, smem_gram_self<T, W>(), s>>>(P, W, X);
     prof_mark(c, 3);
@@ -1487,7 +1512,11 @@ int ecg_solve(ecg_ctx* c, const double* b, const double* x0, double* x_out, doub
   if ((rc = ensure_C(c, (size_t)cap * t * t))) return rc;
   {
     const size_t gymax = ((size_t)cap * t + kChunk - 1) / kChunk;
-    size_t need = std::max((4 * (size_t)c->num_sms + gymax) * kChunk * t, (size_t)c->gx * (t * (t + 1) / 2 + t));
+    size_t need = (4 * (size_t)c->num_sms + gymax) * kChunk * t;
+    for (int i = 0; i < 7 && kWidths[i] <= t; i++) {  // every width a solve can use (t, t/2 after the switch)
+      const size_t w = (size_t)kWidths[i];
+      need = std::max(need, (size_t)std::max(c->gx, c->gx_spmm64[i]) * (w * (w + 1) / 2 + w));
+    }
     if (c->opts.block_residual) need = std::max(need, (size_t)c->gx * t * t);
     if ((rc = ensure_part(c, need))) return rc;
   }
